@@ -1,0 +1,174 @@
+/*
+ * fairrank.h -- C ABI of libfairrank: NSW fair ranking by gradient ascent over batched Sinkhorn
+ * solves on one GB300 (sm_103a).
+ *
+ * Method: Uehara et al., "Fast solution to the fair ranking problem using the Sinkhorn algorithm"
+ * (arXiv 2406.10262). Each consumer u gets a stochastic ranking X_u (|I| items x m columns) that
+ * satisfies Eqs. (1)-(3): every item row sums to 1, each of the K real slots receives mass 1, and
+ * a last dummy slot receives |I|-K (Sec. 2; it is dropped when |I| == K). The library maximises
+ * the Nash social welfare F = sum_i log Imp_i (Eq. 5), Imp_i = sum_u sum_{k<K} r(u,i) e(k) x_uik
+ * (Eq. 4), over transport costs C (Problem (8)): every step solves the entropic optimal-transport
+ * problem (7) of every consumer by log-domain Sinkhorn, reduces impacts across consumers, and
+ * moves C along grad_C F(X*(C)) with Adam (Algorithm 1, Sec. 4.1).
+ *
+ * Conventions for every entry point:
+ *  - Return value: FR_OK or an error status; fr_last_error() gives a message. Nothing throws.
+ *  - Pointers flagged `on_device` are device pointers (e.g. torch CUDA tensors) used on the
+ *    context's stream; other pointers are host memory. The library copies inputs, owns all device
+ *    state it allocates (cudaMalloc in fr_create / fr_set_relevance) and frees it in fr_destroy.
+ *    Outputs go to caller buffers of the stated size.
+ *  - Layouts are row-major and dense: relevance [n_users][n_items], policy / costs / moments
+ *    [n_users][n_items][n_cols], column potentials [n_users][n_cols].
+ *  - A context belongs to one host thread at a time; there is no global mutable state.
+ *  - Every call is stream-ordered on the context's stream and returns after the results it
+ *    reports are available on the host (host outputs) or enqueued (device outputs).
+ */
+#ifndef FAIRRANK_H
+#define FAIRRANK_H
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FR_API __attribute__((visibility("default")))
+#else
+#define FR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fr_ctx fr_ctx; /* opaque; owns all device state of one problem */
+
+typedef enum {
+    FR_OK = 0,
+    FR_EINVAL = 1,    /* invalid argument or configuration (message says which) */
+    FR_ENOMEM = 2,    /* device allocation failed */
+    FR_ECUDA = 3,     /* a CUDA call failed (message carries cudaGetErrorString) */
+    FR_ENUMERIC = 4,  /* an impact became non-positive or a value non-finite */
+    FR_ETIMEOUT = 5,  /* a bounded device-side wait expired */
+    FR_ESTATE = 6,    /* call order: e.g. fr_step before fr_set_relevance / fr_set_exposure */
+    FR_EUNSUPPORTED = 7 /* shape outside the compiled kernel variants (message gives the limit) */
+} fr_status;
+
+enum { FR_PARAM_FULL_C = 0, /* free cost tensor C of Problem (8) (the paper's parametrisation) */
+       FR_PARAM_ITEM = 1 }; /* c_uik = -r(u,i) e(k) exp(theta_i): per-item variables theta */
+enum { FR_GRAD_IMPLICIT = 0, FR_GRAD_UNROLLED = 1 };
+enum { FR_ADAM = 0, FR_SGD = 1 };
+enum { FR_F32 = 0, FR_BF16 = 1, FR_F64 = 2 };
+
+typedef struct fr_config {
+    int32_t n_users, n_items, n_slots; /* |U|, |I|, K; requires 1 <= K <= |I| */
+    int32_t param;          /* FR_PARAM_FULL_C | FR_PARAM_ITEM */
+    double  epsilon;        /* entropic regularisation of Problem (7), > 0 */
+    int32_t sinkhorn_iters; /* L >= 1 Sinkhorn iterations per consumer per step */
+    int32_t warm_start;     /* 1: each solve starts from the previous solve's column potentials */
+    int32_t grad_mode;      /* FR_GRAD_IMPLICIT (optimality conditions of Problem (7)) */
+    int32_t ckpt_every;     /* unrolled gradient: column-potential checkpoint interval */
+    int32_t optimizer;      /* FR_ADAM (PyTorch Adam, maximize) | FR_SGD */
+    double  lr, beta1, beta2, adam_eps;
+    int32_t rel_dtype;      /* storage of r on the device: FR_F32 | FR_BF16 */
+    int32_t reserved[7];    /* must be zero */
+} fr_config;
+
+/* Fills cfg with the defaults: epsilon 1, L = 50, warm start, implicit gradient, checkpoint every
+   10, Adam with lr 0.1 (FR_PARAM_FULL_C) or 0.05 (FR_PARAM_ITEM), betas (0.9, 0.999), eps 1e-8,
+   FP32 relevance. Algorithm 1 leaves these values open; they are this library's choices. */
+FR_API void fr_config_default(fr_config* cfg, int32_t n_users, int32_t n_items, int32_t n_slots,
+                       int32_t param);
+
+/* Number of stored columns m: n_slots + 1 when n_items > n_slots (dummy slot of Sec. 2), else
+   n_slots. */
+FR_API int32_t fr_num_cols(int32_t n_items, int32_t n_slots);
+
+/* Creates a context on the current CUDA device. stream: a cudaStream_t (NULL = legacy default
+   stream); every later call is ordered on it. Allocates the optimiser state (zero costs / theta =
+   the uniform policy, Algorithm 1's unspecified initialisation). FR_EINVAL on a bad config,
+   FR_EUNSUPPORTED on a shape outside the compiled variants, FR_ENOMEM. *out is NULL on error. */
+FR_API fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out);
+FR_API fr_status fr_destroy(fr_ctx* ctx);
+
+/* Resets the optimiser state to its initial value (costs / theta 0, moments 0, potentials 0,
+   t = 0) on the device without host transfers; the policy becomes stale. */
+FR_API fr_status fr_reset(fr_ctx* ctx);
+
+/* Relevance r(u,i) of Eq. (4): n_users x n_items, row stride ld elements (>= n_items), dtype
+   FR_F32 | FR_F64 | FR_BF16 (raw bfloat16 bits). Values must be finite and >= 0 and every item
+   needs some r(u,i) > 0 (log Imp_i of Eq. 5), else FR_EINVAL. Copied (and converted to the
+   configured storage dtype). */
+FR_API fr_status fr_set_relevance(fr_ctx* ctx, const void* r, int32_t dtype, int64_t ld,
+                           int32_t on_device);
+
+/* Exposure e(k) of the K real slots (Eq. 4), host doubles, each > 0 and finite (FR_EINVAL), K must
+   equal cfg.n_slots. The dummy slot has exposure 0. The certificate of fr_certificate additionally
+   needs e non-increasing. Copied. */
+FR_API fr_status fr_set_exposure(fr_ctx* ctx, const double* e, int32_t K);
+
+/* n_steps >= 0 ascent steps of Algorithm 1. If the policy is stale (first call, or after
+   fr_set_*), first solves Sinkhorn for the current parameters. Each step: gradient of F at the
+   current policy, optimiser update, Sinkhorn for every consumer with the new parameters, impacts
+   and F (FP64). nsw_trace (host, nullable, n_steps doubles) receives F after each step.
+   FR_ESTATE before both fr_set_relevance and fr_set_exposure; FR_ENUMERIC if an impact became
+   non-positive or non-finite (the state is then undefined). */
+FR_API fr_status fr_step(fr_ctx* ctx, int32_t n_steps, double* nsw_trace);
+
+/* Algorithm 1 with threshold t on ||grad F||_2 (gradient with respect to the optimised variable):
+   runs steps until one whose gradient norm is <= t (that step's update is applied) or max_steps.
+   *steps_done and *nsw_out (nullable) report the steps run and the final F. */
+FR_API fr_status fr_solve(fr_ctx* ctx, double t, int32_t max_steps, int32_t* steps_done,
+                   double* nsw_out);
+
+/* Current impacts Imp_i (Eq. 4; host, n_items doubles, nullable), user utility sum_i Imp_i / |U|
+   (Sec. 4.1, nullable) and F (Eq. 5, nullable) of the current policy; solves first if stale. */
+FR_API fr_status fr_impacts(fr_ctx* ctx, double* imp_out, double* utility_out, double* nsw_out);
+
+/* Policy X_u of consumers u0 .. u0+n_u-1 (rows of Eqs. (1)-(3)): float [n_u][n_items][n_cols],
+   host or device (on_device). Rows sum to 1 to rounding; the column residual is the remaining
+   Sinkhorn error. FR_EINVAL if the range leaves [0, n_users). */
+FR_API fr_status fr_policy(fr_ctx* ctx, int32_t u0, int32_t n_u, float* x_out, int32_t on_device);
+
+/* Gradient at the current policy of L = sum_i omega_i Imp_i, omega (n_items floats, nullable;
+   NULL means omega_i = 1/Imp_i, i.e. L = F of Eq. 5) in the configured grad_mode. dparam:
+   FR_PARAM_FULL_C dL/dC [n_users][n_items][n_cols]; FR_PARAM_ITEM dL/dtheta [n_items]. dr
+   (nullable): dL/dr [n_users][n_items]. All pointers host or device per on_device. */
+FR_API fr_status fr_grad(fr_ctx* ctx, const float* omega, float* dparam, float* dr, int32_t on_device);
+
+/* Optimiser state: parameters (FR_PARAM_FULL_C: C [n_users][n_items][n_cols]; FR_PARAM_ITEM:
+   theta [n_items]), Adam moments (same shape), column potentials g [n_users][n_cols] in the units
+   of C (the warm start of the next solve) and the Adam step count t. Any pointer may be NULL to
+   leave that part unchanged (set) or unread (get). Setting marks the policy stale. */
+FR_API fr_status fr_set_state(fr_ctx* ctx, const float* param, const float* m1, const float* m2,
+                       const float* g, int64_t t, int32_t on_device);
+FR_API fr_status fr_get_state(fr_ctx* ctx, float* param, float* m1, float* m2, float* g, int64_t* t,
+                       int32_t on_device);
+
+/* Evaluation metrics of Sec. 4.1 at the current policy (host doubles, each nullable): user
+   utility, mean max envy (1/|I|) sum_i max_j (Imp_i(X_j) - Imp_i(X_i)), and the percentage of
+   items whose impact is more than 10% above / below that of the uniform policy x_uik = b_k/|I|. */
+FR_API fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* better_pct,
+                     double* worse_pct);
+
+/* Message of the last failing call on ctx (or of the last failing fr_create on this thread when
+   ctx is NULL). Valid until the next call on ctx. */
+FR_API const char* fr_last_error(const fr_ctx* ctx);
+
+/* ---- measurement helpers --------------------------------------------------------------- */
+
+/* Number of kernels the library launched on ctx since creation (every launch is counted on the
+   host when it is enqueued, graph replays count their kernels). */
+FR_API int64_t fr_launch_count(const fr_ctx* ctx);
+
+/* Times the kernels of the ascent step with CUDA events recorded on the library stream around
+   each launch: runs n_steps >= 1 steps with direct launches (no graph) and writes the mean
+   duration in milliseconds of the fused gradient+Adam+Sinkhorn kernel (ms[0]) and of the
+   cross-consumer reduction kernel (ms[1]). Advances the optimiser state like fr_step. */
+FR_API fr_status fr_time_kernels(fr_ctx* ctx, int32_t n_steps, double* ms);
+
+/* Measures the sustained rate of ex2.approx.f32 on the current device with a dependent-chain-free
+   microbenchmark (grid = SMs x 4 CTAs): writes exp2 evaluations per second. Used as the measured
+   denominator of the Sinkhorn roofline. */
+FR_API fr_status fr_measure_ex2_rate(double* ex2_per_second);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

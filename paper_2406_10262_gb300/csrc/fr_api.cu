@@ -1,0 +1,700 @@
+// fr_api.cu -- the extern "C" entry points of libfairrank (include/fairrank.h).
+//
+// Host side of Algorithm 1: argument checking, device memory, stream ordering and the CUDA graphs
+// that replay chunks of ascent steps. Every step of the method itself runs in the kernels of
+// fr_p1.cu (Sinkhorn, impacts, gradient, Adam) and fr_common.cu (cross-consumer reduction).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fairrank.h"
+#include "fr_internal.h"
+
+using namespace fr;
+
+namespace {
+thread_local std::string g_create_error;
+constexpr int kChunk = 16;  // ascent steps per captured graph
+}
+
+struct fr_ctx {
+    fr_config cfg;
+    int U = 0, I = 0, K = 0, nc = 0, ld = 0, G = 0, nblk = 0;
+    int device = 0;
+    cudaStream_t user = nullptr;  // caller's stream (may be the legacy default stream)
+    cudaStream_t s = nullptr;     // library stream (non-blocking), joined to `user` per call
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    P1Variant var{};
+    float *C = nullptr, *m1 = nullptr, *m2 = nullptr, *gL = nullptr, *gP = nullptr;
+    float *r = nullptr, *e = nullptr, *log2b = nullptr, *omega = nullptr, *part = nullptr;
+    float* tmp = nullptr;  // staging for host transfers (U*I*nc floats)
+    size_t tmp_bytes = 0;
+    double *gn2_part = nullptr, *imp = nullptr, *blk = nullptr, *F_hist = nullptr, *gn_hist = nullptr;
+    int hist_cap = 0;
+    DevState* st = nullptr;
+    DevState* st_host = nullptr;  // pinned
+    int* flags = nullptr;
+    bool have_r = false, have_e = false, fresh = false;
+    cudaGraphExec_t chunk_exec = nullptr;
+    int64_t launches = 0;
+    std::string err;
+};
+
+namespace {
+
+fr_status fail(fr_ctx* c, fr_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    else
+        g_create_error = buf;
+    return st;
+}
+
+#define CU(call)                                                                             \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? FR_ENOMEM : FR_ECUDA, "%s: %s", \
+                        #call, cudaGetErrorString(e_));                                      \
+    } while (0)
+
+// Orders the library stream after the caller's stream (call entry) and back (call exit).
+struct Join {
+    fr_ctx* c;
+    explicit Join(fr_ctx* ctx) : c(ctx) {
+        cudaEventRecord(c->ev_in, c->user);
+        cudaStreamWaitEvent(c->s, c->ev_in, 0);
+    }
+    ~Join() {
+        cudaEventRecord(c->ev_out, c->s);
+        cudaStreamWaitEvent(c->user, c->ev_out, 0);
+    }
+};
+
+P1Args p1_args(fr_ctx* c) {
+    P1Args a{};
+    a.U = c->U; a.I = c->I; a.K = c->K; a.nc = c->nc; a.ld = c->ld;
+    a.L = c->cfg.sinkhorn_iters; a.G = c->G;
+    a.C = c->C; a.m1 = c->m1; a.m2 = c->m2; a.gL = c->gL; a.gP = c->gP;
+    a.r = c->r; a.e = c->e; a.log2b = c->log2b; a.omega = c->omega;
+    a.part = c->part; a.gn2_part = c->gn2_part; a.st = c->st;
+    a.inv_eps_ln2 = (float)(1.0 / (c->cfg.epsilon * std::log(2.0)));
+    a.inv_eps = (float)(1.0 / c->cfg.epsilon);
+    a.lr = (float)c->cfg.lr; a.beta1 = (float)c->cfg.beta1; a.beta2 = (float)c->cfg.beta2;
+    a.adam_eps = (float)c->cfg.adam_eps;
+    a.optimizer = c->cfg.optimizer == FR_SGD ? 1 : 0;
+    a.warm = c->cfg.warm_start ? 1 : 0;
+    return a;
+}
+
+ReduceArgs red_args(fr_ctx* c, int after_update) {
+    ReduceArgs a{};
+    a.I = c->I; a.ld = c->ld; a.G = c->G; a.U = c->U;
+    a.part = c->part; a.gn2_part = c->gn2_part; a.imp = c->imp; a.omega = c->omega;
+    a.blk = c->blk; a.st = c->st; a.F_hist = c->F_hist; a.gn_hist = c->gn_hist;
+    a.hist_cap = c->hist_cap; a.after_update = after_update;
+    return a;
+}
+
+fr_status launch_one_step(fr_ctx* ctx) {
+    CU(p1_launch(ctx->var, MODE_UPDATE_SWEEP, p1_args(ctx), ctx->s));
+    CU(reduce_launch(red_args(ctx, 1), ctx->s));
+    ctx->launches += 2;
+    return FR_OK;
+}
+
+fr_status ensure_fresh(fr_ctx* ctx) {
+    if (!ctx->have_r || !ctx->have_e)
+        return fail(ctx, FR_ESTATE, "set relevance and exposure first");
+    if (ctx->fresh) return FR_OK;
+    CU(p1_launch(ctx->var, MODE_SWEEP, p1_args(ctx), ctx->s));
+    CU(reduce_launch(red_args(ctx, 0), ctx->s));
+    ctx->launches += 2;
+    ctx->fresh = true;
+    return FR_OK;
+}
+
+fr_status ensure_hist(fr_ctx* ctx, int n) {
+    if (n <= ctx->hist_cap) return FR_OK;
+    int cap = ctx->hist_cap > 0 ? ctx->hist_cap : 64;
+    while (cap < n) cap *= 2;
+    CU(cudaStreamSynchronize(ctx->s));
+    cudaFree(ctx->F_hist);
+    cudaFree(ctx->gn_hist);
+    ctx->F_hist = ctx->gn_hist = nullptr;
+    CU(cudaMalloc(&ctx->F_hist, sizeof(double) * cap));
+    CU(cudaMalloc(&ctx->gn_hist, sizeof(double) * cap));
+    ctx->hist_cap = cap;
+    if (ctx->chunk_exec) {  // kernel arguments changed: recapture
+        cudaGraphExecDestroy(ctx->chunk_exec);
+        ctx->chunk_exec = nullptr;
+    }
+    return FR_OK;
+}
+
+fr_status ensure_graph(fr_ctx* ctx) {
+    if (ctx->chunk_exec) return FR_OK;
+    cudaGraph_t g;
+    CU(cudaStreamBeginCapture(ctx->s, cudaStreamCaptureModeThreadLocal));
+    const int64_t before = ctx->launches;
+    for (int j = 0; j < kChunk; ++j) {
+        fr_status st = launch_one_step(ctx);
+        if (st != FR_OK) {
+            cudaStreamEndCapture(ctx->s, &g);
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+    }
+    ctx->launches = before;  // captured, not launched
+    CU(cudaStreamEndCapture(ctx->s, &g));
+    cudaError_t e = cudaGraphInstantiate(&ctx->chunk_exec, g, 0);
+    cudaGraphDestroy(g);
+    CU(e);
+    return FR_OK;
+}
+
+// Writes selected host-side fields of the device step state.
+fr_status set_run_state(fr_ctx* ctx, double thresh) {
+    DevState* h = ctx->st_host;
+    CU(cudaMemcpyAsync(h, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->s));
+    CU(cudaStreamSynchronize(ctx->s));
+    h->hist_idx = 0;
+    h->stop = 0;
+    h->steps_done = 0;
+    h->thresh = thresh;
+    CU(cudaMemcpyAsync(ctx->st, h, sizeof(DevState), cudaMemcpyHostToDevice, ctx->s));
+    return FR_OK;
+}
+
+fr_status read_state(fr_ctx* ctx) {
+    CU(cudaMemcpyAsync(ctx->st_host, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->s));
+    CU(cudaStreamSynchronize(ctx->s));
+    if (ctx->st_host->err)
+        return fail(ctx, FR_ENUMERIC, "non-finite or non-positive impact (flags %d)",
+                    ctx->st_host->err);
+    return FR_OK;
+}
+
+// Runs n steps: whole chunks by graph replay, the remainder by direct launches.
+fr_status run_steps(fr_ctx* ctx, int n, bool check_stop) {
+    int done = 0;
+    if (n >= kChunk) {
+        fr_status st = ensure_graph(ctx);
+        if (st != FR_OK) return st;
+    }
+    while (n - done >= kChunk) {
+        CU(cudaGraphLaunch(ctx->chunk_exec, ctx->s));
+        ctx->launches += 2 * kChunk;
+        done += kChunk;
+        if (check_stop) {
+            fr_status st = read_state(ctx);
+            if (st != FR_OK) return st;
+            if (ctx->st_host->stop) return FR_OK;
+        }
+    }
+    for (; done < n; ++done) {
+        fr_status st = launch_one_step(ctx);
+        if (st != FR_OK) return st;
+    }
+    return FR_OK;
+}
+
+fr_status ensure_tmp(fr_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->tmp_bytes) return FR_OK;
+    CU(cudaStreamSynchronize(ctx->s));
+    cudaFree(ctx->tmp);
+    ctx->tmp = nullptr;
+    ctx->tmp_bytes = 0;
+    CU(cudaMalloc(&ctx->tmp, bytes));
+    ctx->tmp_bytes = bytes;
+    return FR_OK;
+}
+
+void free_all(fr_ctx* c) {
+    if (c->chunk_exec) cudaGraphExecDestroy(c->chunk_exec);
+    float* fs[] = {c->C, c->m1, c->m2, c->gL, c->gP, c->r, c->e, c->log2b, c->omega, c->part, c->tmp};
+    for (float* p : fs) cudaFree(p);
+    double* ds[] = {c->gn2_part, c->imp, c->blk, c->F_hist, c->gn_hist};
+    for (double* p : ds) cudaFree(p);
+    cudaFree(c->st);
+    cudaFree(c->flags);
+    if (c->st_host) cudaFreeHost(c->st_host);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->s) cudaStreamDestroy(c->s);
+}
+
+fr_status zero_state(fr_ctx* ctx) {
+    const size_t cells = (size_t)ctx->U * ctx->nc * ctx->ld;
+    CU(cudaMemsetAsync(ctx->C, 0, sizeof(float) * cells, ctx->s));
+    CU(cudaMemsetAsync(ctx->m1, 0, sizeof(float) * cells, ctx->s));
+    CU(cudaMemsetAsync(ctx->m2, 0, sizeof(float) * cells, ctx->s));
+    CU(cudaMemsetAsync(ctx->gL, 0, sizeof(float) * ctx->U * ctx->nc, ctx->s));
+    CU(cudaMemsetAsync(ctx->gP, 0, sizeof(float) * ctx->U * ctx->nc, ctx->s));
+    DevState z{};
+    z.thresh = -1.0;
+    *ctx->st_host = z;
+    CU(cudaMemcpyAsync(ctx->st, ctx->st_host, sizeof(DevState), cudaMemcpyHostToDevice, ctx->s));
+    CU(cudaStreamSynchronize(ctx->s));
+    ctx->fresh = false;
+    return FR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fr_config_default(fr_config* cfg, int32_t n_users, int32_t n_items, int32_t n_slots,
+                       int32_t param) {
+    std::memset(cfg, 0, sizeof *cfg);
+    cfg->n_users = n_users;
+    cfg->n_items = n_items;
+    cfg->n_slots = n_slots;
+    cfg->param = param;
+    cfg->epsilon = 1.0;
+    cfg->sinkhorn_iters = 50;
+    cfg->warm_start = 1;
+    cfg->grad_mode = FR_GRAD_IMPLICIT;
+    cfg->ckpt_every = 10;
+    cfg->optimizer = FR_ADAM;
+    cfg->lr = param == FR_PARAM_ITEM ? 0.05 : 0.1;
+    cfg->beta1 = 0.9;
+    cfg->beta2 = 0.999;
+    cfg->adam_eps = 1e-8;
+    cfg->rel_dtype = FR_F32;
+}
+
+int32_t fr_num_cols(int32_t n_items, int32_t n_slots) {
+    return n_items > n_slots ? n_slots + 1 : n_slots;
+}
+
+fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
+    fr_ctx* ctx = nullptr;
+    if (!out) return fail(nullptr, FR_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(nullptr, FR_EINVAL, "cfg is NULL");
+    const fr_config& c = *cfg;
+    if (c.n_users < 1 || c.n_items < 1 || c.n_slots < 1 || c.n_slots > c.n_items)
+        return fail(nullptr, FR_EINVAL, "need n_users >= 1 and 1 <= n_slots <= n_items (got %d, %d, %d)",
+                    c.n_users, c.n_items, c.n_slots);
+    if (!(c.epsilon > 0.0) || !std::isfinite(c.epsilon))
+        return fail(nullptr, FR_EINVAL, "epsilon must be positive and finite");
+    if (c.sinkhorn_iters < 1) return fail(nullptr, FR_EINVAL, "sinkhorn_iters must be >= 1");
+    if (!(c.lr > 0.0) || !(c.beta1 >= 0.0 && c.beta1 < 1.0) || !(c.beta2 >= 0.0 && c.beta2 < 1.0) ||
+        !(c.adam_eps >= 0.0))
+        return fail(nullptr, FR_EINVAL, "invalid optimiser hyper-parameters");
+    if (c.optimizer != FR_ADAM && c.optimizer != FR_SGD)
+        return fail(nullptr, FR_EINVAL, "unknown optimizer %d", c.optimizer);
+    if (c.param != FR_PARAM_FULL_C)
+        return fail(nullptr, FR_EUNSUPPORTED, "only FR_PARAM_FULL_C is compiled in this build");
+    if (c.grad_mode != FR_GRAD_IMPLICIT)
+        return fail(nullptr, FR_EUNSUPPORTED, "FR_PARAM_FULL_C supports the implicit gradient only");
+    if (c.rel_dtype != FR_F32)
+        return fail(nullptr, FR_EUNSUPPORTED, "FR_PARAM_FULL_C stores relevance in FP32");
+    for (int j = 0; j < 7; ++j)
+        if (c.reserved[j]) return fail(nullptr, FR_EINVAL, "reserved fields must be zero");
+
+    const int nc = fr_num_cols(c.n_items, c.n_slots);
+    P1Variant var;
+    if (!p1_select(nc, c.n_items, &var))
+        return fail(nullptr, FR_EUNSUPPORTED,
+                    "FR_PARAM_FULL_C needs n_cols <= 64 and n_items <= 512 * rows per thread "
+                    "(2048 for n_cols <= 16, 1024 for <= 32, 512 for <= 64); got n_cols %d, n_items %d",
+                    nc, c.n_items);
+    ctx = new fr_ctx();
+    ctx->cfg = c;
+    ctx->U = c.n_users;
+    ctx->I = c.n_items;
+    ctx->K = c.n_slots;
+    ctx->nc = nc;
+    ctx->ld = (c.n_items + 7) / 8 * 8;
+    ctx->var = var;
+    ctx->user = (cudaStream_t)stream;
+    auto bail = [&](fr_status st) {
+        g_create_error = ctx->err;
+        free_all(ctx);
+        delete ctx;
+        return st;
+    };
+#define CUC(call)                                                                             \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return bail(fail(ctx, e_ == cudaErrorMemoryAllocation ? FR_ENOMEM : FR_ECUDA,     \
+                             "%s: %s", #call, cudaGetErrorString(e_)));                       \
+    } while (0)
+    CUC(cudaGetDevice(&ctx->device));
+    CUC(cudaStreamCreateWithFlags(&ctx->s, cudaStreamNonBlocking));
+    CUC(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
+    CUC(cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming));
+
+    // shared memory and occupancy of the fused update+sweep kernel fix the persistent grid
+    int max_optin = 0, sms = 0;
+    CUC(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    CUC(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    size_t smem_max = 0;
+    for (int m = 0; m < 3; ++m) {
+        size_t b = p1_smem_bytes(var, m, nc, ctx->ld);
+        if (b > (size_t)max_optin)
+            return bail(fail(ctx, FR_EUNSUPPORTED,
+                             "shared memory %zu B exceeds the device limit %d B (n_items * n_cols too large)",
+                             b, max_optin));
+        CUC(cudaFuncSetAttribute(var.fn[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
+        smem_max = b > smem_max ? b : smem_max;
+    }
+    int occ = 0;
+    CUC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, var.fn[MODE_UPDATE_SWEEP], var.threads,
+        p1_smem_bytes(var, MODE_UPDATE_SWEEP, nc, ctx->ld)));
+    if (occ < 1) return bail(fail(ctx, FR_EUNSUPPORTED, "kernel does not fit on an SM"));
+    ctx->G = std::min(ctx->U, occ * sms);
+    ctx->nblk = reduce_blocks(ctx->I);
+
+    const size_t cells = (size_t)ctx->U * nc * ctx->ld;
+    CUC(cudaMalloc(&ctx->C, sizeof(float) * cells));
+    CUC(cudaMalloc(&ctx->m1, sizeof(float) * cells));
+    CUC(cudaMalloc(&ctx->m2, sizeof(float) * cells));
+    CUC(cudaMalloc(&ctx->gL, sizeof(float) * ctx->U * nc));
+    CUC(cudaMalloc(&ctx->gP, sizeof(float) * ctx->U * nc));
+    CUC(cudaMalloc(&ctx->r, sizeof(float) * (size_t)ctx->U * ctx->ld));
+    CUC(cudaMemset(ctx->r, 0, sizeof(float) * (size_t)ctx->U * ctx->ld));
+    CUC(cudaMalloc(&ctx->e, sizeof(float) * nc));
+    CUC(cudaMalloc(&ctx->log2b, sizeof(float) * nc));
+    CUC(cudaMalloc(&ctx->omega, sizeof(float) * ctx->ld));
+    CUC(cudaMalloc(&ctx->part, sizeof(float) * (size_t)ctx->G * ctx->ld));
+    CUC(cudaMalloc(&ctx->gn2_part, sizeof(double) * ctx->G));
+    CUC(cudaMalloc(&ctx->imp, sizeof(double) * ctx->ld));
+    CUC(cudaMalloc(&ctx->blk, sizeof(double) * 2 * ctx->nblk));
+    CUC(cudaMalloc(&ctx->st, sizeof(DevState)));
+    CUC(cudaMalloc(&ctx->flags, sizeof(int) * 4));
+    CUC(cudaMallocHost(&ctx->st_host, sizeof(DevState)));
+#undef CUC
+    fr_status st = zero_state(ctx);
+    if (st != FR_OK) return bail(st);
+    st = ensure_hist(ctx, 64);
+    if (st != FR_OK) return bail(st);
+    *out = ctx;
+    return FR_OK;
+}
+
+fr_status fr_destroy(fr_ctx* ctx) {
+    if (!ctx) return FR_OK;
+    cudaStreamSynchronize(ctx->s);
+    free_all(ctx);
+    delete ctx;
+    return FR_OK;
+}
+
+fr_status fr_reset(fr_ctx* ctx) {
+    if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
+    Join j(ctx);
+    return zero_state(ctx);
+}
+
+fr_status fr_set_relevance(fr_ctx* ctx, const void* r, int32_t dtype, int64_t ld, int32_t on_device) {
+    if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
+    if (!r) return fail(ctx, FR_EINVAL, "r is NULL");
+    if (dtype != FR_F32 && dtype != FR_F64 && dtype != FR_BF16)
+        return fail(ctx, FR_EINVAL, "unknown dtype %d", dtype);
+    if (ld < ctx->I) return fail(ctx, FR_EINVAL, "ld %lld < n_items %d", (long long)ld, ctx->I);
+    Join j(ctx);
+    const size_t esz = dtype == FR_F64 ? 8 : dtype == FR_F32 ? 4 : 2;
+    const void* src = r;
+    int64_t lds = ld;
+    if (!on_device) {
+        fr_status st = ensure_tmp(ctx, esz * (size_t)ctx->U * ctx->I);
+        if (st != FR_OK) return st;
+        CU(cudaMemcpy2DAsync(ctx->tmp, esz * ctx->I, r, esz * ld, esz * ctx->I, ctx->U,
+                             cudaMemcpyHostToDevice, ctx->s));
+        src = ctx->tmp;
+        lds = ctx->I;
+    }
+    CU(launch_relevance_import(src, dtype, lds, ctx->r, ctx->U, ctx->I, ctx->ld, ctx->s));
+    CU(cudaMemsetAsync(ctx->flags, 0, sizeof(int) * 4, ctx->s));
+    CU(launch_relevance_check(ctx->r, ctx->U, ctx->I, ctx->ld, ctx->flags, ctx->s));
+    ctx->launches += 2;
+    int hf[4];
+    CU(cudaMemcpyAsync(hf, ctx->flags, sizeof hf, cudaMemcpyDeviceToHost, ctx->s));
+    CU(cudaStreamSynchronize(ctx->s));
+    if (hf[0]) return fail(ctx, FR_EINVAL, "relevance must be finite and >= 0");
+    if (hf[1]) return fail(ctx, FR_EINVAL, "%d items have no positive relevance (log Imp_i undefined)", hf[1]);
+    ctx->have_r = true;
+    ctx->fresh = false;
+    return FR_OK;
+}
+
+fr_status fr_set_exposure(fr_ctx* ctx, const double* e, int32_t K) {
+    if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
+    if (!e) return fail(ctx, FR_EINVAL, "e is NULL");
+    if (K != ctx->K) return fail(ctx, FR_EINVAL, "K %d != n_slots %d", K, ctx->K);
+    std::vector<float> ep(ctx->nc, 0.f), lb(ctx->nc, 0.f);
+    for (int k = 0; k < K; ++k) {
+        if (!(e[k] > 0.0) || !std::isfinite(e[k]))
+            return fail(ctx, FR_EINVAL, "exposure e[%d] must be positive and finite", k);
+        ep[k] = (float)e[k];
+    }
+    if (ctx->nc > K) lb[K] = (float)std::log2((double)(ctx->I - K));  // dummy mass |I| - K
+    Join j(ctx);
+    CU(cudaMemcpyAsync(ctx->e, ep.data(), sizeof(float) * ctx->nc, cudaMemcpyHostToDevice, ctx->s));
+    CU(cudaMemcpyAsync(ctx->log2b, lb.data(), sizeof(float) * ctx->nc, cudaMemcpyHostToDevice, ctx->s));
+    CU(cudaStreamSynchronize(ctx->s));
+    ctx->have_e = true;
+    ctx->fresh = false;
+    return FR_OK;
+}
+
+fr_status fr_step(fr_ctx* ctx, int32_t n_steps, double* nsw_trace) {
+    if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
+    if (n_steps < 0) return fail(ctx, FR_EINVAL, "n_steps < 0");
+    Join j(ctx);
+    fr_status st = ensure_fresh(ctx);
+    if (st != FR_OK) return st;
+    if ((st = ensure_hist(ctx, n_steps)) != FR_OK) return st;
+    if ((st = set_run_state(ctx, -1.0)) != FR_OK) return st;
+    if ((st = run_steps(ctx, n_steps, false)) != FR_OK) return st;
+    if ((st = read_state(ctx)) != FR_OK) return st;
+    if (nsw_trace && n_steps > 0) {
+        CU(cudaMemcpyAsync(nsw_trace, ctx->F_hist, sizeof(double) * n_steps, cudaMemcpyDeviceToHost,
+                           ctx->s));
+        CU(cudaStreamSynchronize(ctx->s));
+    }
+    return FR_OK;
+}
+
+fr_status fr_solve(fr_ctx* ctx, double t, int32_t max_steps, int32_t* steps_done, double* nsw_out) {
+    if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
+    if (max_steps < 0 || !(t >= 0.0)) return fail(ctx, FR_EINVAL, "need max_steps >= 0 and t >= 0");
+    Join j(ctx);
+    fr_status st = ensure_fresh(ctx);
+    if (st != FR_OK) return st;
+    if ((st = ensure_hist(ctx, max_steps)) != FR_OK) return st;
+    if ((st = set_run_state(ctx, t)) != FR_OK) return st;
+    if ((st = run_steps(ctx, max_steps, true)) != FR_OK) return st;
+    if ((st = read_state(ctx)) != FR_OK) return st;
+    if (steps_done) *steps_done = ctx->st_host->steps_done;
+    if (nsw_out) *nsw_out = ctx->st_host->F;
+    return set_run_state(ctx, -1.0);
+}
+
+fr_status fr_impacts(fr_ctx* ctx, double* imp_out, double* utility_out, double* nsw_out) {
+    if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
+    Join j(ctx);
+    fr_status st = ensure_fresh(ctx);
+    if (st != FR_OK) return st;
+    if (imp_out)
+        CU(cudaMemcpyAsync(imp_out, ctx->imp, sizeof(double) * ctx->I, cudaMemcpyDeviceToHost, ctx->s));
+    if ((st = read_state(ctx)) != FR_OK) return st;
+    if (utility_out) *utility_out = ctx->st_host->utility;
+    if (nsw_out) *nsw_out = ctx->st_host->F;
+    return FR_OK;
+}
+
+fr_status fr_policy(fr_ctx* ctx, int32_t u0, int32_t n_u, float* x_out, int32_t on_device) {
+    if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
+    if (u0 < 0 || n_u < 0 || (int64_t)u0 + n_u > ctx->U)
+        return fail(ctx, FR_EINVAL, "consumer range [%d, %d) outside [0, %d)", u0, u0 + n_u, ctx->U);
+    if (!x_out && n_u > 0) return fail(ctx, FR_EINVAL, "x_out is NULL");
+    Join j(ctx);
+    fr_status st = ensure_fresh(ctx);
+    if (st != FR_OK) return st;
+    const size_t bytes = sizeof(float) * (size_t)n_u * ctx->I * ctx->nc;
+    float* dst = x_out;
+    if (!on_device) {
+        if ((st = ensure_tmp(ctx, bytes)) != FR_OK) return st;
+        dst = ctx->tmp;
+    }
+    CU(launch_policy(p1_args(ctx), u0, n_u, dst, ctx->s));
+    ctx->launches += n_u > 0;
+    if (!on_device && n_u > 0) {
+        CU(cudaMemcpyAsync(x_out, dst, bytes, cudaMemcpyDeviceToHost, ctx->s));
+    }
+    CU(cudaStreamSynchronize(ctx->s));
+    return FR_OK;
+}
+
+fr_status fr_grad(fr_ctx* ctx, const float* omega, float* dparam, float* dr, int32_t on_device) {
+    if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
+    if (!dparam) return fail(ctx, FR_EINVAL, "dparam is NULL");
+    Join j(ctx);
+    fr_status st = ensure_fresh(ctx);
+    if (st != FR_OK) return st;
+    const size_t nC = (size_t)ctx->U * ctx->I * ctx->nc, nr = (size_t)ctx->U * ctx->I;
+    // staging: [omega (ld) | dC (nC) | dr (nr)]
+    const size_t need = sizeof(float) * (ctx->ld + (on_device ? 0 : nC + nr));
+    if ((st = ensure_tmp(ctx, need)) != FR_OK) return st;
+    P1Args a = p1_args(ctx);
+    if (omega) {
+        CU(cudaMemsetAsync(ctx->tmp, 0, sizeof(float) * ctx->ld, ctx->s));
+        CU(cudaMemcpyAsync(ctx->tmp, omega, sizeof(float) * ctx->I,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->s));
+        a.omega = ctx->tmp;
+    }
+    a.dC = on_device ? dparam : ctx->tmp + ctx->ld;
+    a.dr = dr ? (on_device ? dr : ctx->tmp + ctx->ld + nC) : nullptr;
+    CU(p1_launch(ctx->var, MODE_GRAD, a, ctx->s));
+    ctx->launches += 1;
+    if (!on_device) {
+        CU(cudaMemcpyAsync(dparam, a.dC, sizeof(float) * nC, cudaMemcpyDeviceToHost, ctx->s));
+        if (dr) CU(cudaMemcpyAsync(dr, a.dr, sizeof(float) * nr, cudaMemcpyDeviceToHost, ctx->s));
+    }
+    CU(cudaStreamSynchronize(ctx->s));
+    return FR_OK;
+}
+
+fr_status fr_set_state(fr_ctx* ctx, const float* param, const float* m1, const float* m2,
+                       const float* g, int64_t t, int32_t on_device) {
+    if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
+    if (t < 0) return fail(ctx, FR_EINVAL, "t < 0");
+    Join j(ctx);
+    const size_t nC = (size_t)ctx->U * ctx->I * ctx->nc;
+    const float* srcs[3] = {param, m1, m2};
+    float* dsts[3] = {ctx->C, ctx->m1, ctx->m2};
+    fr_status st = ensure_tmp(ctx, sizeof(float) * nC);
+    if (st != FR_OK) return st;
+    for (int q = 0; q < 3; ++q) {
+        if (!srcs[q]) continue;
+        const float* src = srcs[q];
+        if (!on_device) {
+            CU(cudaMemcpyAsync(ctx->tmp, src, sizeof(float) * nC, cudaMemcpyHostToDevice, ctx->s));
+            src = ctx->tmp;
+        }
+        CU(launch_pack_ikn_to_kni(src, dsts[q], ctx->U, ctx->I, ctx->nc, ctx->ld, 1.f, ctx->s));
+        ctx->launches += 1;
+    }
+    if (g) {
+        const float* src = g;
+        if (!on_device) {
+            CU(cudaMemcpyAsync(ctx->tmp, g, sizeof(float) * ctx->U * ctx->nc, cudaMemcpyHostToDevice,
+                               ctx->s));
+            src = ctx->tmp;
+        }
+        CU(launch_scale(src, ctx->gL, (long long)ctx->U * ctx->nc,
+                        (float)(1.0 / (ctx->cfg.epsilon * std::log(2.0))), ctx->s));
+        ctx->launches += 1;
+    }
+    CU(cudaMemcpyAsync(ctx->st_host, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->s));
+    CU(cudaStreamSynchronize(ctx->s));
+    ctx->st_host->t = t;
+    CU(cudaMemcpyAsync(ctx->st, ctx->st_host, sizeof(DevState), cudaMemcpyHostToDevice, ctx->s));
+    CU(cudaStreamSynchronize(ctx->s));
+    ctx->fresh = false;
+    return FR_OK;
+}
+
+fr_status fr_get_state(fr_ctx* ctx, float* param, float* m1, float* m2, float* g, int64_t* t,
+                       int32_t on_device) {
+    if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
+    Join j(ctx);
+    const size_t nC = (size_t)ctx->U * ctx->I * ctx->nc;
+    float* dsts[3] = {param, m1, m2};
+    const float* srcs[3] = {ctx->C, ctx->m1, ctx->m2};
+    fr_status st = ensure_tmp(ctx, sizeof(float) * nC);
+    if (st != FR_OK) return st;
+    for (int q = 0; q < 3; ++q) {
+        if (!dsts[q]) continue;
+        float* dst = on_device ? dsts[q] : ctx->tmp;
+        CU(launch_unpack_kni_to_ikn(srcs[q], dst, ctx->U, ctx->I, ctx->nc, ctx->ld, 1.f, ctx->s));
+        ctx->launches += 1;
+        if (!on_device) {
+            CU(cudaMemcpyAsync(dsts[q], dst, sizeof(float) * nC, cudaMemcpyDeviceToHost, ctx->s));
+            CU(cudaStreamSynchronize(ctx->s));
+        }
+    }
+    if (g) {
+        float* dst = on_device ? g : ctx->tmp;
+        CU(launch_scale(ctx->gL, dst, (long long)ctx->U * ctx->nc,
+                        (float)(ctx->cfg.epsilon * std::log(2.0)), ctx->s));
+        ctx->launches += 1;
+        if (!on_device)
+            CU(cudaMemcpyAsync(g, dst, sizeof(float) * ctx->U * ctx->nc, cudaMemcpyDeviceToHost, ctx->s));
+    }
+    CU(cudaMemcpyAsync(ctx->st_host, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->s));
+    CU(cudaStreamSynchronize(ctx->s));
+    if (t) *t = ctx->st_host->t;
+    return FR_OK;
+}
+
+fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* better_pct,
+                     double* worse_pct) {
+    (void)utility; (void)mean_envy; (void)better_pct; (void)worse_pct;
+    if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
+    return fail(ctx, FR_EUNSUPPORTED, "evaluation metrics are not built yet");
+}
+
+fr_status fr_time_kernels(fr_ctx* ctx, int32_t n_steps, double* ms) {
+    if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
+    if (n_steps < 1 || !ms) return fail(ctx, FR_EINVAL, "need n_steps >= 1 and ms");
+    Join j(ctx);
+    fr_status st = ensure_fresh(ctx);
+    if (st != FR_OK) return st;
+    if ((st = set_run_state(ctx, -1.0)) != FR_OK) return st;
+    cudaEvent_t ev[3];
+    for (auto& e : ev) CU(cudaEventCreate(&e));
+    double acc[2] = {0.0, 0.0};
+    const P1Args pa = p1_args(ctx);
+    const ReduceArgs ra = red_args(ctx, 1);
+    for (int s = 0; s < n_steps; ++s) {
+        CU(cudaEventRecord(ev[0], ctx->s));
+        CU(p1_launch(ctx->var, MODE_UPDATE_SWEEP, pa, ctx->s));
+        CU(cudaEventRecord(ev[1], ctx->s));
+        CU(reduce_launch(ra, ctx->s));
+        CU(cudaEventRecord(ev[2], ctx->s));
+        ctx->launches += 2;
+        CU(cudaEventSynchronize(ev[2]));
+        float a = 0.f, b = 0.f;
+        CU(cudaEventElapsedTime(&a, ev[0], ev[1]));
+        CU(cudaEventElapsedTime(&b, ev[1], ev[2]));
+        acc[0] += a;
+        acc[1] += b;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    ms[0] = acc[0] / n_steps;
+    ms[1] = acc[1] / n_steps;
+    return read_state(ctx);
+}
+
+const char* fr_last_error(const fr_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+int64_t fr_launch_count(const fr_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+fr_status fr_measure_ex2_rate(double* ex2_per_second) {
+    fr_ctx* ctx = nullptr;
+    if (!ex2_per_second) return fail(nullptr, FR_EINVAL, "output is NULL");
+    int dev = 0, sms = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    float* sink = nullptr;
+    CU(cudaMalloc(&sink, sizeof(float) * sms * 8));
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const int blocks = sms * 8, threads = 256, iters = 4096;
+    launch_ex2_bench(sink, blocks, threads, 64, nullptr);  // warm-up
+    cudaEventRecord(a);
+    launch_ex2_bench(sink, blocks, threads, iters, nullptr);
+    cudaEventRecord(b);
+    cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(sink);
+    CU(e);
+    *ex2_per_second = (double)blocks * threads * iters * 8.0 / (ms * 1e-3);
+    return FR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,249 @@
+// fr_common.cu -- the cross-consumer impact reduction and the support kernels of libfairrank.
+#include <cuda_bf16.h>
+
+#include "fr_device.cuh"
+#include "fr_internal.h"
+
+namespace fr {
+
+namespace {
+
+constexpr int RED_ITEMS = 32;  // items per CTA (one per lane)
+constexpr int RED_WARPS = 8;   // warps splitting the per-CTA partials
+
+// Eq. (4) across consumers and Eq. (5): Imp_i = sum over the sweep CTAs' partials (fixed order,
+// FP64), omega_i = 1/Imp_i for the next gradient, F = sum_i log Imp_i in FP64. The last CTA to
+// finish (atomic ticket) combines the per-CTA partial sums of log Imp_i, of Imp_i (utility,
+// Sec. 4.1) and of the squared gradient norm in a fixed order, updates the step state and, for
+// fr_solve, raises the stop flag once the step's gradient norm is <= the threshold.
+__global__ void __launch_bounds__(RED_ITEMS* RED_WARPS) reduce_kernel(const ReduceArgs a) {
+    __shared__ double s_sum[RED_WARPS][RED_ITEMS];
+    __shared__ int s_last;
+    if (a.st->stop) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int item = blockIdx.x * RED_ITEMS + lane;
+    double acc = 0.0;
+    if (item < a.I)
+        for (int g = warp; g < a.G; g += RED_WARPS) acc += (double)a.part[(size_t)g * a.ld + item];
+    s_sum[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < RED_WARPS; ++w) tot += s_sum[w][lane];
+        double lg = 0.0, im = 0.0;
+        if (item < a.I) {
+            a.imp[item] = tot;
+            a.omega[item] = (float)(1.0 / tot);
+            if (!(tot > 0.0) || !isfinite(tot)) atomicOr(&a.st->err, 1);
+            lg = log(tot);
+            im = tot;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lg += __shfl_xor_sync(FULL, lg, o);
+            im += __shfl_xor_sync(FULL, im, o);
+        }
+        if (lane == 0) {
+            a.blk[2 * blockIdx.x] = lg;
+            a.blk[2 * blockIdx.x + 1] = im;
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&a.st->counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last || warp != 0) return;
+    __threadfence();
+    double F = 0.0, S = 0.0, g2 = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) {
+        F += __ldcg(a.blk + 2 * b);
+        S += __ldcg(a.blk + 2 * b + 1);
+    }
+    if (a.after_update)
+        for (int g = lane; g < a.G; g += 32) g2 += __ldcg(a.gn2_part + g);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        F += __shfl_xor_sync(FULL, F, o);
+        S += __shfl_xor_sync(FULL, S, o);
+        g2 += __shfl_xor_sync(FULL, g2, o);
+    }
+    if (lane == 0) {
+        DevState* st = a.st;
+        st->F = F;
+        st->utility = S / a.U;
+        if (!isfinite(F)) st->err |= 1;
+        if (a.after_update) {
+            const double gn = sqrt(g2);
+            if (!isfinite(gn)) st->err |= 2;
+            st->gnorm = gn;
+            st->t += 1;
+            st->steps_done += 1;
+            const int h = st->hist_idx;
+            if (h < a.hist_cap) {
+                a.F_hist[h] = F;
+                a.gn_hist[h] = gn;
+            }
+            st->hist_idx = h + 1;
+            if (st->thresh >= 0.0 && gn <= st->thresh) st->stop = 1;
+        }
+        st->counter = 0u;
+    }
+}
+
+// [U][I][nc] -> [U][nc][ld] (padding rows zero), times scale
+__global__ void pack_kernel(const float* __restrict__ src, float* __restrict__ dst, int U, int I,
+                            int nc, int ld, float scale) {
+    const long long n = (long long)U * nc * ld;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(j % ld);
+        const long long uk = j / ld;
+        const int k = (int)(uk % nc);
+        const long long u = uk / nc;
+        dst[j] = i < I ? src[(u * I + i) * nc + k] * scale : 0.f;
+    }
+}
+
+__global__ void unpack_kernel(const float* __restrict__ src, float* __restrict__ dst, int U, int I,
+                              int nc, int ld, float scale) {
+    const long long n = (long long)U * I * nc;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(j % nc);
+        const long long ui = j / nc;
+        const int i = (int)(ui % I);
+        const long long u = ui / I;
+        dst[j] = src[(u * nc + k) * ld + i] * scale;
+    }
+}
+
+__global__ void scale_kernel(const float* __restrict__ src, float* __restrict__ dst, long long n,
+                             float scale) {
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x)
+        dst[j] = src[j] * scale;
+}
+
+__global__ void relevance_import_kernel(const void* __restrict__ src, int dtype, long long ld_src,
+                                        float* __restrict__ dst, int U, int I, int ld) {
+    const long long n = (long long)U * ld;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
+         j += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(j % ld);
+        const long long u = j / ld;
+        float v = 0.f;
+        if (i < I) {
+            const long long o = u * ld_src + i;
+            if (dtype == FR_F32) v = static_cast<const float*>(src)[o];
+            else if (dtype == FR_F64) v = (float)static_cast<const double*>(src)[o];
+            else v = __bfloat162float(static_cast<const __nv_bfloat16*>(src)[o]);
+        }
+        dst[j] = v;
+    }
+}
+
+// flags[0] |= 1 for a negative or non-finite value; flags[1] counts items without positive r
+__global__ void relevance_check_kernel(const float* __restrict__ r, int U, int I, int ld,
+                                       int* flags) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= I) return;
+    bool bad = false, pos = false;
+    for (int u = 0; u < U; ++u) {
+        const float v = r[(size_t)u * ld + i];
+        bad |= !(v >= 0.f) || !isfinite(v);
+        pos |= v > 0.f;
+    }
+    if (bad) atomicOr(flags, 1);
+    if (!pos) atomicAdd(flags + 1, 1);
+}
+
+// Policy of consumers u0.. (one CTA each): x_ik = softmax_k(g^(L-1)'_k - c'_ik) in base 2, the
+// policy emitted by the last Sinkhorn row update; written in the public [u][i][k] layout.
+__global__ void policy_kernel(const P1Args a, int u0, float* __restrict__ x) {
+    const int u = u0 + blockIdx.x;
+    const int nc = a.nc;
+    const float* C = a.C + (size_t)u * nc * a.ld;
+    const float* gp = a.gP + (size_t)u * nc;
+    for (int i = threadIdx.x; i < a.I; i += blockDim.x) {
+        float M = -INFINITY;
+        for (int k = 0; k < nc; ++k) M = fmaxf(M, gp[k] - C[(size_t)k * a.ld + i] * a.inv_eps_ln2);
+        float S = 0.f;
+        for (int k = 0; k < nc; ++k) S += ex2(gp[k] - C[(size_t)k * a.ld + i] * a.inv_eps_ln2 - M);
+        const float inv = 1.f / S;
+        float* xo = x + ((size_t)blockIdx.x * a.I + i) * nc;
+        for (int k = 0; k < nc; ++k)
+            xo[k] = ex2(gp[k] - C[(size_t)k * a.ld + i] * a.inv_eps_ln2 - M) * inv;
+    }
+}
+
+// 8 independent chains x <- 2^(-x) per thread: MUFU-bound throughput probe
+__global__ void ex2_bench_kernel(float* sink, int iters) {
+    float x[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = 0.1f * j + 1e-3f * (threadIdx.x & 31);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = ex2(-x[j]);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s += x[j];
+    if (s == 12345.f) sink[blockIdx.x] = s;
+}
+
+int grid_for(long long n) {
+    long long b = (n + 255) / 256;
+    return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+}  // namespace
+
+int reduce_blocks(int I) { return (I + RED_ITEMS - 1) / RED_ITEMS; }
+
+cudaError_t reduce_launch(const ReduceArgs& a, cudaStream_t s) {
+    reduce_kernel<<<reduce_blocks(a.I), RED_ITEMS * RED_WARPS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_ikn_to_kni(const float* src, float* dst, int U, int I, int nc, int ld,
+                                   float scale, cudaStream_t s) {
+    pack_kernel<<<grid_for((long long)U * nc * ld), 256, 0, s>>>(src, dst, U, I, nc, ld, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_kni_to_ikn(const float* src, float* dst, int U, int I, int nc, int ld,
+                                     float scale, cudaStream_t s) {
+    unpack_kernel<<<grid_for((long long)U * I * nc), 256, 0, s>>>(src, dst, U, I, nc, ld, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale(const float* src, float* dst, long long n, float scale, cudaStream_t s) {
+    scale_kernel<<<grid_for(n), 256, 0, s>>>(src, dst, n, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relevance_import(const void* src, int dtype, long long ld_src, float* dst,
+                                    int U, int I, int ld, cudaStream_t s) {
+    relevance_import_kernel<<<grid_for((long long)U * ld), 256, 0, s>>>(src, dtype, ld_src, dst,
+                                                                         U, I, ld);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relevance_check(const float* r, int U, int I, int ld, int* flags,
+                                   cudaStream_t s) {
+    relevance_check_kernel<<<(I + 127) / 128, 128, 0, s>>>(r, U, I, ld, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_policy(const P1Args& a, int u0, int n_u, float* x_out, cudaStream_t s) {
+    if (n_u <= 0) return cudaSuccess;
+    policy_kernel<<<n_u, 256, 0, s>>>(a, u0, x_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ex2_bench(float* sink, int blocks, int threads, int iters, cudaStream_t s) {
+    ex2_bench_kernel<<<blocks, threads, 0, s>>>(sink, iters);
+    return cudaGetLastError();
+}
+
+}  // namespace fr

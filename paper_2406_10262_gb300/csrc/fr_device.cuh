@@ -1,0 +1,133 @@
+// fr_device.cuh -- small device helpers shared by the libfairrank kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fr {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// 2^x on the multi-function unit (one MUFU.EX2); flushes subnormal results to zero.
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// 1/x on the multi-function unit (relative error below 2^-22 over the normal range).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+constexpr int pow2ceil(int n) { return n <= 1 ? 1 : 2 * pow2ceil((n + 1) / 2); }
+
+// ---- vector loads/stores of R consecutive floats (R in {1,2,4,8}; 4R-byte aligned) ------------
+template <int R>
+__device__ __forceinline__ void ldv(float (&d)[R], const float* p) {
+    if constexpr (R == 1) {
+        d[0] = *p;
+    } else if constexpr (R == 2) {
+        float2 v = *reinterpret_cast<const float2*>(p);
+        d[0] = v.x; d[1] = v.y;
+    } else if constexpr (R == 4) {
+        float4 v = *reinterpret_cast<const float4*>(p);
+        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+    } else {
+        static_assert(R == 8, "R");
+        float4 v = reinterpret_cast<const float4*>(p)[0];
+        float4 w = reinterpret_cast<const float4*>(p)[1];
+        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+        d[4] = w.x; d[5] = w.y; d[6] = w.z; d[7] = w.w;
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void stv(float* p, const float (&d)[R]) {
+    if constexpr (R == 1) {
+        *p = d[0];
+    } else if constexpr (R == 2) {
+        *reinterpret_cast<float2*>(p) = make_float2(d[0], d[1]);
+    } else if constexpr (R == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(d[0], d[1], d[2], d[3]);
+    } else {
+        static_assert(R == 8, "R");
+        reinterpret_cast<float4*>(p)[0] = make_float4(d[0], d[1], d[2], d[3]);
+        reinterpret_cast<float4*>(p)[1] = make_float4(d[4], d[5], d[6], d[7]);
+    }
+}
+
+// ---- warp reduce-scatter ------------------------------------------------------------------
+// Each lane holds P values (P a power of two). After the call the lanes with owner == true hold,
+// in v[0 .. max(P/32,1)), the warp-wide sums of columns base, base+1, ...; every column has
+// exactly one owner. Costs P/2 + P/4 + ... shuffles instead of 5P for P separate butterflies.
+template <int n, int o>
+__device__ __forceinline__ void rs_level(float* v, int lane, int& base, bool& owner) {
+    if constexpr (n == 1) {  // one value left: plain butterfly, the lower lane owns the sum
+        v[0] += __shfl_xor_sync(FULL, v[0], o);
+        if (lane & o) owner = false;
+    } else {
+        constexpr int h = n / 2;
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < h; ++j) {
+            const float a = v[j], b = v[h + j];
+            const float send = hi ? a : b;
+            const float keep = hi ? b : a;
+            v[j] = keep + __shfl_xor_sync(FULL, send, o);
+        }
+        if (hi) base += h;
+    }
+}
+
+template <int P>
+__device__ __forceinline__ int warp_reduce_scatter(float* v, int lane, bool& owner) {
+    static_assert((P & (P - 1)) == 0, "power of two");
+    int base = 0;
+    owner = true;
+    constexpr int n0 = P, n1 = n0 > 1 ? n0 / 2 : 1, n2 = n1 > 1 ? n1 / 2 : 1,
+                  n3 = n2 > 1 ? n2 / 2 : 1, n4 = n3 > 1 ? n3 / 2 : 1;
+    rs_level<n0, 16>(v, lane, base, owner);
+    rs_level<n1, 8>(v, lane, base, owner);
+    rs_level<n2, 4>(v, lane, base, owner);
+    rs_level<n3, 2>(v, lane, base, owner);
+    rs_level<n4, 1>(v, lane, base, owner);
+    return base;
+}
+
+// Sum of NV per-thread vectors of length NCB over the whole CTA into out[j*ncp + k] (k < nc).
+// s_red needs (blockDim/32) * NV * pow2ceil(NCB) floats. Deterministic (fixed order). Contains two
+// __syncthreads; every thread of the CTA must call it.
+template <int NCB, int NV>
+__device__ __forceinline__ void cta_reduce(float (&v)[NV][NCB], int nc, float* s_red, float* out,
+                                           int ncp) {
+    constexpr int P = pow2ceil(NCB);
+    constexpr int PER = P >= 32 ? P / 32 : 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        float w[P];
+#pragma unroll
+        for (int k = 0; k < P; ++k) w[k] = k < NCB ? v[j][k] : 0.f;
+        bool owner;
+        const int base = warp_reduce_scatter<P>(w, lane, owner);
+        if (owner) {
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int k = base + q;
+                if (k < nc) s_red[(warp * NV + j) * P + k] = w[q];
+            }
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < NV * nc; idx += blockDim.x) {
+        const int j = idx / nc, k = idx - j * nc;
+        float s = 0.f;
+        for (int ww = 0; ww < W; ++ww) s += s_red[(ww * NV + j) * P + k];
+        out[j * ncp + k] = s;
+    }
+    __syncthreads();
+}
+
+}  // namespace fr

@@ -1,0 +1,103 @@
+// fr_internal.h -- structures shared by the libfairrank translation units (host + device).
+//
+// Device layout of one problem (all owned by the context):
+//   C, m1, m2   float [U][nc][ld]  costs and Adam moments, k-major per consumer so that a thread
+//                                  owning consecutive items i reads/writes them with coalesced
+//                                  vector accesses (ld = n_items rounded up to a multiple of 8,
+//                                  padding rows are zero and never enter any sum)
+//   r           float [U][ld]      relevance r(u,i)
+//   gL, gP      float [U][nc]      column potentials in log2 units, g' = g / (eps ln 2): gL is the
+//                                  last solve's g^(L) (the warm start), gP its g^(L-1) (the
+//                                  potentials the emitted policy was formed with)
+//   part        float [G][ld]      per-CTA partial impacts sum_u r(u,i) v(u,i) of the last sweep
+//   gn2_part    double [G]         per-CTA partial squared gradient norms
+//   imp         double [ld]        Imp_i (Eq. 4) after the cross-CTA reduction
+//   omega       float [ld]         dF/dImp_i = 1/Imp_i for the next gradient
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "fairrank.h"
+
+namespace fr {
+
+// Device-resident step state: read and written by the kernels so that captured CUDA graphs can
+// be replayed without changing kernel arguments.
+struct DevState {
+    long long t;          // Adam steps applied
+    int hist_idx;         // next slot of the F / gradient-norm history
+    int stop;             // set by the reduction when a step's gradient norm <= thresh
+    int err;              // bit 0: non-positive or non-finite impact; bit 1: non-finite gradient
+    int steps_done;       // steps applied since the host last cleared it
+    unsigned int counter; // last-block-done counter of the reduction (returns to 0)
+    int pad_;
+    double F, utility, gnorm;
+    double thresh;        // < 0: never stop
+};
+
+enum Mode { MODE_SWEEP = 0, MODE_UPDATE_SWEEP = 1, MODE_GRAD = 2 };
+
+struct P1Args {
+    int U, I, K, nc, ld, L, G;
+    float* C;
+    float* m1;
+    float* m2;
+    float* gL;
+    float* gP;
+    const float* r;
+    const float* e;       // [nc] exposure, dummy = 0
+    const float* log2b;   // [nc] log2 of the column marginals
+    const float* omega;   // [ld]
+    float* part;          // [G][ld]
+    double* gn2_part;     // [G]
+    DevState* st;
+    float* dC;            // MODE_GRAD: dF/dC, [U][I][nc] (public layout)
+    float* dr;            // MODE_GRAD: dF/dr, [U][I] (nullable)
+    float inv_eps_ln2;    // 1 / (eps ln 2)
+    float inv_eps;
+    float lr, beta1, beta2, adam_eps;
+    int optimizer;        // 0 Adam, 1 SGD
+    int warm;
+};
+
+struct ReduceArgs {
+    int I, ld, G, U;
+    const float* part;
+    const double* gn2_part;
+    double* imp;
+    float* omega;
+    double* blk;          // [nblocks][2] partial (sum log Imp, sum Imp)
+    DevState* st;
+    double* F_hist;
+    double* gn_hist;
+    int hist_cap;
+    int after_update;     // 1 if the sweep followed an optimiser update
+};
+
+// Launchers (return cudaError_t of the launch). `variant` is resolved by p1_select.
+struct P1Variant {
+    int ncb, rows, exact;
+    int threads;          // CTA size
+    size_t smem;          // dynamic shared memory (bytes) of the largest mode
+    const void* fn[3];    // kernels by Mode
+};
+
+bool p1_select(int nc, int I, P1Variant* out);
+cudaError_t p1_launch(const P1Variant& v, int mode, const P1Args& a, cudaStream_t s);
+size_t p1_smem_bytes(const P1Variant& v, int mode, int nc, int ld);
+cudaError_t reduce_launch(const ReduceArgs& a, cudaStream_t s);
+int reduce_blocks(int I);
+
+cudaError_t launch_pack_ikn_to_kni(const float* src, float* dst, int U, int I, int nc, int ld,
+                                   float scale, cudaStream_t s);
+cudaError_t launch_unpack_kni_to_ikn(const float* src, float* dst, int U, int I, int nc, int ld,
+                                     float scale, cudaStream_t s);
+cudaError_t launch_scale(const float* src, float* dst, long long n, float scale, cudaStream_t s);
+cudaError_t launch_relevance_import(const void* src, int dtype, long long ld_src, float* dst,
+                                    int U, int I, int ld, cudaStream_t s);
+cudaError_t launch_relevance_check(const float* r, int U, int I, int ld, int* flags,
+                                   cudaStream_t s);
+cudaError_t launch_policy(const P1Args& a, int u0, int n_u, float* x_out, cudaStream_t s);
+cudaError_t launch_ex2_bench(float* sink, int blocks, int threads, int iters, cudaStream_t s);
+
+}  // namespace fr

@@ -1,0 +1,191 @@
+"""GPU parity of the free-cost path (Problem (8)) against the FP64 oracle, through the C-ABI.
+
+Tolerances: F (Eq. 5) within 1e-6 relative, policy X within 1e-5 max-abs, impacts within 1e-6
+relative, gradients within 1e-5 relative L2 (FP32 kernels against the FP64 oracle on identical
+seeded inputs)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import NSW_RTOL, X_ATOL, pair, rel, require_gpu, seeded_state
+from paper_2406_10262_gb300 import fairrank as fr
+from paper_2406_10262_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def test_initial_sweep_is_the_uniform_policy():
+    U, I, K = 6, 23, 5
+    r = synth.relevance_uniform(U, I, 3)
+    g, o = pair(U, I, K, r)
+    imp, util, F = g.impacts()
+    oimp, outil, oF = o.impacts()
+    assert rel(F, oF) < NSW_RTOL
+    np.testing.assert_allclose(imp, oimp, rtol=1e-6)
+    X = g.policy()
+    b = np.r_[np.ones(K), I - K] / I
+    np.testing.assert_allclose(X, np.broadcast_to(b, X.shape), atol=1e-6)
+
+
+@pytest.mark.parametrize("U,I,K,eps,L,warm", [
+    (50, 50, 50, 1.0, 50, 1),     # square doubly-stochastic (no dummy column)
+    (7, 37, 10, 1.0, 50, 1),      # ragged item count, dummy column
+    (3, 129, 10, 0.7, 20, 1),     # several warps per consumer, eps != 1
+    (5, 11, 10, 1.0, 30, 0),      # dummy mass 1, cold start
+    (2, 300, 3, 1.3, 1, 1),       # generic column bucket, L = 1
+    (4, 64, 20, 1.0, 40, 1),      # generic 32-column bucket
+])
+def test_one_step_from_seeded_state(U, I, K, eps, L, warm):
+    r = synth.relevance_lowrank(U, I, seed=U + I)
+    g, o = pair(U, I, K, r, epsilon=eps, sinkhorn_iters=L, warm_start=warm)
+    C, m1, m2, gg = seeded_state(U, I, K, seed=I)
+    g.set_state(C, m1, m2, gg, t=3)
+    o.set_state(C.astype(np.float64), m1.astype(np.float64), m2.astype(np.float64),
+                gg.astype(np.float64), 3)
+    # solve at the seeded state: F, impacts, policy, gradient
+    imp, _, F = g.impacts()
+    oimp, _, oF = o.impacts()
+    assert rel(F, oF) < NSW_RTOL
+    np.testing.assert_allclose(imp, oimp, rtol=1e-6)
+    np.testing.assert_allclose(g.policy(), o.policy(), atol=X_ATOL)
+    dg = g.grad()
+    do = o.grad()
+    assert np.linalg.norm(dg - do) <= 1e-5 * np.linalg.norm(do)
+    # one ascent step
+    Fg = g.step(1)
+    Fo, _ = o.step(1)
+    assert rel(Fg[0], Fo[0]) < NSW_RTOL
+    np.testing.assert_allclose(g.policy(), o.policy(), atol=X_ATOL)
+    pg, m1g, m2g, ggg, tg = g.get_state()
+    po, m1o, m2o, ggo, to = o.get_state()
+    assert tg == to == 4
+    np.testing.assert_allclose(pg.reshape(-1), po, atol=2e-5, rtol=1e-5)
+
+
+def test_parity50_trajectory_against_golden():
+    """|U| = |I| = 50, square, r ~ U(0,1) seed 0, 100 Adam steps x 50 Sinkhorn iterations."""
+    gold = json.load(open(os.path.join(GOLDEN, "parity50.json")))
+    U, I, K = gold["n_users"], gold["n_items"], gold["n_slots"]
+    r = synth.workload_relevance("parity50")
+    g, _ = pair(U, I, K, r, lr=gold["lr"])
+    _, _, F0 = g.impacts()
+    assert rel(F0, gold["F0"]) < NSW_RTOL
+    F = g.step(gold["steps"])
+    Fo = np.array(gold["F"])
+    errs = np.abs(F - Fo) / np.abs(Fo)
+    assert errs[:10].max() < NSW_RTOL
+    assert errs.max() < NSW_RTOL, f"max rel F error {errs.max():.2e} at step {errs.argmax()}"
+    imp, _, _ = g.impacts()
+    np.testing.assert_allclose(imp, gold["imp_final"], rtol=1e-5)
+
+
+def test_sgd_trajectory_policy_parity():
+    U, I, K = 9, 40, 6
+    r = synth.relevance_lowrank(U, I, seed=5)
+    g, o = pair(U, I, K, r, optimizer=fr.SGD, lr=0.5)
+    F = g.step(30)
+    Fo, _ = o.step(30)
+    np.testing.assert_allclose(F, Fo, rtol=NSW_RTOL)
+    np.testing.assert_allclose(g.policy(), o.policy(), atol=X_ATOL)
+    assert np.all(np.diff(F) > -1e-6 * np.abs(F[1:]))  # monotone ascent at small steps
+
+
+def test_multiple_calls_equal_one_call_and_are_deterministic():
+    U, I, K = 8, 30, 4
+    r = synth.relevance_uniform(U, I, 11)
+    g1, _ = pair(U, I, K, r)
+    a = np.concatenate([g1.step(5), g1.step(20), g1.step(1)])
+    g2, _ = pair(U, I, K, r)
+    b = g2.step(26)
+    np.testing.assert_array_equal(a, b)
+    g2.reset()
+    np.testing.assert_array_equal(g2.step(26), b)
+
+
+def test_solve_stops_like_the_oracle():
+    U, I, K = 6, 20, 3
+    r = synth.relevance_lowrank(U, I, seed=2)
+    g, o = pair(U, I, K, r)
+    _, gn = o.step(60)
+    thr = float(gn[40]) * 1.0000001
+    o2 = pair(U, I, K, r)[1]
+    n_o, F_o = o2.solve(thr, 60)
+    n_g, F_g = g.solve(thr, 60)
+    assert n_g == n_o
+    assert rel(F_g, F_o) < NSW_RTOL
+
+
+def test_error_statuses():
+    with pytest.raises(fr.FairRankError) as ei:
+        fr.FairRank(4, 5, 2, param=fr.PARAM_ITEM, grad_mode=7)
+    g = fr.FairRank(4, 6, 2)
+    with pytest.raises(fr.FairRankError) as ei:
+        g.step(1)
+    assert ei.value.status == 6  # FR_ESTATE
+    bad = np.ones((4, 6), np.float32)
+    bad[2, 3] = -1
+    with pytest.raises(fr.FairRankError) as ei:
+        g.set_relevance(bad)
+    assert ei.value.status == 1
+    zero_item = np.ones((4, 6), np.float32)
+    zero_item[:, 5] = 0
+    with pytest.raises(fr.FairRankError):
+        g.set_relevance(zero_item)
+    with pytest.raises(fr.FairRankError):
+        g.set_exposure([1.0, 0.0])
+    with pytest.raises(fr.FairRankError):
+        g.policy(3, 2)
+    g.set_relevance(np.ones((4, 6), np.float32))
+    g.set_exposure([1.0, 0.5])
+    g.step(2)
+    assert g.launch_count() > 0
+
+
+def test_state_round_trip():
+    U, I, K = 3, 17, 4
+    g, _ = pair(U, I, K, synth.relevance_uniform(U, I, 1))
+    C, m1, m2, gg = seeded_state(U, I, K, seed=9)
+    g.set_state(C, m1, m2, gg, t=12)
+    p, a, b, q, t = g.get_state()
+    np.testing.assert_array_equal(p, C)
+    np.testing.assert_array_equal(a, m1)
+    np.testing.assert_array_equal(b, m2)
+    np.testing.assert_allclose(q, gg, rtol=1e-6)
+    assert t == 12
+
+
+def test_full_size_plain_workload_sampled_parity():
+    """2000 x 1000, K = 10 (the benchmarked shape): per-consumer Sinkhorn parity on sampled
+    consumers at a seeded state, and F / impacts of the whole market after the solve and after
+    one ascent step against the oracle."""
+    U, I, K = 2000, 1000, 10
+    r = synth.relevance_lowrank(U, I, seed=0)
+    g, o = pair(U, I, K, r)
+    C, m1, m2, gg = seeded_state(U, I, K, seed=77, scale=0.5)
+    g.set_state(C, m1, m2, gg, t=0)
+    o.set_state(C.astype(np.float64), m1.astype(np.float64), m2.astype(np.float64),
+                gg.astype(np.float64), 0)
+    b, _ = oracle.marginals(I, K, synth.dcg_exposure(K))
+    for u in (0, 1, 777, 1999):
+        X = g.policy(u, 1)[0]
+        xo, _, _ = oracle.sinkhorn(C[u].astype(np.float64), b, 1.0, 50, gg[u].astype(np.float64))
+        np.testing.assert_allclose(X, xo, atol=X_ATOL)
+        np.testing.assert_allclose(X.sum(1), 1.0, atol=1e-5)
+    imp, _, F = g.impacts()
+    oimp, _, oF = o.impacts()
+    assert rel(F, oF) < NSW_RTOL
+    np.testing.assert_allclose(imp, oimp, rtol=1e-6)
+    Fg = g.step(1)
+    Fo, _ = o.step(1)
+    assert rel(Fg[0], Fo[0]) < NSW_RTOL
+    x0 = g.policy(1234, 1)[0]
+    np.testing.assert_allclose(x0, o.policy(1234, 1)[0], atol=X_ATOL)
