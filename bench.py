@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="plain2000x1000")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="profiling driver: set up the workload, run this many ascent steps, exit")
     return ap.parse_args()
 
 
@@ -179,6 +181,12 @@ def run_ours(args, w):
     def solve():
         g.reset()
         g.step(S, trace=False)
+
+    if args.profile_steps:
+        g.step(args.profile_steps, trace=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_steps": args.profile_steps, "launches": g.launch_count()}))
+        return
 
     def barrier():
         torch.cuda.synchronize()
