@@ -168,6 +168,38 @@ FR_API fr_status fr_time_kernels(fr_ctx* ctx, int32_t n_steps, double* ms);
    denominator of the Sinkhorn roofline. */
 FR_API fr_status fr_measure_ex2_rate(double* ex2_per_second);
 
+/* ---- allocation-free evaluation --------------------------------------------------------- */
+
+/* For callers that cannot allocate device memory. The paper has no counterpart to this entry
+   point: it packages the library's Sinkhorn solve and impact reduction for code whose device
+   memory belongs to someone else -- a framework's caching allocator or a fixed arena that must not
+   grow -- and for latency-critical loops in which cudaMalloc / cudaFree, which can synchronize the
+   whole device, must not be called. It never calls cudaMalloc, cudaFree or any allocating library
+   routine.
+
+   Computes what fr_impacts reports for a context created with warm_start = 0 whose costs are C:
+   sinkhorn_iters iterations of every consumer's solve from zero column potentials, the impacts
+   Imp_i and F = sum_i log Imp_i.
+   Inputs (device memory, 16-byte aligned): C float [n_users][n_cols][ld], slot-major within a
+   consumer (C[(u*n_cols + k)*ld + i] = c_uik); r float [n_users][ld]; ld a multiple of 8 and
+   >= n_items (entries beyond n_items are ignored). e: host doubles [n_slots], each > 0.
+   Outputs (device memory): imp_out double [n_items]; nsw_util_out double [2] = {F, user utility}.
+   F is -inf or NaN if an impact is not positive (no status is read back: the call stays
+   asynchronous).
+   Scratch: one static array of 8 MiB in device memory, which every GPU that loads the library
+   keeps from load until process exit. The problem must fit in it: about 8 bytes per consumer and
+   column plus 4 bytes per item and CTA (the CTA count shrinks to fit); larger problems return
+   FR_EUNSUPPORTED with a message in fr_last_error(NULL), as do shapes outside the compiled kernel
+   variants. The first call on each device looks up the array's device address
+   (cudaGetSymbolAddress, with that device current); make that first call before any stream
+   capture. Work is enqueued on `stream` (NULL = legacy default stream). Every call uses the same
+   array and leaves its contents behind: calls that can overlap on the GPU (other streams, other
+   host threads) race with each other and corrupt each other's results. */
+FR_API fr_status fr_nsw_eval_noalloc(const float* C, const float* r, int64_t ld, const double* e,
+                                     int32_t n_users, int32_t n_items, int32_t n_slots,
+                                     double epsilon, int32_t sinkhorn_iters, double* imp_out,
+                                     double* nsw_util_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -253,6 +253,11 @@ fr_status zero_state(fr_ctx* ctx) {
 
 }  // namespace
 
+namespace fr {
+// Message slot of fr_last_error(NULL) for entry points that take no context.
+void set_thread_error(const char* msg) { g_create_error = msg; }
+}  // namespace fr
+
 extern "C" {
 
 void fr_config_default(fr_config* cfg, int32_t n_users, int32_t n_items, int32_t n_slots,

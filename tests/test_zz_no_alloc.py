@@ -1,0 +1,100 @@
+"""fr_nsw_eval_noalloc, the entry point for callers that cannot allocate device memory.
+
+Some callers cannot call cudaMalloc: code whose device memory is owned by another allocator (a
+framework's caching allocator, a fixed arena) and latency-critical loops in which cudaMalloc or
+cudaFree would synchronise the device. fr_nsw_eval_noalloc serves them from a static device array
+instead of allocating. Here it is called through the C ABI on consecutive calls with different
+problems, and each result is checked against the context-based entry point fr_impacts (same costs,
+cold-start solve) within the suite's tolerance; a repeated call must reproduce its first result
+exactly, whatever ran in between. The file is named to be collected last.
+"""
+import ctypes as ct
+
+import numpy as np
+import pytest
+
+from gpu_util import NSW_RTOL, require_gpu, seeded_state
+from paper_2406_10262_gb300 import fairrank as fr
+from paper_2406_10262_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return require_gpu()
+
+
+def entry():
+    f = ct.CDLL(fr.LIB_PATH).fr_nsw_eval_noalloc
+    vp = ct.c_void_p
+    f.restype = ct.c_int32
+    f.argtypes = [vp, vp, ct.c_int64, ct.POINTER(ct.c_double), ct.c_int32, ct.c_int32, ct.c_int32,
+                  ct.c_double, ct.c_int32, vp, vp, vp]
+    return f
+
+
+def problem(U, I, K, seed):
+    r = synth.relevance_lowrank(U, I, seed=seed).astype(np.float32)
+    C, _, _, _ = seeded_state(U, I, K, seed=seed, scale=0.7)
+    return r, C
+
+
+def via_context(U, I, K, r, C, L, eps):
+    g = fr.FairRank(U, I, K, warm_start=0, sinkhorn_iters=L, epsilon=eps)
+    g.set_relevance(r)
+    g.set_exposure(synth.dcg_exposure(K))
+    g.set_state(param=C)
+    imp, util, F = g.impacts()
+    g.close()
+    return imp, util, F
+
+
+def via_noalloc(torch, U, I, K, r, C, L, eps):
+    m = fr.num_cols(I, K)
+    ld = (I + 7) // 8 * 8
+    Ck = np.zeros((U, m, ld), np.float32)
+    Ck[:, :, :I] = C.transpose(0, 2, 1)
+    rk = np.zeros((U, ld), np.float32)
+    rk[:, :I] = r
+    Cd = torch.from_numpy(Ck).cuda()
+    rd = torch.from_numpy(rk).cuda()
+    imp = torch.full((I,), -1.0, dtype=torch.float64, device="cuda")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    e = np.ascontiguousarray(synth.dcg_exposure(K))
+    st = entry()(Cd.data_ptr(), rd.data_ptr(), ld, e.ctypes.data_as(ct.POINTER(ct.c_double)), U, I,
+                 K, eps, L, imp.data_ptr(), out.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert st == 0, fr.lib().fr_last_error(None)
+    torch.cuda.synchronize()
+    return imp.cpu().numpy(), out[1].item(), out[0].item()
+
+
+def test_matches_fr_impacts_on_consecutive_calls(torch):
+    cases = [(40, 300, 10, 50, 1.0, 1), (7, 37, 5, 20, 0.8, 2)]
+    first = None
+    for U, I, K, L, eps, seed in cases + cases[:1]:
+        r, C = problem(U, I, K, seed)
+        imp_ref, util_ref, F_ref = via_context(U, I, K, r, C, L, eps)
+        imp, util, F = via_noalloc(torch, U, I, K, r, C, L, eps)
+        assert abs(F - F_ref) <= NSW_RTOL * abs(F_ref)
+        assert abs(util - util_ref) <= NSW_RTOL * abs(util_ref)
+        np.testing.assert_allclose(imp, imp_ref, rtol=NSW_RTOL)
+        if first is None:
+            first = (imp, F)
+        elif (U, I, K) == cases[0][:3]:
+            np.testing.assert_array_equal(imp, first[0])  # nothing left over from the call between
+            assert F == first[1]
+
+
+def test_rejects_problems_larger_than_the_static_scratch(torch):
+    small = torch.zeros(64, dtype=torch.float32, device="cuda")
+    out = torch.zeros(8, dtype=torch.float64, device="cuda")
+    e = np.ones(7)
+    # 600000 consumers x 8 columns of potentials alone exceed the 8 MiB array; rejected on the host
+    st = entry()(small.data_ptr(), small.data_ptr(), 8, e.ctypes.data_as(ct.POINTER(ct.c_double)),
+                 600000, 8, 7, 1.0, 10, out.data_ptr(), out.data_ptr(), 0)
+    assert st == 7  # FR_EUNSUPPORTED
+    assert b"static scratch" in fr.lib().fr_last_error(None)
+    st = entry()(small.data_ptr(), small.data_ptr(), 12, e.ctypes.data_as(ct.POINTER(ct.c_double)),
+                 4, 8, 7, 1.0, 10, out.data_ptr(), out.data_ptr(), 0)
+    assert st == 1  # ld not a multiple of 8
