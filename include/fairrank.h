@@ -159,8 +159,9 @@ FR_API int64_t fr_launch_count(const fr_ctx* ctx);
 
 /* Times the kernels of the ascent step with CUDA events recorded on the library stream around
    each launch: runs n_steps >= 1 steps with direct launches (no graph) and writes the mean
-   duration in milliseconds of the fused gradient+Adam+Sinkhorn kernel (ms[0]) and of the
-   cross-consumer reduction kernel (ms[1]). Advances the optimiser state like fr_step. */
+   duration in milliseconds of the fused gradient+Adam+Sinkhorn kernel (ms[0]), of the
+   cross-consumer reduction kernel (ms[1]) and of a Sinkhorn-only solve of the same costs (ms[2],
+   launched after each step). Advances the optimiser state like fr_step. */
 FR_API fr_status fr_time_kernels(fr_ctx* ctx, int32_t n_steps, double* ms);
 
 /* Measures the sustained rate of ex2.approx.f32 on the current device with a dependent-chain-free

@@ -180,6 +180,8 @@ fr_status set_run_state(fr_ctx* ctx, double thresh) {
 fr_status read_state(fr_ctx* ctx) {
     CU(cudaMemcpyAsync(ctx->st_host, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->s));
     CU(cudaStreamSynchronize(ctx->s));
+    if (ctx->st_host->err & 4)
+        return fail(ctx, FR_ETIMEOUT, "a bounded wait for a staged bulk copy expired");
     if (ctx->st_host->err)
         return fail(ctx, FR_ENUMERIC, "non-finite or non-positive impact (flags %d)",
                     ctx->st_host->err);
@@ -353,7 +355,9 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
         size_t b = p1_smem_bytes(var, m, nc, ctx->ld);
         if (b > (size_t)max_optin)
             return bail(fail(ctx, FR_EUNSUPPORTED,
-                             "shared memory %zu B exceeds the device limit %d B (n_items * n_cols too large)",
+                             "shared memory %zu B exceeds the device limit %d B: the free-cost "
+                             "parametrisation stages one consumer's n_items x n_cols cost tile "
+                             "(about n_items * (4 * n_cols + 20) bytes)",
                              b, max_optin));
         CUC(cudaFuncSetAttribute(var.fn[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
         smem_max = b > smem_max ? b : smem_max;
@@ -644,9 +648,9 @@ fr_status fr_time_kernels(fr_ctx* ctx, int32_t n_steps, double* ms) {
     fr_status st = ensure_fresh(ctx);
     if (st != FR_OK) return st;
     if ((st = set_run_state(ctx, -1.0)) != FR_OK) return st;
-    cudaEvent_t ev[3];
+    cudaEvent_t ev[4];
     for (auto& e : ev) CU(cudaEventCreate(&e));
-    double acc[2] = {0.0, 0.0};
+    double acc[3] = {0.0, 0.0, 0.0};
     const P1Args pa = p1_args(ctx);
     const ReduceArgs ra = red_args(ctx, 1);
     for (int s = 0; s < n_steps; ++s) {
@@ -655,17 +659,23 @@ fr_status fr_time_kernels(fr_ctx* ctx, int32_t n_steps, double* ms) {
         CU(cudaEventRecord(ev[1], ctx->s));
         CU(reduce_launch(ra, ctx->s));
         CU(cudaEventRecord(ev[2], ctx->s));
-        ctx->launches += 2;
-        CU(cudaEventSynchronize(ev[2]));
-        float a = 0.f, b = 0.f;
+        CU(p1_launch(ctx->var, MODE_SWEEP, pa, ctx->s));  // Sinkhorn only, same costs
+        CU(cudaEventRecord(ev[3], ctx->s));
+        CU(reduce_launch(red_args(ctx, 0), ctx->s));
+        ctx->launches += 4;
+        CU(cudaEventSynchronize(ev[3]));
+        float a = 0.f, b = 0.f, c = 0.f;
         CU(cudaEventElapsedTime(&a, ev[0], ev[1]));
         CU(cudaEventElapsedTime(&b, ev[1], ev[2]));
+        CU(cudaEventElapsedTime(&c, ev[2], ev[3]));
         acc[0] += a;
         acc[1] += b;
+        acc[2] += c;
     }
     for (auto& e : ev) cudaEventDestroy(e);
     ms[0] = acc[0] / n_steps;
     ms[1] = acc[1] / n_steps;
+    ms[2] = acc[2] / n_steps;
     return read_state(ctx);
 }
 

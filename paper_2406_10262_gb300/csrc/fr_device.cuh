@@ -21,7 +21,88 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return y;
 }
 
+// log2(x) on the multi-function unit (absolute error ~2^-22 near 1).
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 constexpr int pow2ceil(int n) { return n <= 1 ? 1 : 2 * pow2ceil((n + 1) / 2); }
+
+// ---- bulk (TMA) copies and mbarriers --------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// Global -> shared bulk copy completing on `bar` (16-byte aligned addresses, size % 16 == 0).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// Bulk prefetch of [src, src + bytes) into L2 (16-byte aligned, size % 16 == 0).
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+// Bounded wait for phase `parity` of `bar`: returns false if it did not complete within
+// `max_polls` polls (the caller records an error instead of spinning forever).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
+                                          unsigned max_polls) {
+    for (unsigned it = 0; it < max_polls; ++it) {
+        unsigned done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// ---- packed pairs of FP32 values (sm_100+ f32x2 arithmetic: two lanes per instruction) ---------
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1,%2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk(f2 v, float& a, float& b) {
+    asm("mov.b64 {%0,%1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
 
 // ---- vector loads/stores of R consecutive floats (R in {1,2,4,8}; 4R-byte aligned) ------------
 template <int R>
@@ -126,6 +207,32 @@ __device__ __forceinline__ void cta_reduce(float (&v)[NV][NCB], int nc, float* s
         float s = 0.f;
         for (int ww = 0; ww < W; ++ww) s += s_red[(ww * NV + j) * P + k];
         out[j * ncp + k] = s;
+    }
+    __syncthreads();
+}
+
+// Sum of one per-thread vector of length N over the CTA into out[k] (k < n_valid). s_red needs
+// (blockDim/32) * pow2ceil(N) floats. Deterministic; two __syncthreads.
+template <int N>
+__device__ __forceinline__ void cta_reduce_vec(float (&v)[N], int n_valid, float* s_red, float* out) {
+    constexpr int P = pow2ceil(N);
+    constexpr int PER = P >= 32 ? P / 32 : 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+    float w[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) w[k] = k < N ? v[k] : 0.f;
+    bool owner;
+    const int base = warp_reduce_scatter<P>(w, lane, owner);
+    if (owner) {
+#pragma unroll
+        for (int q = 0; q < PER; ++q)
+            if (base + q < n_valid) s_red[warp * P + base + q] = w[q];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_valid; k += blockDim.x) {
+        float s = 0.f;
+        for (int ww = 0; ww < W; ++ww) s += s_red[ww * P + k];
+        out[k] = s;
     }
     __syncthreads();
 }

@@ -1,30 +1,42 @@
 // fr_p1.cu -- kernels of the free-cost parametrisation (Problem (8): one cost c_uik per cell).
 //
 // One persistent CTA processes consumers u = blockIdx.x, blockIdx.x + G, ... (Algorithm 1's
-// parallel loop over consumers). A thread owns R consecutive items (rows) of the consumer; their
-// costs stay in registers for the whole Sinkhorn solve, so the L iterations touch HBM only once.
+// parallel loop over consumers). Each consumer's cost tile and relevance row are bulk-copied (TMA)
+// into shared memory one consumer ahead, while the previous consumer's Sinkhorn iterations run.
 //
 // Sinkhorn (Problem (7)) runs in the fused single-pass log-domain form, in log2 units
 // c' = c / (eps ln 2), g' = g / (eps ln 2):
 //   p_ik = 2^(g'_k - c~_ik),  S_i = sum_k p_ik,  x_ik = p_ik / S_i       (row update, Eq. 1)
 //   cs_k = sum_i x_ik,        g'_k += log2 b_k - log2 cs_k               (column update, Eq. 2)
 // which equals the textbook two-pass update (f_i = -eps LSE_k, g_k = eps log b_k - eps LSE_i)
-// algebraically and costs one exp2 per cell per iteration. c~_ik = c'_ik + shift_i carries a
-// per-row shift fixed at the start of the solve (row max), so 2^(.) stays in range without a
-// max pass per iteration; a row whose S_i leaves [2^-64, 2^64] is re-shifted exactly.
+// algebraically and costs one exp2 per cell per iteration. A thread owns R consecutive items
+// (rows) and keeps their costs in registers for the whole solve. c~_ik = c'_ik + shift_i carries
+// a per-row shift fixed at the start of the solve (the row max), so 2^(.) stays in range without
+// a max pass per iteration; a row whose S_i leaves [2^-64, 2^64] is re-shifted exactly.
+//
+// Inner loop: two rows at a time in packed f32x2 arithmetic (one instruction per pair of cells),
+// one exp2 per cell on the MUFU. Column sums: per-warp reduce-scatter by shuffles, one
+// __syncthreads per iteration on double-buffered partials, after which every warp sums the
+// per-warp partials of its lanes' columns in the same fixed order and updates its own copy of the
+// column potentials (so no second barrier is needed and every warp holds identical g').
 //
 // The last iteration emits x (the policy right after the last row update, rows sum to 1) and adds
 // r(u,i) * sum_{k<K} e_k x_ik into per-thread impact accumulators (Eq. 4) that persist over the
 // CTA's consumers; they are written once per launch to part[blockIdx][i] and combined across CTAs
 // by the reduction kernel in a fixed order.
 //
-// MODE_UPDATE_SWEEP first takes the gradient step of Algorithm 1 for the consumer: it re-forms
-// the previous policy from C and g^(L-1), computes dF/dC by implicit differentiation of the
-// optimality conditions of Problem (7),
+// MODE_UPDATE_SWEEP first takes the gradient step of Algorithm 1 for the consumer, working from
+// the shared-memory tile with compact loops (the code runs once per consumer, so it is kept small
+// for the instruction cache): it re-forms the previous policy from C and g^(L-1), computes dF/dC
+// by implicit differentiation of the optimality conditions of Problem (7),
 //   h_i = sum_k x_ik G_ik, q_k = sum_i x_ik G_ik, (diag(cs) - X^T X) beta = q - X^T h (beta_last = 0),
 //   alpha_i = h_i - sum_k x_ik beta_k,  dF/dc_ik = -(1/eps) x_ik (G_ik - alpha_i - beta_k),
-// with G_ik = r(u,i) e_k / Imp_i, applies Adam (ascent) to C in registers, writes C and the
-// moments back, and then solves Sinkhorn on the new costs without reloading them.
+// with G_ik = r(u,i) e_k / Imp_i, applies Adam (ascent) to the tile and writes C and the moments
+// back, then solves Sinkhorn on the new costs without reloading them from HBM. The Gram block is
+// accumulated in registers for narrow tiles (<= 16 columns) and from a shared copy of the policy
+// otherwise; the (m-1) x (m-1) system is solved by one warp, lane-parallel in single precision for
+// narrow tiles (double-precision division and square root are long software sequences on this
+// part) and in double precision for wide ones.
 #include "fr_device.cuh"
 #include "fr_internal.h"
 
@@ -32,27 +44,43 @@ namespace fr {
 
 namespace {
 
-// dynamic shared-memory layout (floats unless noted)
 struct Smem {
-    float* g;     // [NCP] current g'
-    float* gp;    // [NCP] g^(L-1)' of the previous solve (update mode)
-    float* l2b;   // [NCP] log2 b
-    float* e;     // [NCP] exposure
-    float* red;   // [W][3][P] reduction scratch
-    float* out;   // [3][NCP] reduction results
-    float* beta;  // [NCP]
-    double* A;    // [n*n] Gram system (update mode)
-    double* rhs;  // [NCP]
-    float* X;     // [nc][ld] policy of the consumer (update mode)
+    float* gp;    // [ncx] g^(L-1)' of the previous solve (update modes)
+    float* l2b;   // [ncx] log2 b
+    float* e;     // [ncx] exposure
+    float* beta;  // [ncx]
+    float* coef;  // [2] Adam step size and sqrt of the second bias correction
+    unsigned long long* bar;  // mbarrier of the staged copies
+    float* red;   // reduction scratch (sweep double buffer / update reductions)
+    float* out;   // [3*ncp + NG] reduction results
+    double* A;    // [n*n] Gram system (update modes; floats for narrow tiles)
+    double* rhs;  // [ncp]
+    float* Lt;    // [n*n] transposed Cholesky factor (update modes, narrow tiles)
+    float* C;     // [nc][ld] staged cost tile of the consumer
+    float* r;     // [ld] staged relevance row
+    float* om;    // [ld] dF/dImp_i (update modes)
+    float* lse;   // [ld] row log2-normalisers of the previous policy (update modes)
+    float* h;     // [ld]
+    float* alpha; // [ld]
+    float* vimp;  // [ld] sum_{k<K} e_k x_ik (gradient mode)
+    float* X;     // [nc][ld] policy of the consumer (update modes, wide tiles only)
 };
 
-constexpr int NCP_ALIGN = 4;
+__host__ __device__ constexpr bool reg_gram(int ncb) { return ncb <= 16; }
+__host__ __device__ constexpr int n_gram(int ncb) { return reg_gram(ncb) ? ncb * (ncb - 1) / 2 : 1; }
 
-__host__ __device__ inline int ncp_of(int nc) { return (nc + NCP_ALIGN - 1) / NCP_ALIGN * NCP_ALIGN; }
+__host__ __device__ inline int ncp_of(int nc) { return (nc + 3) / 4 * 4; }
+// per-column shared arrays hold max(nc, NCB) entries (zero beyond nc) so that unrolled loops over
+// the compiled column bucket read zeros, never a neighbouring array
+__host__ __device__ inline int ncx_of(int nc, int ncb) { return ncp_of(nc > ncb ? nc : ncb); }
 
-__host__ __device__ inline size_t smem_layout(int nc, int ld, int W, int P, int mode, Smem* s,
+__host__ __device__ inline size_t smem_layout(int ncb, int nc, int ld, int W, int mode, Smem* s,
                                               unsigned char* base) {
+    const int P = pow2ceil(ncb);
+    const int NG = n_gram(ncb);
+    const int PG = pow2ceil(NG);
     const int ncp = ncp_of(nc);
+    const int ncx = ncx_of(nc, ncb);
     const int n = nc - 1;
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -60,35 +88,55 @@ __host__ __device__ inline size_t smem_layout(int nc, int ld, int W, int P, int 
         off += (bytes + 15) / 16 * 16;
         return o;
     };
-    size_t o_g = take(sizeof(float) * ncp), o_gp = take(sizeof(float) * ncp);
-    size_t o_l2b = take(sizeof(float) * ncp), o_e = take(sizeof(float) * ncp);
-    size_t o_red = take(sizeof(float) * (size_t)W * 3 * P);
-    size_t o_out = take(sizeof(float) * 3 * ncp);
-    size_t o_beta = take(sizeof(float) * ncp);
-    size_t o_A = 0, o_rhs = 0, o_X = 0;
-    if (mode != MODE_SWEEP) {
+    const bool upd = mode != MODE_SWEEP;
+    size_t red_f = (size_t)W * 3 * P;
+    if ((size_t)W * PG > red_f) red_f = (size_t)W * PG;
+    const size_t o_gp = take(sizeof(float) * ncx), o_l2b = take(sizeof(float) * ncx);
+    const size_t o_e = take(sizeof(float) * ncx), o_beta = take(sizeof(float) * ncx);
+    const size_t o_coef = take(sizeof(float) * 2), o_bar = take(sizeof(unsigned long long));
+    const size_t o_red = take(sizeof(float) * red_f);
+    const size_t o_out = take(sizeof(float) * (3 * ncp + NG));
+    const size_t o_C = take(sizeof(float) * (size_t)nc * ld);
+    const size_t o_r = take(sizeof(float) * ld);
+    size_t o_A = 0, o_rhs = 0, o_Lt = 0, o_om = 0, o_lse = 0, o_h = 0, o_al = 0, o_vi = 0, o_X = 0;
+    if (upd) {
         o_A = take(sizeof(double) * (size_t)(n > 0 ? n * n : 1));
         o_rhs = take(sizeof(double) * ncp);
-        o_X = take(sizeof(float) * (size_t)nc * ld);
+        o_Lt = take(sizeof(float) * (size_t)(n > 0 ? n * n : 1));
+        o_om = take(sizeof(float) * ld);
+        o_lse = take(sizeof(float) * ld);
+        o_h = take(sizeof(float) * ld);
+        o_al = take(sizeof(float) * ld);
+        if (mode == MODE_GRAD) o_vi = take(sizeof(float) * ld);
+        if (!reg_gram(ncb)) o_X = take(sizeof(float) * (size_t)nc * ld);
     }
     if (s) {
-        s->g = (float*)(base + o_g);
         s->gp = (float*)(base + o_gp);
         s->l2b = (float*)(base + o_l2b);
         s->e = (float*)(base + o_e);
+        s->beta = (float*)(base + o_beta);
+        s->coef = (float*)(base + o_coef);
+        s->bar = (unsigned long long*)(base + o_bar);
         s->red = (float*)(base + o_red);
         s->out = (float*)(base + o_out);
-        s->beta = (float*)(base + o_beta);
         s->A = (double*)(base + o_A);
         s->rhs = (double*)(base + o_rhs);
+        s->Lt = (float*)(base + o_Lt);
+        s->C = (float*)(base + o_C);
+        s->r = (float*)(base + o_r);
+        s->om = (float*)(base + o_om);
+        s->lse = (float*)(base + o_lse);
+        s->h = (float*)(base + o_h);
+        s->alpha = (float*)(base + o_al);
+        s->vimp = (float*)(base + o_vi);
         s->X = (float*)(base + o_X);
     }
     return off;
 }
 
-// Cholesky solve of the n x n SPD system in s.A (row-major, lower triangle used) with right-hand
-// side s.rhs, by one warp, in double precision. Pivots below `floor` are raised to it (a column
-// with no mass leaves the Laplacian-like Gram matrix singular; its beta is then ~0).
+// Cholesky solve of the n x n SPD system A (row-major) with right-hand side rhs, by one warp, in
+// double precision (wide tiles). Pivots below `floor` are raised to it (a column with no mass
+// leaves the Laplacian-like Gram matrix singular; its beta is then ~0).
 __device__ void warp_cholesky_solve(double* A, double* rhs, int n, int lane) {
     double dmax = 0.0;
     for (int j = 0; j < n; ++j) dmax = fmax(dmax, A[j * n + j]);
@@ -122,284 +170,564 @@ __device__ void warp_cholesky_solve(double* A, double* rhs, int n, int lane) {
     }
 }
 
+// Solve of the n x n SPD system (n <= NM <= 31) held in shared memory (A row-major, rhs), by one
+// warp in single precision: lane i keeps row i of A in registers; right-looking Cholesky with the
+// pivot column broadcast by shuffles, forward substitution in registers, back substitution from a
+// transposed copy of L in shared memory (Lt, n*n floats). Pivots below `floor` are raised to it.
+// Writes beta[0..n).
+template <int NM>
+__device__ void warp_cholesky_solve_f32(const float* A, const float* rhs, int n, float* Lt,
+                                        float* beta, int lane) {
+    float row[NM];
+#pragma unroll
+    for (int k = 0; k < NM; ++k) row[k] = (lane < n && k < n) ? A[lane * n + k] : 0.f;
+    float dmax = 0.f;
+#pragma unroll
+    for (int j = 0; j < NM; ++j)
+        if (j < n) dmax = fmaxf(dmax, __shfl_sync(FULL, row[j], j));
+    const float floor_ = 1e-12f * fmaxf(dmax, 1e-30f);
+#pragma unroll
+    for (int j = 0; j < NM; ++j) {
+        if (j >= n) break;
+        const float ljj = sqrtf(fmaxf(__shfl_sync(FULL, row[j], j), floor_));
+        const float lij = lane > j ? row[j] / ljj : (lane == j ? ljj : 0.f);
+        row[j] = lij;
+#pragma unroll
+        for (int k = j + 1; k < NM; ++k) {
+            const float lkj = __shfl_sync(FULL, lij, k);
+            if (lane > j) row[k] -= lij * lkj;
+        }
+    }
+    float y = lane < n ? rhs[lane] : 0.f;  // L y = rhs: lane i holds y_i
+#pragma unroll
+    for (int j = 0; j < NM; ++j) {
+        if (j >= n) break;
+        const float yj = __shfl_sync(FULL, y, j) / __shfl_sync(FULL, row[j], j);
+        if (lane == j) y = yj;
+        if (lane > j) y -= row[j] * yj;
+    }
+    if (lane < n) {  // Lt[k][i] = L[i][k]
+#pragma unroll
+        for (int k = 0; k < NM; ++k)
+            if (k < n) Lt[k * n + lane] = row[k];
+    }
+    __syncwarp();
+    float z = y;  // L^T z = y
+    for (int j = n - 1; j >= 0; --j) {
+        const float zj = __shfl_sync(FULL, z, j) / Lt[j * n + j];
+        if (lane == j) z = zj;
+        if (lane < j) z -= Lt[lane * n + j] * zj;  // (L^T)[i][j] = L[j][i]
+    }
+    if (lane < n) beta[lane] = z;
+}
+
+// Broadcast of the column potentials held by lane k % 32 (slot k / 32) to every lane.
+template <int NCB, int GPL>
+__device__ __forceinline__ void bcast_g(const float (&gm)[GPL], float (&gk)[NCB]) {
+#pragma unroll
+    for (int k = 0; k < NCB; ++k) gk[k] = __shfl_sync(FULL, gm[k / 32], k % 32);
+}
+
+// Column update after the row sums: warp reduce-scatter of cs, one barrier, then every warp sums
+// the per-warp partials of its lanes' columns and updates its copy of g'.
+template <int NCB, int GPL>
+__device__ __forceinline__ void column_update(float (&cs)[NCB], float (&gm)[GPL], int nc,
+                                              float* s_red, const float* s_l2b, int par, int lane,
+                                              int warp, int W) {
+    constexpr int P = pow2ceil(NCB);
+    constexpr int PER = P >= 32 ? P / 32 : 1;
+    float w[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) w[k] = k < NCB ? cs[k] : 0.f;
+    bool owner;
+    const int base = warp_reduce_scatter<P>(w, lane, owner);
+    float* buf = s_red + (size_t)par * W * P;
+    if (owner) {
+#pragma unroll
+        for (int q = 0; q < PER; ++q)
+            if (base + q < nc) buf[warp * P + base + q] = w[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < GPL; ++j) {
+        const int col = j * 32 + lane;
+        if (col < nc) {
+            float sum = 0.f;
+            for (int ww = 0; ww < W; ++ww) sum += buf[ww * P + col];
+            gm[j] += s_l2b[col] - log2f(fmaxf(sum, 1e-37f));
+        }
+    }
+}
+
+// Thread 0: bulk-copies consumer un's cost tile and relevance row into the staging buffers. Every
+// thread of the CTA must be done reading them (the caller sits after a __syncthreads).
+__device__ __forceinline__ void stage_consumer(const P1Args& a, int un, int nc, int ld,
+                                               const Smem& s, bool prefetch_moments) {
+    if (un >= a.U) return;
+    const unsigned tile = (unsigned)(sizeof(float) * (size_t)nc * ld);
+    const unsigned row = (unsigned)(sizeof(float) * ld);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(s.bar, tile + row);
+    bulk_g2s(s.C, a.C + (size_t)un * nc * ld, tile, s.bar);
+    bulk_g2s(s.r, a.r + (size_t)un * ld, row, s.bar);
+    if (prefetch_moments) {  // the Adam moments of that consumer: into L2 for the gradient step
+        bulk_prefetch_l2(a.m1 + (size_t)un * nc * ld, tile);
+        bulk_prefetch_l2(a.m2 + (size_t)un * nc * ld, tile);
+    }
+}
+
 template <int NCB, int R, bool EXACT, int MODE>
 __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int P = pow2ceil(NCB);
+    constexpr int GPL = (NCB + 31) / 32;
+    constexpr bool REG_GRAM = reg_gram(NCB);
+    constexpr int NG = n_gram(NCB);
+    constexpr bool PAIR = R % 2 == 0;
     const int nc = EXACT ? NCB : a.nc;
     const int ncp = ncp_of(nc);
+    const int ncx = ncx_of(nc, NCB);
+    const int n = nc - 1;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
+    const int T = blockDim.x;
     const int I = a.I, ld = a.ld;
     const int i0 = tid * R;
     const bool any_row = i0 < I;
+    const float sc = a.inv_eps_ln2;
     Smem s;
-    smem_layout(nc, ld, W, P, MODE, &s, smem_raw);
+    smem_layout(NCB, nc, ld, W, MODE, &s, smem_raw);
 
     if (a.st->stop) return;  // fr_solve reached its threshold: the remaining steps are no-ops
 
-    for (int k = tid; k < ncp; k += blockDim.x) {
+    if (tid == 0) {
+        mbar_init(s.bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();  // the mbarrier is initialised before any thread waits on it
+    if (tid == 0) {
+        stage_consumer(a, blockIdx.x, nc, ld, s, MODE == MODE_UPDATE_SWEEP && a.optimizer == 0);
+        // Adam bias corrections for this step (t counts applied steps before this one)
+        float step_size = a.lr, bc2s = 1.f;
+        if (MODE == MODE_UPDATE_SWEEP && a.optimizer == 0) {
+            const double t1 = (double)(a.st->t + 1);
+            const double bc1 = 1.0 - pow((double)a.beta1, t1);
+            const double bc2 = 1.0 - pow((double)a.beta2, t1);
+            step_size = (float)((double)a.lr / bc1);
+            bc2s = (float)sqrt(bc2);
+        }
+        s.coef[0] = step_size;
+        s.coef[1] = bc2s;
+    }
+    for (int k = tid; k < ncx; k += T) {
         s.l2b[k] = k < nc ? a.log2b[k] : 0.f;
         s.e[k] = k < nc ? a.e[k] : 0.f;
     }
+    if (MODE != MODE_SWEEP)
+        for (int i = tid; i < ld; i += T) s.om[i] = i < I ? a.omega[i] : 0.f;
 
     float acc_imp[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc_imp[r] = 0.f;
     double gn2 = 0.0;
-
-    // Adam bias corrections for this step (t counts applied steps before this one)
-    float step_size = a.lr, bc2s = 1.f;
-    if (MODE == MODE_UPDATE_SWEEP && a.optimizer == 0) {
-        const double t1 = (double)(a.st->t + 1);
-        const double bc1 = 1.0 - pow((double)a.beta1, t1);
-        const double bc2 = 1.0 - pow((double)a.beta2, t1);
-        step_size = (float)((double)a.lr / bc1);
-        bc2s = (float)sqrt(bc2);
-    }
+    int par = 0;
+    unsigned phase = 0;
 
     for (int u = blockIdx.x; u < a.U; u += gridDim.x) {
         const size_t tile = (size_t)u * nc * ld;
-        if (tid < nc) {
-            s.g[tid] = a.warm ? a.gL[(size_t)u * nc + tid] : 0.f;
-            if (MODE != MODE_SWEEP) s.gp[tid] = a.gP[(size_t)u * nc + tid];
+        float gm[GPL];  // column potentials of the columns this lane holds (same in every warp)
+#pragma unroll
+        for (int j = 0; j < GPL; ++j) {
+            const int col = j * 32 + lane;
+            gm[j] = (a.warm && col < nc) ? a.gL[(size_t)u * nc + col] : 0.f;
         }
-        float rr[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) rr[r] = 0.f;
-        if (any_row) ldv<R>(rr, a.r + (size_t)u * ld + i0);
-        bool vr[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) vr[r] = i0 + r < I;
-
-        // costs of the owned rows, natural units
-        float c[R][NCB];
-#pragma unroll
-        for (int k = 0; k < NCB; ++k) {
-            float tmp[R];
-            if ((EXACT || k < nc) && any_row) {
-                ldv<R>(tmp, a.C + tile + (size_t)k * ld + i0);
-            } else {
-#pragma unroll
-                for (int r = 0; r < R; ++r) tmp[r] = 0.f;
-            }
-#pragma unroll
-            for (int r = 0; r < R; ++r) c[r][k] = tmp[r];
+        if (MODE != MODE_SWEEP && tid < ncx) s.gp[tid] = tid < nc ? a.gP[(size_t)u * nc + tid] : 0.f;
+        // the consumer's tile was staged one consumer ago; a bounded wait records a timeout
+        // instead of hanging (the CTA then continues on whatever data is there)
+        if (!mbar_wait(s.bar, phase, 1u << 26)) {
+            if (tid == 0) atomicOr(&a.st->err, 4);
         }
-        __syncthreads();  // s.g / s.gp / s.e / s.l2b visible
+        phase ^= 1u;
+        __syncthreads();  // s.gp / s.e / s.l2b / s.om / s.coef visible
 
         if constexpr (MODE != MODE_SWEEP) {
             // ---------------- gradient of F at the previous policy ------------------------------
-            float wr[R], om[R];
+            // x_ik = 2^(g'_k - c'_ik - lse_i) is re-formed from the staged tile and the row
+            // log-normaliser lse_i of the first pass.
+            {
+                float acc[3][NCB];  // q, cs, X^T h partials
 #pragma unroll
-            for (int r = 0; r < R; ++r) om[r] = 0.f;
-            if (any_row) ldv<R>(om, a.omega + i0);
+                for (int k = 0; k < NCB; ++k) acc[0][k] = acc[1][k] = acc[2][k] = 0.f;
+                for (int i = tid; i < I; i += T) {
+                    float x[NCB];
+                    float M = -INFINITY;
 #pragma unroll
-            for (int r = 0; r < R; ++r) wr[r] = vr[r] ? om[r] * rr[r] : 0.f;  // dF/dx_ik = wr_i e_k
-            float acc[3][NCB];  // q, cs, X^T h partials
-#pragma unroll
-            for (int k = 0; k < NCB; ++k) acc[0][k] = acc[1][k] = acc[2][k] = 0.f;
-            float hrow[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                hrow[r] = 0.f;
-                if (!vr[r]) continue;
-                float p[NCB];
-                float M = -INFINITY;
-#pragma unroll
-                for (int k = 0; k < NCB; ++k)
-                    if (EXACT || k < nc) M = fmaxf(M, s.gp[k] - c[r][k] * a.inv_eps_ln2);
-                float S = 0.f;
-#pragma unroll
-                for (int k = 0; k < NCB; ++k) {
-                    p[k] = (EXACT || k < nc) ? ex2(s.gp[k] - c[r][k] * a.inv_eps_ln2 - M) : 0.f;
-                    S += p[k];
-                }
-                const float inv = 1.f / S;
-                float h = 0.f;
-#pragma unroll
-                for (int k = 0; k < NCB; ++k) {
-                    p[k] *= inv;
-                    if (EXACT || k < nc) h += p[k] * (wr[r] * s.e[k]);
-                }
-                hrow[r] = h;
-#pragma unroll
-                for (int k = 0; k < NCB; ++k) {
-                    if (EXACT || k < nc) {
-                        s.X[k * ld + i0 + r] = p[k];
-                        acc[0][k] += p[k] * (wr[r] * s.e[k]);
-                        acc[1][k] += p[k];
-                        acc[2][k] += p[k] * h;
+                    for (int k = 0; k < NCB; ++k) {
+                        x[k] = (EXACT || k < nc) ? s.gp[k] - s.C[k * ld + i] * sc : -INFINITY;
+                        M = fmaxf(M, x[k]);
                     }
-                }
-            }
-            cta_reduce<NCB, 3>(acc, nc, s.red, s.out, ncp);  // s.out: [q | cs | X^T h]
-            // Gram block M[0:n,0:n] of diag(cs) - X^T X (rows of x sum to 1, so the diagonal is
-            // sum_i x_ik (1 - x_ik) without cancellation), and the right-hand side q - X^T h.
-            const int n = nc - 1;
-            const int npairs = n * (n + 1) / 2;
-            for (int pidx = warp; pidx < npairs; pidx += W) {
-                int k = 0, rem = pidx;
-                while (rem >= n - k) { rem -= n - k; ++k; }
-                const int l = k + rem;
-                const float* xk = s.X + k * ld;
-                const float* xl = s.X + l * ld;
-                float sum = 0.f;
-                if (k == l) {
-                    for (int i = lane; i < I; i += 32) sum += xk[i] * (1.f - xk[i]);
-                } else {
-                    for (int i = lane; i < I; i += 32) sum -= xk[i] * xl[i];
-                }
+                    float S = 0.f;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
-                if (lane == 0) {
-                    s.A[k * n + l] = (double)sum;
-                    s.A[l * n + k] = (double)sum;
-                }
-            }
-            for (int k = tid; k < n; k += blockDim.x)
-                s.rhs[k] = (double)s.out[k] - (double)s.out[2 * ncp + k];
-            __syncthreads();
-            if (warp == 0) warp_cholesky_solve(s.A, s.rhs, n, lane);
-            __syncthreads();
-            for (int k = tid; k < ncp; k += blockDim.x) s.beta[k] = k < n ? (float)s.rhs[k] : 0.f;
-            __syncthreads();
-
-            float alpha[R];
+                    for (int k = 0; k < NCB; ++k) {
+                        x[k] = ex2(x[k] - M);
+                        S += x[k];
+                    }
+                    const float inv = 1.f / S;
+                    const float wr = s.om[i] * s.r[i];  // dF/dx_ik = wr_i e_k
+                    float hh = 0.f, vi = 0.f;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float sb = 0.f;
-                if (vr[r]) {
+                    for (int k = 0; k < NCB; ++k) {
+                        x[k] *= inv;
+                        hh += x[k] * (wr * s.e[k]);
+                        if (MODE == MODE_GRAD && k < a.K) vi += s.e[k] * x[k];
+                    }
+#pragma unroll
+                    for (int k = 0; k < NCB; ++k) {
+                        acc[0][k] += x[k] * (wr * s.e[k]);
+                        acc[1][k] += x[k];
+                        acc[2][k] += x[k] * hh;
+                        if constexpr (!REG_GRAM) {
+                            if (EXACT || k < nc) s.X[k * ld + i] = x[k];
+                        }
+                    }
+                    s.lse[i] = M + log2f(S);
+                    s.h[i] = hh;
+                    if (MODE == MODE_GRAD) s.vimp[i] = vi;
+                }
+                cta_reduce<NCB, 3>(acc, nc, s.red, s.out, ncp);  // s.out: [q | cs | X^T h]
+            }
+            // Gram block M[0:n,0:n] of diag(cs) - X^T X; rows of x sum to 1, so the diagonal is
+            // sum_i x_ik (1 - x_ik) without cancellation.
+            if constexpr (REG_GRAM) {
+                float gram[NG];
+#pragma unroll
+                for (int q = 0; q < NG; ++q) gram[q] = 0.f;
+                for (int i = tid; i < I; i += T) {
+                    float x[NCB];
+                    const float l = s.lse[i];
 #pragma unroll
                     for (int k = 0; k < NCB; ++k)
-                        if (EXACT || k < nc) sb += s.X[k * ld + i0 + r] * s.beta[k];
+                        x[k] = (EXACT || k < nc) ? ex2(s.gp[k] - s.C[k * ld + i] * sc - l) : 0.f;
+                    int q = 0;
+#pragma unroll
+                    for (int k = 0; k < NCB - 1; ++k) {
+#pragma unroll
+                        for (int m = k; m < NCB - 1; ++m, ++q) {
+                            if (EXACT || m < n) gram[q] += k == m ? x[k] * (1.f - x[k]) : -x[k] * x[m];
+                        }
+                    }
                 }
-                alpha[r] = hrow[r] - sb;
+                float* gout = s.out + 3 * ncp;
+                cta_reduce_vec<NG>(gram, NG, s.red, gout);
+                float* Af = reinterpret_cast<float*>(s.A);
+                float* rf = reinterpret_cast<float*>(s.rhs);
+                for (int idx = tid; idx < n * n; idx += T) {
+                    int k = idx / n, m = idx % n;
+                    if (k > m) { const int t = k; k = m; m = t; }
+                    Af[idx] = gout[k * (NCB - 1) - k * (k - 1) / 2 + (m - k)];
+                }
+                for (int k = tid; k < ncx; k += T) {
+                    if (k < n) rf[k] = s.out[k] - s.out[2 * ncp + k];
+                    s.beta[k] = 0.f;
+                }
+                __syncthreads();
+                if (warp == 0) warp_cholesky_solve_f32<NCB - 1>(Af, rf, n, s.Lt, s.beta, lane);
+                __syncthreads();
+            } else {
+                for (int pidx = warp; pidx < n * (n + 1) / 2; pidx += W) {
+                    int k = 0, rem = pidx;
+                    while (rem >= n - k) { rem -= n - k; ++k; }
+                    const int m = k + rem;
+                    const float* xk = s.X + k * ld;
+                    const float* xm = s.X + m * ld;
+                    float sum = 0.f;
+                    if (k == m) {
+                        for (int i = lane; i < I; i += 32) sum += xk[i] * (1.f - xk[i]);
+                    } else {
+                        for (int i = lane; i < I; i += 32) sum -= xk[i] * xm[i];
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
+                    if (lane == 0) {
+                        s.A[k * n + m] = (double)sum;
+                        s.A[m * n + k] = (double)sum;
+                    }
+                }
+                for (int k = tid; k < n; k += T)
+                    s.rhs[k] = (double)s.out[k] - (double)s.out[2 * ncp + k];
+                __syncthreads();
+                if (warp == 0) warp_cholesky_solve(s.A, s.rhs, n, lane);
+                __syncthreads();
+                for (int k = tid; k < ncx; k += T) s.beta[k] = k < n ? (float)s.rhs[k] : 0.f;
+                __syncthreads();
             }
+            // alpha_i = h_i - sum_k x_ik beta_k
+            for (int i = tid; i < I; i += T) {
+                const float l = s.lse[i];
+                float sb = 0.f;
+#pragma unroll
+                for (int k = 0; k < NCB; ++k)
+                    if (EXACT || k < nc) sb += ex2(s.gp[k] - s.C[k * ld + i] * sc - l) * s.beta[k];
+                s.alpha[i] = s.h[i] - sb;
+            }
+            __syncthreads();
+            // gradient and Adam over the tile, four consecutive items per step (float4)
+            const float step_size = s.coef[0], bc2s = s.coef[1];
+            const int g4 = ld / 4;
+            float* __restrict__ Cg = a.C;
+            float* __restrict__ m1g = a.m1;
+            float* __restrict__ m2g = a.m2;
             float gsq = 0.f;
+#pragma unroll 4
+            for (int q = tid; q < nc * g4; q += T) {
+                const int k = q / g4;
+                const int i = (q - k * g4) * 4;
+                if (i >= I) continue;
+                const float4 c4 = reinterpret_cast<const float4*>(s.C)[q];
+                const float4 l4 = reinterpret_cast<const float4*>(s.lse)[i / 4];
+                const float4 a4 = reinterpret_cast<const float4*>(s.alpha)[i / 4];
+                const float4 o4 = reinterpret_cast<const float4*>(s.om)[i / 4];
+                const float4 r4 = reinterpret_cast<const float4*>(s.r)[i / 4];
+                const float gpk = s.gp[k], ek = s.e[k], bk = s.beta[k];
+                float cv[4] = {c4.x, c4.y, c4.z, c4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
+                float av[4] = {a4.x, a4.y, a4.z, a4.w};
+                float wv[4] = {o4.x * r4.x, o4.y * r4.y, o4.z * r4.z, o4.w * r4.w};
+                float gr[4];
 #pragma unroll
-            for (int k = 0; k < NCB; ++k) {
-                if (!(EXACT || k < nc) || !any_row) continue;
-                float xk[R], gr[R];
-                ldv<R>(xk, s.X + k * ld + i0);
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    gr[r] = vr[r] ? -a.inv_eps * xk[r] * (wr[r] * s.e[k] - alpha[r] - s.beta[k]) : 0.f;
-                    gsq += gr[r] * gr[r];
+                for (int j = 0; j < 4; ++j) {
+                    const bool valid = i + j < I;
+                    const float x = valid ? ex2(gpk - cv[j] * sc - lv[j]) : 0.f;
+                    gr[j] = valid ? -a.inv_eps * x * (wv[j] * ek - av[j] - bk) : 0.f;
+                    gsq += gr[j] * gr[j];
                 }
                 if constexpr (MODE == MODE_GRAD) {
 #pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        if (vr[r]) a.dC[((size_t)u * I + i0 + r) * nc + k] = gr[r];
+                    for (int j = 0; j < 4; ++j)
+                        if (i + j < I) a.dC[((size_t)u * I + i + j) * nc + k] = gr[j];
                 } else {
-                    const size_t off = tile + (size_t)k * ld + i0;
+                    const size_t off = tile + (size_t)q * 4;
                     if (a.optimizer == 1) {
 #pragma unroll
-                        for (int r = 0; r < R; ++r) c[r][k] += a.lr * gr[r];
+                        for (int j = 0; j < 4; ++j) cv[j] += a.lr * gr[j];
                     } else {
-                        float mm[R], vv[R];
-                        ldv<R>(mm, a.m1 + off);
-                        ldv<R>(vv, a.m2 + off);
+                        const float4 mm4 = *reinterpret_cast<const float4*>(m1g + off);
+                        const float4 vv4 = *reinterpret_cast<const float4*>(m2g + off);
+                        float mm[4] = {mm4.x, mm4.y, mm4.z, mm4.w};
+                        float vv[4] = {vv4.x, vv4.y, vv4.z, vv4.w};
 #pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            mm[r] = a.beta1 * mm[r] + (1.f - a.beta1) * gr[r];
-                            vv[r] = a.beta2 * vv[r] + (1.f - a.beta2) * gr[r] * gr[r];
-                            c[r][k] += step_size * mm[r] / (sqrtf(vv[r]) / bc2s + a.adam_eps);
+                        for (int j = 0; j < 4; ++j) {
+                            mm[j] = a.beta1 * mm[j] + (1.f - a.beta1) * gr[j];
+                            vv[j] = a.beta2 * vv[j] + (1.f - a.beta2) * gr[j] * gr[j];
+                            cv[j] += step_size * mm[j] / (sqrtf(vv[j]) / bc2s + a.adam_eps);
                         }
-                        stv<R>(a.m1 + off, mm);
-                        stv<R>(a.m2 + off, vv);
+                        *reinterpret_cast<float4*>(m1g + off) = make_float4(mm[0], mm[1], mm[2], mm[3]);
+                        *reinterpret_cast<float4*>(m2g + off) = make_float4(vv[0], vv[1], vv[2], vv[3]);
                     }
-                    float cw[R];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) cw[r] = c[r][k];
-                    stv<R>(a.C + off, cw);
+                    const float4 cn = make_float4(cv[0], cv[1], cv[2], cv[3]);
+                    *reinterpret_cast<float4*>(Cg + off) = cn;
+                    reinterpret_cast<float4*>(s.C)[q] = cn;
                 }
             }
             gn2 += (double)gsq;
             if constexpr (MODE == MODE_GRAD) {
                 if (a.dr) {
                     // dF/dr(u,i) = (dF/dImp_i) sum_{k<K} e_k x_ik (C does not depend on r)
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        if (!vr[r]) continue;
-                        float v = 0.f;
-#pragma unroll
-                        for (int k = 0; k < NCB; ++k)
-                            if ((EXACT || k < nc) && k < a.K) v += s.e[k] * s.X[k * ld + i0 + r];
-                        a.dr[(size_t)u * I + i0 + r] = om[r] * v;
-                    }
+                    for (int i = tid; i < I; i += T) a.dr[(size_t)u * I + i] = s.om[i] * s.vimp[i];
                 }
                 __syncthreads();
+                if (tid == 0) stage_consumer(a, u + gridDim.x, nc, ld, s, false);
                 continue;  // no solve in gradient mode
             }
-            __syncthreads();  // s.X / s.beta reused by the next consumer
+            __syncthreads();  // updated tile visible
         }
 
         // ---------------- Sinkhorn solve on the consumer's (new) costs ----------------------------
+        float rr[R];
+        bool vr[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            float M = -INFINITY;
+        for (int r = 0; r < R; ++r) rr[r] = 0.f;
+        if (any_row) ldv<R>(rr, s.r + i0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) vr[r] = i0 + r < I;
+        float c[R][NCB];
+        {
+            float gk[NCB];
+            bcast_g<NCB, GPL>(gm, gk);
 #pragma unroll
             for (int k = 0; k < NCB; ++k) {
-                if (EXACT || k < nc) {
-                    c[r][k] *= a.inv_eps_ln2;
-                    M = fmaxf(M, s.g[k] - c[r][k]);
-                } else {
-                    c[r][k] = INFINITY;  // padding column: 2^(-inf) = 0
-                }
+                float tmp[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) tmp[r] = 0.f;
+                if ((EXACT || k < nc) && any_row) ldv<R>(tmp, s.C + k * ld + i0);
+#pragma unroll
+                for (int r = 0; r < R; ++r) c[r][k] = tmp[r];
             }
 #pragma unroll
-            for (int k = 0; k < NCB; ++k)
-                if (EXACT || k < nc) c[r][k] += vr[r] ? M : 0.f;
-        }
-        for (int l = 0; l < a.L; ++l) {
-            const bool last = l == a.L - 1;
-            if (last && tid < nc) a.gP[(size_t)u * nc + tid] = s.g[tid];
-            float gk[NCB];
-#pragma unroll
-            for (int k = 0; k < NCB; ++k) gk[k] = (EXACT || k < nc) ? s.g[k] : 0.f;
-            float cs[1][NCB];
-#pragma unroll
-            for (int k = 0; k < NCB; ++k) cs[0][k] = 0.f;
-#pragma unroll
             for (int r = 0; r < R; ++r) {
-                if (!vr[r]) continue;
-                float p[NCB];
-                float S = 0.f;
-#pragma unroll
-                for (int k = 0; k < NCB; ++k) {
-                    p[k] = ex2(gk[k] - c[r][k]);
-                    S += p[k];
-                }
-                if (!(S >= 0x1p-64f && S <= 0x1p64f)) {  // re-shift this row exactly
-                    float M = -INFINITY;
+                float M = 0.f;
+                if (vr[r]) {
+                    M = -INFINITY;
 #pragma unroll
                     for (int k = 0; k < NCB; ++k)
-                        if (EXACT || k < nc) M = fmaxf(M, gk[k] - c[r][k]);
-                    S = 0.f;
+                        if (EXACT || k < nc) M = fmaxf(M, gk[k] - c[r][k] * sc);
+                }
+#pragma unroll
+                for (int k = 0; k < NCB; ++k)
+                    c[r][k] = (vr[r] && (EXACT || k < nc)) ? c[r][k] * sc + M : INFINITY;
+            }
+        }
+        if constexpr (PAIR) {
+            constexpr int RP = R / 2;
+            f2 c2[RP][NCB];
+#pragma unroll
+            for (int rp = 0; rp < RP; ++rp)
+#pragma unroll
+                for (int k = 0; k < NCB; ++k) c2[rp][k] = pk(c[2 * rp][k], c[2 * rp + 1][k]);
+            for (int l = 0; l < a.L; ++l) {
+                const bool last = l == a.L - 1;
+                if (last && warp == 0) {
+#pragma unroll
+                    for (int j = 0; j < GPL; ++j)
+                        if (j * 32 + lane < nc) a.gP[(size_t)u * nc + j * 32 + lane] = gm[j];
+                }
+                f2 g2[NCB];
+                {
+                    float gk[NCB];
+                    bcast_g<NCB, GPL>(gm, gk);
+#pragma unroll
+                    for (int k = 0; k < NCB; ++k) g2[k] = pk(gk[k], gk[k]);
+                }
+                f2 cs2[NCB];
+#pragma unroll
+                for (int k = 0; k < NCB; ++k) cs2[k] = 0ull;
+#pragma unroll
+                for (int rp = 0; rp < RP; ++rp) {
+                    const bool v0 = vr[2 * rp], v1 = vr[2 * rp + 1];
+                    f2 p2[NCB];
+                    f2 S2 = 0ull;
 #pragma unroll
                     for (int k = 0; k < NCB; ++k) {
-                        if (EXACT || k < nc) c[r][k] += M;
+                        float d0, d1;
+                        upk(sub2(g2[k], c2[rp][k]), d0, d1);
+                        p2[k] = pk(ex2(d0), ex2(d1));
+                        S2 = add2(S2, p2[k]);
+                    }
+                    float S0, S1;
+                    upk(S2, S0, S1);
+                    const bool bad0 = v0 && !(S0 >= 0x1p-64f && S0 <= 0x1p64f);
+                    const bool bad1 = v1 && !(S1 >= 0x1p-64f && S1 <= 0x1p64f);
+                    if (bad0 || bad1) {  // re-shift the pair's rows exactly
+                        float M0 = -INFINITY, M1 = -INFINITY;
+#pragma unroll
+                        for (int k = 0; k < NCB; ++k) {
+                            if (EXACT || k < nc) {
+                                float gkk, gdup, c0, c1;
+                                upk(g2[k], gkk, gdup);
+                                upk(c2[rp][k], c0, c1);
+                                M0 = fmaxf(M0, gkk - c0);
+                                M1 = fmaxf(M1, gkk - c1);
+                            }
+                        }
+                        const f2 M2 = pk(bad0 ? M0 : 0.f, bad1 ? M1 : 0.f);
+                        S2 = 0ull;
+#pragma unroll
+                        for (int k = 0; k < NCB; ++k) {
+                            if (EXACT || k < nc) c2[rp][k] = add2(c2[rp][k], M2);
+                            float d0, d1;
+                            upk(sub2(g2[k], c2[rp][k]), d0, d1);
+                            p2[k] = pk(ex2(d0), ex2(d1));
+                            S2 = add2(S2, p2[k]);
+                        }
+                        upk(S2, S0, S1);
+                    }
+                    const float inv0 = v0 ? rcp_approx(S0) : 0.f;
+                    const float inv1 = v1 ? rcp_approx(S1) : 0.f;
+                    const f2 inv2 = pk(inv0, inv1);
+#pragma unroll
+                    for (int k = 0; k < NCB; ++k) cs2[k] = fma2(p2[k], inv2, cs2[k]);
+                    if (last) {
+                        float w0 = 0.f, w1 = 0.f;
+#pragma unroll
+                        for (int k = 0; k < NCB; ++k) {
+                            if (k < a.K) {
+                                float p0, p1;
+                                upk(p2[k], p0, p1);
+                                w0 += s.e[k] * p0;
+                                w1 += s.e[k] * p1;
+                            }
+                        }
+                        acc_imp[2 * rp] += rr[2 * rp] * (w0 * inv0);
+                        acc_imp[2 * rp + 1] += rr[2 * rp + 1] * (w1 * inv1);
+                    }
+                }
+                float cs[NCB];
+#pragma unroll
+                for (int k = 0; k < NCB; ++k) {
+                    float lo, hi;
+                    upk(cs2[k], lo, hi);
+                    cs[k] = lo + hi;
+                }
+                column_update<NCB, GPL>(cs, gm, nc, s.red, s.l2b, par, lane, warp, W);
+                par ^= 1;
+                if (l == 0 && tid == 0)
+                    stage_consumer(a, u + gridDim.x, nc, ld, s, MODE == MODE_UPDATE_SWEEP && a.optimizer == 0);
+            }
+        } else {
+            for (int l = 0; l < a.L; ++l) {
+                const bool last = l == a.L - 1;
+                if (last && warp == 0) {
+#pragma unroll
+                    for (int j = 0; j < GPL; ++j)
+                        if (j * 32 + lane < nc) a.gP[(size_t)u * nc + j * 32 + lane] = gm[j];
+                }
+                float gk[NCB];
+                bcast_g<NCB, GPL>(gm, gk);
+                float cs[NCB];
+#pragma unroll
+                for (int k = 0; k < NCB; ++k) cs[k] = 0.f;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (!vr[r]) continue;
+                    float p[NCB];
+                    float S = 0.f;
+#pragma unroll
+                    for (int k = 0; k < NCB; ++k) {
                         p[k] = ex2(gk[k] - c[r][k]);
                         S += p[k];
                     }
-                }
-                const float inv = rcp_approx(S);
+                    if (!(S >= 0x1p-64f && S <= 0x1p64f)) {
+                        float M = -INFINITY;
 #pragma unroll
-                for (int k = 0; k < NCB; ++k) cs[0][k] += p[k] * inv;
-                if (last) {
-                    float v = 0.f;
+                        for (int k = 0; k < NCB; ++k)
+                            if (EXACT || k < nc) M = fmaxf(M, gk[k] - c[r][k]);
+                        S = 0.f;
 #pragma unroll
-                    for (int k = 0; k < NCB; ++k)
-                        if (k < a.K) v += s.e[k] * p[k];
-                    acc_imp[r] += rr[r] * (v * inv);
+                        for (int k = 0; k < NCB; ++k) {
+                            if (EXACT || k < nc) c[r][k] += M;
+                            p[k] = ex2(gk[k] - c[r][k]);
+                            S += p[k];
+                        }
+                    }
+                    const float inv = rcp_approx(S);
+#pragma unroll
+                    for (int k = 0; k < NCB; ++k) cs[k] += p[k] * inv;
+                    if (last) {
+                        float v = 0.f;
+#pragma unroll
+                        for (int k = 0; k < NCB; ++k)
+                            if (k < a.K) v += s.e[k] * p[k];
+                        acc_imp[r] += rr[r] * (v * inv);
+                    }
                 }
+                column_update<NCB, GPL>(cs, gm, nc, s.red, s.l2b, par, lane, warp, W);
+                par ^= 1;
+                if (l == 0 && tid == 0)
+                    stage_consumer(a, u + gridDim.x, nc, ld, s, MODE == MODE_UPDATE_SWEEP && a.optimizer == 0);
             }
-            cta_reduce<NCB, 1>(cs, nc, s.red, s.out, ncp);
-            if (tid < nc) s.g[tid] += s.l2b[tid] - log2f(fmaxf(s.out[tid], 1e-37f));
-            __syncthreads();
         }
-        if (tid < nc) a.gL[(size_t)u * nc + tid] = s.g[tid];
-        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int j = 0; j < GPL; ++j)
+                if (j * 32 + lane < nc) a.gL[(size_t)u * nc + j * 32 + lane] = gm[j];
+        }
     }
 
     if constexpr (MODE != MODE_GRAD) {
@@ -407,8 +735,8 @@ __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
     }
     if constexpr (MODE == MODE_UPDATE_SWEEP) {
         // CTA sum of the squared gradient in double, fixed order
-        double* s_d = reinterpret_cast<double*>(s.red);
         __syncthreads();
+        double* s_d = reinterpret_cast<double*>(s.red);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) gn2 += __shfl_xor_sync(FULL, gn2, o);
         if (lane == 0) s_d[warp] = gn2;
@@ -438,7 +766,7 @@ P1Variant make_variant(int threads) {
 }  // namespace
 
 size_t p1_smem_bytes(const P1Variant& v, int mode, int nc, int ld) {
-    return smem_layout(nc, ld, v.threads / 32, pow2ceil(v.ncb), mode, nullptr, nullptr);
+    return smem_layout(v.ncb, nc, ld, v.threads / 32, mode, nullptr, nullptr);
 }
 
 // Compiled variants: exact column counts for the hot shapes, padded buckets for the rest.

@@ -250,7 +250,7 @@ class FairRank:
         return dict(zip(["utility", "mean_envy", "better_pct", "worse_pct"], [v.value for v in vals]))
 
     def time_kernels(self, n_steps: int):
-        ms = np.zeros(2)
+        ms = np.zeros(3)
         self._check(lib().fr_time_kernels(self.h, n_steps, ms.ctypes.data_as(_dp)))
         return ms
 
