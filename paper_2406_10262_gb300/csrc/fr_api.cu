@@ -2,7 +2,8 @@
 //
 // Host side of Algorithm 1: argument checking, device memory, stream ordering and the CUDA graphs
 // that replay chunks of ascent steps. Every step of the method itself runs in the kernels of
-// fr_p1.cu (Sinkhorn, impacts, gradient, Adam) and fr_common.cu (cross-consumer reduction).
+// fr_p1.cu (free costs: Sinkhorn, impacts, gradient, Adam), fr_p2*.cu (per-item variables) and
+// fr_common.cu (cross-consumer reduction).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,15 +26,24 @@ constexpr int kChunk = 16;  // ascent steps per captured graph
 
 struct fr_ctx {
     fr_config cfg;
+    bool p2 = false;  // per-item parametrisation
     int U = 0, I = 0, K = 0, nc = 0, ld = 0, G = 0, nblk = 0;
     int device = 0;
     cudaStream_t user = nullptr;  // caller's stream (may be the legacy default stream)
     cudaStream_t s = nullptr;     // library stream (non-blocking), joined to `user` per call
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     P1Variant var{};
-    float *C = nullptr, *m1 = nullptr, *m2 = nullptr, *gL = nullptr, *gP = nullptr;
-    float *r = nullptr, *e = nullptr, *log2b = nullptr, *omega = nullptr, *part = nullptr;
-    float* tmp = nullptr;  // staging for host transfers (U*I*nc floats)
+    P2Variant var2{};
+    int r_bf16 = 0;
+    float emax = 0.f;
+    // free costs: C, Adam moments [U][nc][ld]; per-item: theta, moments, w = exp(theta) [ld]
+    float *C = nullptr, *m1 = nullptr, *m2 = nullptr;
+    float *theta = nullptr, *tm1 = nullptr, *tm2 = nullptr, *w = nullptr, *gpart = nullptr;
+    double *ad_blk = nullptr, *gn2_one = nullptr;
+    float *gL = nullptr, *gP = nullptr, *e = nullptr, *log2b = nullptr, *omega = nullptr,
+          *part = nullptr;
+    void* r = nullptr;  // [U][ld] float or bfloat16
+    float* tmp = nullptr;  // staging for host transfers
     size_t tmp_bytes = 0;
     double *gn2_part = nullptr, *imp = nullptr, *blk = nullptr, *F_hist = nullptr, *gn_hist = nullptr;
     int hist_cap = 0;
@@ -87,7 +97,7 @@ P1Args p1_args(fr_ctx* c) {
     a.U = c->U; a.I = c->I; a.K = c->K; a.nc = c->nc; a.ld = c->ld;
     a.L = c->cfg.sinkhorn_iters; a.G = c->G;
     a.C = c->C; a.m1 = c->m1; a.m2 = c->m2; a.gL = c->gL; a.gP = c->gP;
-    a.r = c->r; a.e = c->e; a.log2b = c->log2b; a.omega = c->omega;
+    a.r = static_cast<const float*>(c->r); a.e = c->e; a.log2b = c->log2b; a.omega = c->omega;
     a.part = c->part; a.gn2_part = c->gn2_part; a.st = c->st;
     a.inv_eps_ln2 = (float)(1.0 / (c->cfg.epsilon * std::log(2.0)));
     a.inv_eps = (float)(1.0 / c->cfg.epsilon);
@@ -98,29 +108,82 @@ P1Args p1_args(fr_ctx* c) {
     return a;
 }
 
-ReduceArgs red_args(fr_ctx* c, int after_update) {
-    ReduceArgs a{};
-    a.I = c->I; a.ld = c->ld; a.G = c->G; a.U = c->U;
-    a.part = c->part; a.gn2_part = c->gn2_part; a.imp = c->imp; a.omega = c->omega;
-    a.blk = c->blk; a.st = c->st; a.F_hist = c->F_hist; a.gn_hist = c->gn_hist;
-    a.hist_cap = c->hist_cap; a.after_update = after_update;
+P2Args p2_args(fr_ctx* c, float* part) {
+    P2Args a{};
+    a.U = c->U; a.I = c->I; a.K = c->K; a.nc = c->nc; a.ld = c->ld;
+    a.L = c->cfg.sinkhorn_iters; a.G = c->G;
+    a.r = c->r; a.r_bf16 = c->r_bf16; a.w = c->w; a.e = c->e; a.log2b = c->log2b;
+    a.emax = c->emax; a.gL = c->gL; a.gP = c->gP; a.part = part; a.omega = c->omega;
+    a.dr = nullptr; a.st = c->st;
+    a.inv_eps_ln2 = (float)(1.0 / (c->cfg.epsilon * std::log(2.0)));
+    a.inv_eps = (float)(1.0 / c->cfg.epsilon);
+    a.warm = c->cfg.warm_start ? 1 : 0;
     return a;
 }
 
-fr_status launch_one_step(fr_ctx* ctx) {
-    CU(p1_launch(ctx->var, MODE_UPDATE_SWEEP, p1_args(ctx), ctx->s));
-    CU(reduce_launch(red_args(ctx, 1), ctx->s));
+P2AdamArgs adam_args(fr_ctx* c, int apply, float* dtheta_out) {
+    P2AdamArgs a{};
+    a.I = c->I; a.ld = c->ld; a.G = c->G; a.part = c->gpart;
+    a.theta = c->theta; a.m1 = c->tm1; a.m2 = c->tm2; a.w = c->w; a.dtheta_out = dtheta_out;
+    a.gn2_out = c->gn2_one; a.blk = c->ad_blk; a.st = c->st;
+    a.lr = (float)c->cfg.lr; a.beta1 = (float)c->cfg.beta1; a.beta2 = (float)c->cfg.beta2;
+    a.adam_eps = (float)c->cfg.adam_eps;
+    a.optimizer = c->cfg.optimizer == FR_SGD ? 1 : 0;
+    a.apply = apply;
+    return a;
+}
+
+ReduceArgs red_args(fr_ctx* c, int after_update) {
+    ReduceArgs a{};
+    a.I = c->I; a.ld = c->ld; a.G = c->G; a.U = c->U;
+    a.part = c->part; a.imp = c->imp; a.omega = c->omega;
+    a.blk = c->blk; a.st = c->st; a.F_hist = c->F_hist; a.gn_hist = c->gn_hist;
+    a.hist_cap = c->hist_cap; a.after_update = after_update;
+    if (c->p2) {
+        a.gn2_part = c->gn2_one;
+        a.Ggn = 1;
+    } else {
+        a.gn2_part = c->gn2_part;
+        a.Ggn = c->G;
+    }
+    return a;
+}
+
+// Sinkhorn for every consumer at the current parameters, then impacts and F.
+fr_status launch_solve(fr_ctx* ctx) {
+    if (ctx->p2)
+        CU(p2_launch_sweep(ctx->var2, p2_args(ctx, ctx->part), ctx->s));
+    else
+        CU(p1_launch(ctx->var, MODE_SWEEP, p1_args(ctx), ctx->s));
+    CU(reduce_launch(red_args(ctx, 0), ctx->s));
     ctx->launches += 2;
     return FR_OK;
 }
+
+// One ascent step of Algorithm 1: gradient at the current policy, update, Sinkhorn, impacts.
+fr_status launch_one_step(fr_ctx* ctx) {
+    if (ctx->p2) {
+        CU(p2_launch_grad(ctx->var2, p2_args(ctx, ctx->gpart), ctx->s));
+        CU(p2_launch_adam(adam_args(ctx, 1, nullptr), ctx->s));
+        CU(p2_launch_sweep(ctx->var2, p2_args(ctx, ctx->part), ctx->s));
+        ctx->launches += 3;
+    } else {
+        CU(p1_launch(ctx->var, MODE_UPDATE_SWEEP, p1_args(ctx), ctx->s));
+        ctx->launches += 1;
+    }
+    CU(reduce_launch(red_args(ctx, 1), ctx->s));
+    ctx->launches += 1;
+    return FR_OK;
+}
+
+int kernels_per_step(const fr_ctx* c) { return c->p2 ? 4 : 2; }
 
 fr_status ensure_fresh(fr_ctx* ctx) {
     if (!ctx->have_r || !ctx->have_e)
         return fail(ctx, FR_ESTATE, "set relevance and exposure first");
     if (ctx->fresh) return FR_OK;
-    CU(p1_launch(ctx->var, MODE_SWEEP, p1_args(ctx), ctx->s));
-    CU(reduce_launch(red_args(ctx, 0), ctx->s));
-    ctx->launches += 2;
+    fr_status st = launch_solve(ctx);
+    if (st != FR_OK) return st;
     ctx->fresh = true;
     return FR_OK;
 }
@@ -145,7 +208,7 @@ fr_status ensure_hist(fr_ctx* ctx, int n) {
 
 fr_status ensure_graph(fr_ctx* ctx) {
     if (ctx->chunk_exec) return FR_OK;
-    cudaGraph_t g;
+    cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(ctx->s, cudaStreamCaptureModeThreadLocal));
     const int64_t before = ctx->launches;
     for (int j = 0; j < kChunk; ++j) {
@@ -153,6 +216,7 @@ fr_status ensure_graph(fr_ctx* ctx) {
         if (st != FR_OK) {
             cudaStreamEndCapture(ctx->s, &g);
             if (g) cudaGraphDestroy(g);
+            ctx->launches = before;
             return st;
         }
     }
@@ -197,7 +261,7 @@ fr_status run_steps(fr_ctx* ctx, int n, bool check_stop) {
     }
     while (n - done >= kChunk) {
         CU(cudaGraphLaunch(ctx->chunk_exec, ctx->s));
-        ctx->launches += 2 * kChunk;
+        ctx->launches += (int64_t)kernels_per_step(ctx) * kChunk;
         done += kChunk;
         if (check_stop) {
             fr_status st = read_state(ctx);
@@ -225,10 +289,12 @@ fr_status ensure_tmp(fr_ctx* ctx, size_t bytes) {
 
 void free_all(fr_ctx* c) {
     if (c->chunk_exec) cudaGraphExecDestroy(c->chunk_exec);
-    float* fs[] = {c->C, c->m1, c->m2, c->gL, c->gP, c->r, c->e, c->log2b, c->omega, c->part, c->tmp};
+    float* fs[] = {c->C, c->m1, c->m2, c->theta, c->tm1, c->tm2, c->w, c->gpart, c->gL, c->gP,
+                   c->e, c->log2b, c->omega, c->part, c->tmp};
     for (float* p : fs) cudaFree(p);
-    double* ds[] = {c->gn2_part, c->imp, c->blk, c->F_hist, c->gn_hist};
+    double* ds[] = {c->gn2_part, c->imp, c->blk, c->F_hist, c->gn_hist, c->ad_blk, c->gn2_one};
     for (double* p : ds) cudaFree(p);
+    cudaFree(c->r);
     cudaFree(c->st);
     cudaFree(c->flags);
     if (c->st_host) cudaFreeHost(c->st_host);
@@ -237,11 +303,23 @@ void free_all(fr_ctx* c) {
     if (c->s) cudaStreamDestroy(c->s);
 }
 
+size_t nparam(const fr_ctx* c) {  // public parameter count
+    return c->p2 ? (size_t)c->I : (size_t)c->U * c->I * c->nc;
+}
+
 fr_status zero_state(fr_ctx* ctx) {
-    const size_t cells = (size_t)ctx->U * ctx->nc * ctx->ld;
-    CU(cudaMemsetAsync(ctx->C, 0, sizeof(float) * cells, ctx->s));
-    CU(cudaMemsetAsync(ctx->m1, 0, sizeof(float) * cells, ctx->s));
-    CU(cudaMemsetAsync(ctx->m2, 0, sizeof(float) * cells, ctx->s));
+    if (ctx->p2) {
+        CU(cudaMemsetAsync(ctx->theta, 0, sizeof(float) * ctx->ld, ctx->s));
+        CU(cudaMemsetAsync(ctx->tm1, 0, sizeof(float) * ctx->ld, ctx->s));
+        CU(cudaMemsetAsync(ctx->tm2, 0, sizeof(float) * ctx->ld, ctx->s));
+        CU(launch_exp_theta(ctx->theta, ctx->w, ctx->I, ctx->ld, ctx->s));
+        ctx->launches += 1;
+    } else {
+        const size_t cells = (size_t)ctx->U * ctx->nc * ctx->ld;
+        CU(cudaMemsetAsync(ctx->C, 0, sizeof(float) * cells, ctx->s));
+        CU(cudaMemsetAsync(ctx->m1, 0, sizeof(float) * cells, ctx->s));
+        CU(cudaMemsetAsync(ctx->m2, 0, sizeof(float) * cells, ctx->s));
+    }
     CU(cudaMemsetAsync(ctx->gL, 0, sizeof(float) * ctx->U * ctx->nc, ctx->s));
     CU(cudaMemsetAsync(ctx->gP, 0, sizeof(float) * ctx->U * ctx->nc, ctx->s));
     DevState z{};
@@ -303,30 +381,46 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
         return fail(nullptr, FR_EINVAL, "invalid optimiser hyper-parameters");
     if (c.optimizer != FR_ADAM && c.optimizer != FR_SGD)
         return fail(nullptr, FR_EINVAL, "unknown optimizer %d", c.optimizer);
-    if (c.param != FR_PARAM_FULL_C)
-        return fail(nullptr, FR_EUNSUPPORTED, "only FR_PARAM_FULL_C is compiled in this build");
+    if (c.param != FR_PARAM_FULL_C && c.param != FR_PARAM_ITEM)
+        return fail(nullptr, FR_EINVAL, "unknown param %d", c.param);
+    if (c.grad_mode != FR_GRAD_IMPLICIT && c.grad_mode != FR_GRAD_UNROLLED)
+        return fail(nullptr, FR_EINVAL, "unknown grad_mode %d", c.grad_mode);
     if (c.grad_mode != FR_GRAD_IMPLICIT)
-        return fail(nullptr, FR_EUNSUPPORTED, "FR_PARAM_FULL_C supports the implicit gradient only");
-    if (c.rel_dtype != FR_F32)
+        return fail(nullptr, FR_EUNSUPPORTED, "this build differentiates implicitly only");
+    if (c.rel_dtype != FR_F32 && c.rel_dtype != FR_BF16)
+        return fail(nullptr, FR_EINVAL, "rel_dtype must be FR_F32 or FR_BF16");
+    if (c.param == FR_PARAM_FULL_C && c.rel_dtype != FR_F32)
         return fail(nullptr, FR_EUNSUPPORTED, "FR_PARAM_FULL_C stores relevance in FP32");
     for (int j = 0; j < 7; ++j)
         if (c.reserved[j]) return fail(nullptr, FR_EINVAL, "reserved fields must be zero");
 
     const int nc = fr_num_cols(c.n_items, c.n_slots);
-    P1Variant var;
-    if (!p1_select(nc, c.n_items, &var))
+    const bool p2 = c.param == FR_PARAM_ITEM;
+    P1Variant var{};
+    P2Variant var2{};
+    if (p2) {
+        if (!p2_select(nc, c.n_items, &var2))
+            return fail(nullptr, FR_EUNSUPPORTED,
+                        "FR_PARAM_ITEM needs n_cols <= 32 and n_items <= 12288 (4096 unless "
+                        "n_cols is 6, 11 or 21); got n_cols %d, n_items %d",
+                        nc, c.n_items);
+    } else if (!p1_select(nc, c.n_items, &var)) {
         return fail(nullptr, FR_EUNSUPPORTED,
                     "FR_PARAM_FULL_C needs n_cols <= 64 and n_items <= 512 * rows per thread "
                     "(2048 for n_cols <= 16, 1024 for <= 32, 512 for <= 64); got n_cols %d, n_items %d",
                     nc, c.n_items);
+    }
     ctx = new fr_ctx();
     ctx->cfg = c;
+    ctx->p2 = p2;
     ctx->U = c.n_users;
     ctx->I = c.n_items;
     ctx->K = c.n_slots;
     ctx->nc = nc;
     ctx->ld = (c.n_items + 7) / 8 * 8;
     ctx->var = var;
+    ctx->var2 = var2;
+    ctx->r_bf16 = c.rel_dtype == FR_BF16 ? 1 : 0;
     ctx->user = (cudaStream_t)stream;
     auto bail = [&](fr_status st) {
         g_create_error = ctx->err;
@@ -346,44 +440,70 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
     CUC(cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming));
     CUC(cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming));
 
-    // shared memory and occupancy of the fused update+sweep kernel fix the persistent grid
-    int max_optin = 0, sms = 0;
+    // shared memory and occupancy fix the persistent grid G
+    int max_optin = 0, sms = 0, occ = 0;
     CUC(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
     CUC(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-    size_t smem_max = 0;
-    for (int m = 0; m < 3; ++m) {
-        size_t b = p1_smem_bytes(var, m, nc, ctx->ld);
+    auto set_smem = [&](const void* fn, size_t b) -> fr_status {
         if (b > (size_t)max_optin)
-            return bail(fail(ctx, FR_EUNSUPPORTED,
-                             "shared memory %zu B exceeds the device limit %d B: the free-cost "
-                             "parametrisation stages one consumer's n_items x n_cols cost tile "
-                             "(about n_items * (4 * n_cols + 20) bytes)",
-                             b, max_optin));
-        CUC(cudaFuncSetAttribute(var.fn[m], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b));
-        smem_max = b > smem_max ? b : smem_max;
+            return fail(ctx, FR_EUNSUPPORTED,
+                        "shared memory %zu B exceeds the device limit %d B for this shape", b,
+                        max_optin);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+        if (e != cudaSuccess) return fail(ctx, FR_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+        return FR_OK;
+    };
+    if (p2) {
+        const int esz = ctx->r_bf16 ? 2 : 4;
+        const size_t bs = p2_sweep_smem(var2, nc, ctx->ld, esz);
+        const size_t bg = p2_grad_smem(var2, nc, ctx->ld, esz);
+        fr_status st = set_smem(var2.sweep, bs);
+        if (st == FR_OK) st = set_smem(var2.grad, bg);
+        if (st != FR_OK) return bail(st);
+        int o1 = 0, o2 = 0;
+        CUC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, var2.sweep, var2.threads, bs));
+        CUC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, var2.grad, var2.threads, bg));
+        occ = std::min(o1, o2);
+    } else {
+        for (int m = 0; m < 3; ++m) {
+            fr_status st = set_smem(var.fn[m], p1_smem_bytes(var, m, nc, ctx->ld));
+            if (st != FR_OK) return bail(st);
+        }
+        CUC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, var.fn[MODE_UPDATE_SWEEP], var.threads,
+            p1_smem_bytes(var, MODE_UPDATE_SWEEP, nc, ctx->ld)));
     }
-    int occ = 0;
-    CUC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, var.fn[MODE_UPDATE_SWEEP], var.threads,
-        p1_smem_bytes(var, MODE_UPDATE_SWEEP, nc, ctx->ld)));
     if (occ < 1) return bail(fail(ctx, FR_EUNSUPPORTED, "kernel does not fit on an SM"));
     ctx->G = std::min(ctx->U, occ * sms);
     ctx->nblk = reduce_blocks(ctx->I);
 
-    const size_t cells = (size_t)ctx->U * nc * ctx->ld;
-    CUC(cudaMalloc(&ctx->C, sizeof(float) * cells));
-    CUC(cudaMalloc(&ctx->m1, sizeof(float) * cells));
-    CUC(cudaMalloc(&ctx->m2, sizeof(float) * cells));
+    const size_t ld = ctx->ld;
+    if (p2) {
+        CUC(cudaMalloc(&ctx->theta, sizeof(float) * ld));
+        CUC(cudaMalloc(&ctx->tm1, sizeof(float) * ld));
+        CUC(cudaMalloc(&ctx->tm2, sizeof(float) * ld));
+        CUC(cudaMalloc(&ctx->w, sizeof(float) * ld));
+        CUC(cudaMalloc(&ctx->gpart, sizeof(float) * (size_t)ctx->G * ld));
+        CUC(cudaMalloc(&ctx->ad_blk, sizeof(double) * p2_adam_blocks(ctx->I)));
+        CUC(cudaMalloc(&ctx->gn2_one, sizeof(double)));
+    } else {
+        const size_t cells = (size_t)ctx->U * nc * ld;
+        CUC(cudaMalloc(&ctx->C, sizeof(float) * cells));
+        CUC(cudaMalloc(&ctx->m1, sizeof(float) * cells));
+        CUC(cudaMalloc(&ctx->m2, sizeof(float) * cells));
+    }
+    const size_t rbytes = (size_t)ctx->U * ld * (ctx->r_bf16 ? 2 : 4);
+    CUC(cudaMalloc(&ctx->r, rbytes));
+    CUC(cudaMemset(ctx->r, 0, rbytes));
     CUC(cudaMalloc(&ctx->gL, sizeof(float) * ctx->U * nc));
     CUC(cudaMalloc(&ctx->gP, sizeof(float) * ctx->U * nc));
-    CUC(cudaMalloc(&ctx->r, sizeof(float) * (size_t)ctx->U * ctx->ld));
-    CUC(cudaMemset(ctx->r, 0, sizeof(float) * (size_t)ctx->U * ctx->ld));
     CUC(cudaMalloc(&ctx->e, sizeof(float) * nc));
     CUC(cudaMalloc(&ctx->log2b, sizeof(float) * nc));
-    CUC(cudaMalloc(&ctx->omega, sizeof(float) * ctx->ld));
-    CUC(cudaMalloc(&ctx->part, sizeof(float) * (size_t)ctx->G * ctx->ld));
+    CUC(cudaMalloc(&ctx->omega, sizeof(float) * ld));
+    CUC(cudaMemset(ctx->omega, 0, sizeof(float) * ld));
+    CUC(cudaMalloc(&ctx->part, sizeof(float) * (size_t)ctx->G * ld));
     CUC(cudaMalloc(&ctx->gn2_part, sizeof(double) * ctx->G));
-    CUC(cudaMalloc(&ctx->imp, sizeof(double) * ctx->ld));
+    CUC(cudaMalloc(&ctx->imp, sizeof(double) * ld));
     CUC(cudaMalloc(&ctx->blk, sizeof(double) * 2 * ctx->nblk));
     CUC(cudaMalloc(&ctx->st, sizeof(DevState)));
     CUC(cudaMalloc(&ctx->flags, sizeof(int) * 4));
@@ -429,15 +549,16 @@ fr_status fr_set_relevance(fr_ctx* ctx, const void* r, int32_t dtype, int64_t ld
         src = ctx->tmp;
         lds = ctx->I;
     }
-    CU(launch_relevance_import(src, dtype, lds, ctx->r, ctx->U, ctx->I, ctx->ld, ctx->s));
+    CU(launch_relevance_import(src, dtype, lds, ctx->r, ctx->r_bf16, ctx->U, ctx->I, ctx->ld, ctx->s));
     CU(cudaMemsetAsync(ctx->flags, 0, sizeof(int) * 4, ctx->s));
-    CU(launch_relevance_check(ctx->r, ctx->U, ctx->I, ctx->ld, ctx->flags, ctx->s));
+    CU(launch_relevance_check(ctx->r, ctx->r_bf16, ctx->U, ctx->I, ctx->ld, ctx->flags, ctx->s));
     ctx->launches += 2;
     int hf[4];
     CU(cudaMemcpyAsync(hf, ctx->flags, sizeof hf, cudaMemcpyDeviceToHost, ctx->s));
     CU(cudaStreamSynchronize(ctx->s));
     if (hf[0]) return fail(ctx, FR_EINVAL, "relevance must be finite and >= 0");
-    if (hf[1]) return fail(ctx, FR_EINVAL, "%d items have no positive relevance (log Imp_i undefined)", hf[1]);
+    if (hf[1])
+        return fail(ctx, FR_EINVAL, "%d items have no positive relevance (log Imp_i undefined)", hf[1]);
     ctx->have_r = true;
     ctx->fresh = false;
     return FR_OK;
@@ -448,16 +569,19 @@ fr_status fr_set_exposure(fr_ctx* ctx, const double* e, int32_t K) {
     if (!e) return fail(ctx, FR_EINVAL, "e is NULL");
     if (K != ctx->K) return fail(ctx, FR_EINVAL, "K %d != n_slots %d", K, ctx->K);
     std::vector<float> ep(ctx->nc, 0.f), lb(ctx->nc, 0.f);
+    float emax = 0.f;
     for (int k = 0; k < K; ++k) {
         if (!(e[k] > 0.0) || !std::isfinite(e[k]))
             return fail(ctx, FR_EINVAL, "exposure e[%d] must be positive and finite", k);
         ep[k] = (float)e[k];
+        emax = std::max(emax, ep[k]);
     }
     if (ctx->nc > K) lb[K] = (float)std::log2((double)(ctx->I - K));  // dummy mass |I| - K
     Join j(ctx);
     CU(cudaMemcpyAsync(ctx->e, ep.data(), sizeof(float) * ctx->nc, cudaMemcpyHostToDevice, ctx->s));
     CU(cudaMemcpyAsync(ctx->log2b, lb.data(), sizeof(float) * ctx->nc, cudaMemcpyHostToDevice, ctx->s));
     CU(cudaStreamSynchronize(ctx->s));
+    ctx->emax = emax;
     ctx->have_e = true;
     ctx->fresh = false;
     return FR_OK;
@@ -523,11 +647,12 @@ fr_status fr_policy(fr_ctx* ctx, int32_t u0, int32_t n_u, float* x_out, int32_t 
         if ((st = ensure_tmp(ctx, bytes)) != FR_OK) return st;
         dst = ctx->tmp;
     }
-    CU(launch_policy(p1_args(ctx), u0, n_u, dst, ctx->s));
+    if (ctx->p2)
+        CU(launch_p2_policy(p2_args(ctx, ctx->part), u0, n_u, dst, ctx->s));
+    else
+        CU(launch_policy(p1_args(ctx), u0, n_u, dst, ctx->s));
     ctx->launches += n_u > 0;
-    if (!on_device && n_u > 0) {
-        CU(cudaMemcpyAsync(x_out, dst, bytes, cudaMemcpyDeviceToHost, ctx->s));
-    }
+    if (!on_device && n_u > 0) CU(cudaMemcpyAsync(x_out, dst, bytes, cudaMemcpyDeviceToHost, ctx->s));
     CU(cudaStreamSynchronize(ctx->s));
     return FR_OK;
 }
@@ -538,24 +663,37 @@ fr_status fr_grad(fr_ctx* ctx, const float* omega, float* dparam, float* dr, int
     Join j(ctx);
     fr_status st = ensure_fresh(ctx);
     if (st != FR_OK) return st;
-    const size_t nC = (size_t)ctx->U * ctx->I * ctx->nc, nr = (size_t)ctx->U * ctx->I;
-    // staging: [omega (ld) | dC (nC) | dr (nr)]
-    const size_t need = sizeof(float) * (ctx->ld + (on_device ? 0 : nC + nr));
+    const size_t nP = nparam(ctx), nr = (size_t)ctx->U * ctx->I;
+    // staging: [omega (ld) | dparam (nP) | dr (nr)]
+    const size_t need = sizeof(float) * (ctx->ld + (on_device ? 0 : nP + nr));
     if ((st = ensure_tmp(ctx, need)) != FR_OK) return st;
-    P1Args a = p1_args(ctx);
+    const float* om = ctx->omega;
     if (omega) {
         CU(cudaMemsetAsync(ctx->tmp, 0, sizeof(float) * ctx->ld, ctx->s));
         CU(cudaMemcpyAsync(ctx->tmp, omega, sizeof(float) * ctx->I,
                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->s));
-        a.omega = ctx->tmp;
+        om = ctx->tmp;
     }
-    a.dC = on_device ? dparam : ctx->tmp + ctx->ld;
-    a.dr = dr ? (on_device ? dr : ctx->tmp + ctx->ld + nC) : nullptr;
-    CU(p1_launch(ctx->var, MODE_GRAD, a, ctx->s));
-    ctx->launches += 1;
+    float* dP = on_device ? dparam : ctx->tmp + ctx->ld;
+    float* dR = dr ? (on_device ? dr : ctx->tmp + ctx->ld + nP) : nullptr;
+    if (ctx->p2) {
+        P2Args a = p2_args(ctx, ctx->gpart);
+        a.omega = om;
+        a.dr = dR;
+        CU(p2_launch_grad(ctx->var2, a, ctx->s));
+        CU(p2_launch_adam(adam_args(ctx, 0, dP), ctx->s));
+        ctx->launches += 2;
+    } else {
+        P1Args a = p1_args(ctx);
+        a.omega = om;
+        a.dC = dP;
+        a.dr = dR;
+        CU(p1_launch(ctx->var, MODE_GRAD, a, ctx->s));
+        ctx->launches += 1;
+    }
     if (!on_device) {
-        CU(cudaMemcpyAsync(dparam, a.dC, sizeof(float) * nC, cudaMemcpyDeviceToHost, ctx->s));
-        if (dr) CU(cudaMemcpyAsync(dr, a.dr, sizeof(float) * nr, cudaMemcpyDeviceToHost, ctx->s));
+        CU(cudaMemcpyAsync(dparam, dP, sizeof(float) * nP, cudaMemcpyDeviceToHost, ctx->s));
+        if (dr) CU(cudaMemcpyAsync(dr, dR, sizeof(float) * nr, cudaMemcpyDeviceToHost, ctx->s));
     }
     CU(cudaStreamSynchronize(ctx->s));
     return FR_OK;
@@ -566,26 +704,36 @@ fr_status fr_set_state(fr_ctx* ctx, const float* param, const float* m1, const f
     if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
     if (t < 0) return fail(ctx, FR_EINVAL, "t < 0");
     Join j(ctx);
-    const size_t nC = (size_t)ctx->U * ctx->I * ctx->nc;
+    const size_t nP = nparam(ctx);
     const float* srcs[3] = {param, m1, m2};
-    float* dsts[3] = {ctx->C, ctx->m1, ctx->m2};
-    fr_status st = ensure_tmp(ctx, sizeof(float) * nC);
+    float* dsts[3] = {ctx->p2 ? ctx->theta : ctx->C, ctx->p2 ? ctx->tm1 : ctx->m1,
+                      ctx->p2 ? ctx->tm2 : ctx->m2};
+    fr_status st = ensure_tmp(ctx, sizeof(float) * std::max(nP, (size_t)ctx->U * ctx->nc));
     if (st != FR_OK) return st;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     for (int q = 0; q < 3; ++q) {
         if (!srcs[q]) continue;
-        const float* src = srcs[q];
-        if (!on_device) {
-            CU(cudaMemcpyAsync(ctx->tmp, src, sizeof(float) * nC, cudaMemcpyHostToDevice, ctx->s));
-            src = ctx->tmp;
+        if (ctx->p2) {  // [I] vectors, padding stays zero
+            CU(cudaMemsetAsync(dsts[q], 0, sizeof(float) * ctx->ld, ctx->s));
+            CU(cudaMemcpyAsync(dsts[q], srcs[q], sizeof(float) * ctx->I, kind, ctx->s));
+        } else {
+            const float* src = srcs[q];
+            if (!on_device) {
+                CU(cudaMemcpyAsync(ctx->tmp, src, sizeof(float) * nP, kind, ctx->s));
+                src = ctx->tmp;
+            }
+            CU(launch_pack_ikn_to_kni(src, dsts[q], ctx->U, ctx->I, ctx->nc, ctx->ld, 1.f, ctx->s));
+            ctx->launches += 1;
         }
-        CU(launch_pack_ikn_to_kni(src, dsts[q], ctx->U, ctx->I, ctx->nc, ctx->ld, 1.f, ctx->s));
+    }
+    if (ctx->p2 && param) {
+        CU(launch_exp_theta(ctx->theta, ctx->w, ctx->I, ctx->ld, ctx->s));
         ctx->launches += 1;
     }
     if (g) {
         const float* src = g;
         if (!on_device) {
-            CU(cudaMemcpyAsync(ctx->tmp, g, sizeof(float) * ctx->U * ctx->nc, cudaMemcpyHostToDevice,
-                               ctx->s));
+            CU(cudaMemcpyAsync(ctx->tmp, g, sizeof(float) * ctx->U * ctx->nc, kind, ctx->s));
             src = ctx->tmp;
         }
         CU(launch_scale(src, ctx->gL, (long long)ctx->U * ctx->nc,
@@ -605,20 +753,24 @@ fr_status fr_get_state(fr_ctx* ctx, float* param, float* m1, float* m2, float* g
                        int32_t on_device) {
     if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
     Join j(ctx);
-    const size_t nC = (size_t)ctx->U * ctx->I * ctx->nc;
+    const size_t nP = nparam(ctx);
     float* dsts[3] = {param, m1, m2};
-    const float* srcs[3] = {ctx->C, ctx->m1, ctx->m2};
-    fr_status st = ensure_tmp(ctx, sizeof(float) * nC);
+    const float* srcs[3] = {ctx->p2 ? ctx->theta : ctx->C, ctx->p2 ? ctx->tm1 : ctx->m1,
+                            ctx->p2 ? ctx->tm2 : ctx->m2};
+    fr_status st = ensure_tmp(ctx, sizeof(float) * std::max(nP, (size_t)ctx->U * ctx->nc));
     if (st != FR_OK) return st;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     for (int q = 0; q < 3; ++q) {
         if (!dsts[q]) continue;
-        float* dst = on_device ? dsts[q] : ctx->tmp;
-        CU(launch_unpack_kni_to_ikn(srcs[q], dst, ctx->U, ctx->I, ctx->nc, ctx->ld, 1.f, ctx->s));
-        ctx->launches += 1;
-        if (!on_device) {
-            CU(cudaMemcpyAsync(dsts[q], dst, sizeof(float) * nC, cudaMemcpyDeviceToHost, ctx->s));
-            CU(cudaStreamSynchronize(ctx->s));
+        if (ctx->p2) {
+            CU(cudaMemcpyAsync(dsts[q], srcs[q], sizeof(float) * ctx->I, kind, ctx->s));
+        } else {
+            float* dst = on_device ? dsts[q] : ctx->tmp;
+            CU(launch_unpack_kni_to_ikn(srcs[q], dst, ctx->U, ctx->I, ctx->nc, ctx->ld, 1.f, ctx->s));
+            ctx->launches += 1;
+            if (!on_device) CU(cudaMemcpyAsync(dsts[q], dst, sizeof(float) * nP, kind, ctx->s));
         }
+        CU(cudaStreamSynchronize(ctx->s));
     }
     if (g) {
         float* dst = on_device ? g : ctx->tmp;
@@ -626,7 +778,7 @@ fr_status fr_get_state(fr_ctx* ctx, float* param, float* m1, float* m2, float* g
                         (float)(ctx->cfg.epsilon * std::log(2.0)), ctx->s));
         ctx->launches += 1;
         if (!on_device)
-            CU(cudaMemcpyAsync(g, dst, sizeof(float) * ctx->U * ctx->nc, cudaMemcpyDeviceToHost, ctx->s));
+            CU(cudaMemcpyAsync(g, dst, sizeof(float) * ctx->U * ctx->nc, kind, ctx->s));
     }
     CU(cudaMemcpyAsync(ctx->st_host, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->s));
     CU(cudaStreamSynchronize(ctx->s));
@@ -651,26 +803,41 @@ fr_status fr_time_kernels(fr_ctx* ctx, int32_t n_steps, double* ms) {
     cudaEvent_t ev[4];
     for (auto& e : ev) CU(cudaEventCreate(&e));
     double acc[3] = {0.0, 0.0, 0.0};
-    const P1Args pa = p1_args(ctx);
-    const ReduceArgs ra = red_args(ctx, 1);
     for (int s = 0; s < n_steps; ++s) {
         CU(cudaEventRecord(ev[0], ctx->s));
-        CU(p1_launch(ctx->var, MODE_UPDATE_SWEEP, pa, ctx->s));
-        CU(cudaEventRecord(ev[1], ctx->s));
-        CU(reduce_launch(ra, ctx->s));
-        CU(cudaEventRecord(ev[2], ctx->s));
-        CU(p1_launch(ctx->var, MODE_SWEEP, pa, ctx->s));  // Sinkhorn only, same costs
-        CU(cudaEventRecord(ev[3], ctx->s));
-        CU(reduce_launch(red_args(ctx, 0), ctx->s));
-        ctx->launches += 4;
-        CU(cudaEventSynchronize(ev[3]));
+        if (ctx->p2) {  // [gradient + theta update] [Sinkhorn] [reduction]
+            CU(p2_launch_grad(ctx->var2, p2_args(ctx, ctx->gpart), ctx->s));
+            CU(p2_launch_adam(adam_args(ctx, 1, nullptr), ctx->s));
+            CU(cudaEventRecord(ev[1], ctx->s));
+            CU(p2_launch_sweep(ctx->var2, p2_args(ctx, ctx->part), ctx->s));
+            CU(cudaEventRecord(ev[2], ctx->s));
+            CU(reduce_launch(red_args(ctx, 1), ctx->s));
+            CU(cudaEventRecord(ev[3], ctx->s));
+            ctx->launches += 4;
+        } else {  // [fused step] [reduction] [Sinkhorn only, same costs]
+            CU(p1_launch(ctx->var, MODE_UPDATE_SWEEP, p1_args(ctx), ctx->s));
+            CU(cudaEventRecord(ev[1], ctx->s));
+            CU(reduce_launch(red_args(ctx, 1), ctx->s));
+            CU(cudaEventRecord(ev[2], ctx->s));
+            CU(p1_launch(ctx->var, MODE_SWEEP, p1_args(ctx), ctx->s));
+            CU(cudaEventRecord(ev[3], ctx->s));
+            CU(reduce_launch(red_args(ctx, 0), ctx->s));
+            ctx->launches += 4;
+        }
+        CU(cudaStreamSynchronize(ctx->s));
         float a = 0.f, b = 0.f, c = 0.f;
         CU(cudaEventElapsedTime(&a, ev[0], ev[1]));
         CU(cudaEventElapsedTime(&b, ev[1], ev[2]));
         CU(cudaEventElapsedTime(&c, ev[2], ev[3]));
-        acc[0] += a;
-        acc[1] += b;
-        acc[2] += c;
+        if (ctx->p2) {
+            acc[0] += b;  // Sinkhorn kernel
+            acc[1] += c;  // reduction
+            acc[2] += a;  // gradient + theta update
+        } else {
+            acc[0] += a;
+            acc[1] += b;
+            acc[2] += c;
+        }
     }
     for (auto& e : ev) cudaEventDestroy(e);
     ms[0] = acc[0] / n_steps;

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(RED_ITEMS* RED_WARPS) reduce_kernel(const Redu
         S += __ldcg(a.blk + 2 * b + 1);
     }
     if (a.after_update)
-        for (int g = lane; g < a.G; g += 32) g2 += __ldcg(a.gn2_part + g);
+        for (int g = lane; g < a.Ggn; g += 32) g2 += __ldcg(a.gn2_part + g);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         F += __shfl_xor_sync(FULL, F, o);
@@ -125,7 +125,7 @@ __global__ void scale_kernel(const float* __restrict__ src, float* __restrict__ 
 }
 
 __global__ void relevance_import_kernel(const void* __restrict__ src, int dtype, long long ld_src,
-                                        float* __restrict__ dst, int U, int I, int ld) {
+                                        void* __restrict__ dst, int dst_bf16, int U, int I, int ld) {
     const long long n = (long long)U * ld;
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n;
          j += (long long)gridDim.x * blockDim.x) {
@@ -138,18 +138,23 @@ __global__ void relevance_import_kernel(const void* __restrict__ src, int dtype,
             else if (dtype == FR_F64) v = (float)static_cast<const double*>(src)[o];
             else v = __bfloat162float(static_cast<const __nv_bfloat16*>(src)[o]);
         }
-        dst[j] = v;
+        if (dst_bf16)
+            static_cast<__nv_bfloat16*>(dst)[j] = __float2bfloat16_rn(v);
+        else
+            static_cast<float*>(dst)[j] = v;
     }
 }
 
 // flags[0] |= 1 for a negative or non-finite value; flags[1] counts items without positive r
-__global__ void relevance_check_kernel(const float* __restrict__ r, int U, int I, int ld,
-                                       int* flags) {
+__global__ void relevance_check_kernel(const void* __restrict__ r, int r_bf16, int U, int I,
+                                       int ld, int* flags) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= I) return;
     bool bad = false, pos = false;
     for (int u = 0; u < U; ++u) {
-        const float v = r[(size_t)u * ld + i];
+        const size_t o = (size_t)u * ld + i;
+        const float v = r_bf16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(r)[o])
+                               : static_cast<const float*>(r)[o];
         bad |= !(v >= 0.f) || !isfinite(v);
         pos |= v > 0.f;
     }
@@ -222,16 +227,16 @@ cudaError_t launch_scale(const float* src, float* dst, long long n, float scale,
     return cudaGetLastError();
 }
 
-cudaError_t launch_relevance_import(const void* src, int dtype, long long ld_src, float* dst,
-                                    int U, int I, int ld, cudaStream_t s) {
+cudaError_t launch_relevance_import(const void* src, int dtype, long long ld_src, void* dst,
+                                    int dst_bf16, int U, int I, int ld, cudaStream_t s) {
     relevance_import_kernel<<<grid_for((long long)U * ld), 256, 0, s>>>(src, dtype, ld_src, dst,
-                                                                         U, I, ld);
+                                                                         dst_bf16, U, I, ld);
     return cudaGetLastError();
 }
 
-cudaError_t launch_relevance_check(const float* r, int U, int I, int ld, int* flags,
+cudaError_t launch_relevance_check(const void* r, int r_bf16, int U, int I, int ld, int* flags,
                                    cudaStream_t s) {
-    relevance_check_kernel<<<(I + 127) / 128, 128, 0, s>>>(r, U, I, ld, flags);
+    relevance_check_kernel<<<(I + 127) / 128, 128, 0, s>>>(r, r_bf16, U, I, ld, flags);
     return cudaGetLastError();
 }
 

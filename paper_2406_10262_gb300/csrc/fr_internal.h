@@ -62,6 +62,7 @@ struct P1Args {
 
 struct ReduceArgs {
     int I, ld, G, U;
+    int Ggn;              // number of squared-gradient-norm partials (G for the free-cost path)
     const float* part;
     const double* gn2_part;
     double* imp;
@@ -73,6 +74,63 @@ struct ReduceArgs {
     int hist_cap;
     int after_update;     // 1 if the sweep followed an optimiser update
 };
+
+// ---- per-item parametrisation c_uik = -r(u,i) e_k exp(theta_i) ----------------------------------
+struct P2Args {
+    int U, I, K, nc, ld, L, G;
+    const void* r;        // [U][ld] relevance, float or bfloat16 (r_bf16)
+    int r_bf16;
+    const float* w;       // [ld] exp(theta)
+    const float* e;       // [nc] exposure, dummy = 0
+    const float* log2b;   // [nc]
+    float emax;           // max_k e_k
+    float* gL;            // [U][nc] log2-unit potentials (re-referenced to the last column)
+    float* gP;
+    float* part;          // [G][ld] per-CTA impact partials (sweep) or dL/dtheta partials (grad)
+    const float* omega;   // [ld] dL/dImp_i (grad)
+    float* dr;            // grad: dL/dr [U][I] (nullable)
+    DevState* st;
+    float inv_eps_ln2, inv_eps;
+    int warm;
+};
+
+struct P2Variant {
+    int ncb, rows, exact, threads;
+    const void* sweep;
+    const void* grad;
+};
+
+// dL/dtheta from the per-CTA partials (FP64, fixed order), its squared norm, and optionally the
+// optimiser step on theta (w = exp(theta) refreshed).
+struct P2AdamArgs {
+    int I, ld, G;
+    const float* part;    // [G][ld]
+    float* theta;
+    float* m1;
+    float* m2;
+    float* w;
+    float* dtheta_out;    // nullable: dL/dtheta as float [I]
+    double* gn2_out;      // squared norm (one partial for the reduction kernel)
+    double* blk;          // [nblocks] per-block partial squared norms
+    DevState* st;
+    float lr, beta1, beta2, adam_eps;
+    int optimizer;        // 0 Adam, 1 SGD
+    int apply;            // 0: gradient only
+};
+
+bool p2_select(int nc, int I, P2Variant* out);
+size_t p2_sweep_smem(const P2Variant& v, int nc, int ld, int esz);
+size_t p2_grad_smem(const P2Variant& v, int nc, int ld, int esz);
+cudaError_t p2_launch_sweep(const P2Variant& v, const P2Args& a, cudaStream_t s);
+cudaError_t p2_launch_grad(const P2Variant& v, const P2Args& a, cudaStream_t s);
+cudaError_t p2_launch_adam(const P2AdamArgs& a, cudaStream_t s);
+cudaError_t launch_exp_theta(const float* theta, float* w, int I, int ld, cudaStream_t s);
+cudaError_t launch_p2_policy(const P2Args& a, int u0, int n_u, float* x, cudaStream_t s);
+int p2_adam_blocks(int I);
+bool p2_variant_k21(int R, int threads, P2Variant* out);
+bool p2_variant_k11(int R, int threads, P2Variant* out);
+bool p2_variant_k6(int R, int threads, P2Variant* out);
+bool p2_variant_generic(int ncb, int threads, P2Variant* out);
 
 // Launchers (return cudaError_t of the launch). `variant` is resolved by p1_select.
 struct P1Variant {
@@ -93,9 +151,11 @@ cudaError_t launch_pack_ikn_to_kni(const float* src, float* dst, int U, int I, i
 cudaError_t launch_unpack_kni_to_ikn(const float* src, float* dst, int U, int I, int nc, int ld,
                                      float scale, cudaStream_t s);
 cudaError_t launch_scale(const float* src, float* dst, long long n, float scale, cudaStream_t s);
-cudaError_t launch_relevance_import(const void* src, int dtype, long long ld_src, float* dst,
-                                    int U, int I, int ld, cudaStream_t s);
-cudaError_t launch_relevance_check(const float* r, int U, int I, int ld, int* flags,
+// relevance [U][I] (row stride ld_src, dtype FR_F32 | FR_F64 | FR_BF16) -> [U][ld] stored as
+// float or bfloat16 (dst_bf16, round to nearest even), padding zero
+cudaError_t launch_relevance_import(const void* src, int dtype, long long ld_src, void* dst,
+                                    int dst_bf16, int U, int I, int ld, cudaStream_t s);
+cudaError_t launch_relevance_check(const void* r, int r_bf16, int U, int I, int ld, int* flags,
                                    cudaStream_t s);
 cudaError_t launch_policy(const P1Args& a, int u0, int n_u, float* x_out, cudaStream_t s);
 cudaError_t launch_ex2_bench(float* sink, int blocks, int threads, int iters, cudaStream_t s);

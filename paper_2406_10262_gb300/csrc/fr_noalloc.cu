@@ -169,6 +169,7 @@ extern "C" fr_status fr_nsw_eval_noalloc(const float* C, const float* r, int64_t
     ra.I = n_items; ra.ld = (int)ld; ra.G = G; ra.U = n_users;
     ra.part = part; ra.gn2_part = gn2; ra.imp = imp_out; ra.omega = omega; ra.blk = blk; ra.st = st;
     ra.F_hist = nullptr; ra.gn_hist = nullptr; ra.hist_cap = 0; ra.after_update = 0;
+    ra.Ggn = 0;
     if (reduce_launch(ra, s) != cudaSuccess) return FR_ECUDA;
     noalloc_finish<<<1, 1, 0, s>>>(st, nsw_util_out);
     if (cudaGetLastError() != cudaSuccess) return FR_ECUDA;

@@ -134,131 +134,6 @@ __host__ __device__ inline size_t smem_layout(int ncb, int nc, int ld, int W, in
     return off;
 }
 
-// Cholesky solve of the n x n SPD system A (row-major) with right-hand side rhs, by one warp, in
-// double precision (wide tiles). Pivots below `floor` are raised to it (a column with no mass
-// leaves the Laplacian-like Gram matrix singular; its beta is then ~0).
-__device__ void warp_cholesky_solve(double* A, double* rhs, int n, int lane) {
-    double dmax = 0.0;
-    for (int j = 0; j < n; ++j) dmax = fmax(dmax, A[j * n + j]);
-    const double floor_ = 1e-13 * fmax(dmax, 1e-300);
-    for (int j = 0; j < n; ++j) {
-        __syncwarp();
-        const double ljj = sqrt(fmax(A[j * n + j], floor_));
-        for (int i = j + 1 + lane; i < n; i += 32) A[i * n + j] /= ljj;
-        __syncwarp();
-        if (lane == 0) A[j * n + j] = ljj;
-        const int m = n - j - 1;
-        for (int idx = lane; idx < m * m; idx += 32) {
-            const int i = j + 1 + idx / m, k = j + 1 + idx % m;
-            if (k <= i) A[i * n + k] -= A[i * n + j] * A[k * n + j];
-        }
-    }
-    __syncwarp();
-    for (int j = 0; j < n; ++j) {  // L y = rhs
-        const double yj = rhs[j] / A[j * n + j];
-        __syncwarp();
-        for (int i = j + 1 + lane; i < n; i += 32) rhs[i] -= A[i * n + j] * yj;
-        if (lane == 0) rhs[j] = yj;
-        __syncwarp();
-    }
-    for (int j = n - 1; j >= 0; --j) {  // L^T z = y
-        const double zj = rhs[j] / A[j * n + j];
-        __syncwarp();
-        for (int i = lane; i < j; i += 32) rhs[i] -= A[j * n + i] * zj;
-        if (lane == 0) rhs[j] = zj;
-        __syncwarp();
-    }
-}
-
-// Solve of the n x n SPD system (n <= NM <= 31) held in shared memory (A row-major, rhs), by one
-// warp in single precision: lane i keeps row i of A in registers; right-looking Cholesky with the
-// pivot column broadcast by shuffles, forward substitution in registers, back substitution from a
-// transposed copy of L in shared memory (Lt, n*n floats). Pivots below `floor` are raised to it.
-// Writes beta[0..n).
-template <int NM>
-__device__ void warp_cholesky_solve_f32(const float* A, const float* rhs, int n, float* Lt,
-                                        float* beta, int lane) {
-    float row[NM];
-#pragma unroll
-    for (int k = 0; k < NM; ++k) row[k] = (lane < n && k < n) ? A[lane * n + k] : 0.f;
-    float dmax = 0.f;
-#pragma unroll
-    for (int j = 0; j < NM; ++j)
-        if (j < n) dmax = fmaxf(dmax, __shfl_sync(FULL, row[j], j));
-    const float floor_ = 1e-12f * fmaxf(dmax, 1e-30f);
-#pragma unroll
-    for (int j = 0; j < NM; ++j) {
-        if (j >= n) break;
-        const float ljj = sqrtf(fmaxf(__shfl_sync(FULL, row[j], j), floor_));
-        const float lij = lane > j ? row[j] / ljj : (lane == j ? ljj : 0.f);
-        row[j] = lij;
-#pragma unroll
-        for (int k = j + 1; k < NM; ++k) {
-            const float lkj = __shfl_sync(FULL, lij, k);
-            if (lane > j) row[k] -= lij * lkj;
-        }
-    }
-    float y = lane < n ? rhs[lane] : 0.f;  // L y = rhs: lane i holds y_i
-#pragma unroll
-    for (int j = 0; j < NM; ++j) {
-        if (j >= n) break;
-        const float yj = __shfl_sync(FULL, y, j) / __shfl_sync(FULL, row[j], j);
-        if (lane == j) y = yj;
-        if (lane > j) y -= row[j] * yj;
-    }
-    if (lane < n) {  // Lt[k][i] = L[i][k]
-#pragma unroll
-        for (int k = 0; k < NM; ++k)
-            if (k < n) Lt[k * n + lane] = row[k];
-    }
-    __syncwarp();
-    float z = y;  // L^T z = y
-    for (int j = n - 1; j >= 0; --j) {
-        const float zj = __shfl_sync(FULL, z, j) / Lt[j * n + j];
-        if (lane == j) z = zj;
-        if (lane < j) z -= Lt[lane * n + j] * zj;  // (L^T)[i][j] = L[j][i]
-    }
-    if (lane < n) beta[lane] = z;
-}
-
-// Broadcast of the column potentials held by lane k % 32 (slot k / 32) to every lane.
-template <int NCB, int GPL>
-__device__ __forceinline__ void bcast_g(const float (&gm)[GPL], float (&gk)[NCB]) {
-#pragma unroll
-    for (int k = 0; k < NCB; ++k) gk[k] = __shfl_sync(FULL, gm[k / 32], k % 32);
-}
-
-// Column update after the row sums: warp reduce-scatter of cs, one barrier, then every warp sums
-// the per-warp partials of its lanes' columns and updates its copy of g'.
-template <int NCB, int GPL>
-__device__ __forceinline__ void column_update(float (&cs)[NCB], float (&gm)[GPL], int nc,
-                                              float* s_red, const float* s_l2b, int par, int lane,
-                                              int warp, int W) {
-    constexpr int P = pow2ceil(NCB);
-    constexpr int PER = P >= 32 ? P / 32 : 1;
-    float w[P];
-#pragma unroll
-    for (int k = 0; k < P; ++k) w[k] = k < NCB ? cs[k] : 0.f;
-    bool owner;
-    const int base = warp_reduce_scatter<P>(w, lane, owner);
-    float* buf = s_red + (size_t)par * W * P;
-    if (owner) {
-#pragma unroll
-        for (int q = 0; q < PER; ++q)
-            if (base + q < nc) buf[warp * P + base + q] = w[q];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < GPL; ++j) {
-        const int col = j * 32 + lane;
-        if (col < nc) {
-            float sum = 0.f;
-            for (int ww = 0; ww < W; ++ww) sum += buf[ww * P + col];
-            gm[j] += s_l2b[col] - log2f(fmaxf(sum, 1e-37f));
-        }
-    }
-}
-
 // Thread 0: bulk-copies consumer un's cost tile and relevance row into the staging buffers. Every
 // thread of the CTA must be done reading them (the caller sits after a __syncthreads).
 __device__ __forceinline__ void stage_consumer(const P1Args& a, int un, int nc, int ld,

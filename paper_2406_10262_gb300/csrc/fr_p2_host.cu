@@ -1,0 +1,160 @@
+// fr_p2_host.cu -- variant selection and launches of the per-item parametrisation, and the
+// cross-consumer reduction of dL/dtheta with the optimiser step on theta.
+#include <cuda_bf16.h>
+
+#include "fr_device.cuh"
+#include "fr_internal.h"
+#include "fr_p2.cuh"
+
+namespace fr {
+
+namespace {
+
+constexpr int AD_ITEMS = 32, AD_WARPS = 8;
+
+// dL/dtheta_i = sum over the per-CTA partials (FP64, fixed order); its squared norm; the ascent
+// step of Algorithm 1 on theta (Adam as in PyTorch with maximize=True, or SGD) and w = exp(theta).
+__global__ void __launch_bounds__(AD_ITEMS* AD_WARPS) p2_adam_kernel(const P2AdamArgs a) {
+    __shared__ double s_sum[AD_WARPS][AD_ITEMS];
+    __shared__ int s_last;
+    if (a.st->stop) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int item = blockIdx.x * AD_ITEMS + lane;
+    double acc = 0.0;
+    if (item < a.I)
+        for (int g = warp; g < a.G; g += AD_WARPS) acc += (double)a.part[(size_t)g * a.ld + item];
+    s_sum[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0) {
+        double d = 0.0;
+        for (int w = 0; w < AD_WARPS; ++w) d += s_sum[w][lane];
+        double g2 = 0.0;
+        if (item < a.I) {
+            g2 = d * d;
+            if (a.dtheta_out) a.dtheta_out[item] = (float)d;
+            if (a.apply) {
+                const float gr = (float)d;
+                float th = a.theta[item];
+                if (a.optimizer == 1) {
+                    th += a.lr * gr;
+                } else {
+                    const double t1 = (double)(a.st->t + 1);
+                    const float step = (float)((double)a.lr / (1.0 - pow((double)a.beta1, t1)));
+                    const float bc2s = (float)sqrt(1.0 - pow((double)a.beta2, t1));
+                    float m = a.m1[item], v = a.m2[item];
+                    m = a.beta1 * m + (1.f - a.beta1) * gr;
+                    v = a.beta2 * v + (1.f - a.beta2) * gr * gr;
+                    th += step * m / (sqrtf(v) / bc2s + a.adam_eps);
+                    a.m1[item] = m;
+                    a.m2[item] = v;
+                }
+                a.theta[item] = th;
+                a.w[item] = expf(th);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) g2 += __shfl_xor_sync(FULL, g2, o);
+        if (lane == 0) a.blk[blockIdx.x] = g2;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&a.st->counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last || warp != 0) return;
+    __threadfence();
+    double t = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(a.blk + b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+    if (lane == 0) {
+        *a.gn2_out = t;
+        a.st->counter = 0u;
+    }
+}
+
+// Policy of consumers u0.. (one CTA each): x_ik = softmax_k(g^(L-1)'_k + s_i (e_k - e_max)),
+// s_i = r(u,i) w_i / (eps ln 2), the policy of the last row update; public [u][i][k] layout.
+__global__ void p2_policy_kernel(const P2Args a, int u0, float* __restrict__ x) {
+    const int u = u0 + blockIdx.x;
+    const int nc = a.nc;
+    const float* gp = a.gP + (size_t)u * nc;
+    for (int i = threadIdx.x; i < a.I; i += blockDim.x) {
+        const size_t o = (size_t)u * a.ld + i;
+        const float r = a.r_bf16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(a.r)[o])
+                                 : static_cast<const float*>(a.r)[o];
+        const float si = r * a.w[i] * a.inv_eps_ln2;
+        float M = -INFINITY;
+        for (int k = 0; k < nc; ++k) M = fmaxf(M, fmaf(si, a.e[k] - a.emax, gp[k]));
+        float S = 0.f;
+        for (int k = 0; k < nc; ++k) S += ex2(fmaf(si, a.e[k] - a.emax, gp[k]) - M);
+        const float inv = 1.f / S;
+        float* xo = x + ((size_t)blockIdx.x * a.I + i) * nc;
+        for (int k = 0; k < nc; ++k) xo[k] = ex2(fmaf(si, a.e[k] - a.emax, gp[k]) - M) * inv;
+    }
+}
+
+__global__ void exp_theta_kernel(const float* __restrict__ theta, float* __restrict__ w, int I,
+                                 int ld) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ld; i += gridDim.x * blockDim.x)
+        w[i] = i < I ? expf(theta[i]) : 0.f;
+}
+
+}  // namespace
+
+int p2_adam_blocks(int I) { return (I + AD_ITEMS - 1) / AD_ITEMS; }
+
+// Rows per thread: 8 for up to 1024 items, 16 up to 8192, 24 up to 12288 (CTA <= 512 threads).
+bool p2_select(int nc, int I, P2Variant* out) {
+    auto threads_for = [&](int R) {
+        const int t = (I + R - 1) / R;
+        return (t + 31) / 32 * 32;
+    };
+    int R = I <= 1024 ? 8 : (threads_for(16) <= 512 ? 16 : 24);
+    if (threads_for(R) > 512) return false;
+    const int T = threads_for(R);
+    if (nc == 21) return p2_variant_k21(R, T, out);
+    if (nc == 11) return p2_variant_k11(R, T, out);
+    if (nc == 6) return p2_variant_k6(R, T, out);
+    if (threads_for(8) > 512) return false;
+    const int ncb = nc <= 8 ? 8 : (nc <= 16 ? 16 : (nc <= 32 ? 32 : 0));
+    if (!ncb) return false;
+    return p2_variant_generic(ncb, threads_for(8), out);
+}
+
+size_t p2_sweep_smem(const P2Variant& v, int nc, int ld, int esz) {
+    return p2::sweep_layout(v.ncb, nc, ld, v.threads / 32, esz, nullptr, nullptr);
+}
+
+size_t p2_grad_smem(const P2Variant& v, int nc, int ld, int esz) {
+    return p2::grad_layout(v.ncb, nc, ld, v.threads / 32, esz, nullptr, nullptr);
+}
+
+cudaError_t p2_launch_sweep(const P2Variant& v, const P2Args& a, cudaStream_t s) {
+    void* args[] = {const_cast<P2Args*>(&a)};
+    return cudaLaunchKernel(v.sweep, dim3(a.G), dim3(v.threads), args,
+                            p2_sweep_smem(v, a.nc, a.ld, a.r_bf16 ? 2 : 4), s);
+}
+
+cudaError_t p2_launch_grad(const P2Variant& v, const P2Args& a, cudaStream_t s) {
+    void* args[] = {const_cast<P2Args*>(&a)};
+    return cudaLaunchKernel(v.grad, dim3(a.G), dim3(v.threads), args,
+                            p2_grad_smem(v, a.nc, a.ld, a.r_bf16 ? 2 : 4), s);
+}
+
+cudaError_t p2_launch_adam(const P2AdamArgs& a, cudaStream_t s) {
+    p2_adam_kernel<<<p2_adam_blocks(a.I), AD_ITEMS * AD_WARPS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_p2_policy(const P2Args& a, int u0, int n_u, float* x, cudaStream_t s) {
+    if (n_u <= 0) return cudaSuccess;
+    p2_policy_kernel<<<n_u, 256, 0, s>>>(a, u0, x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_exp_theta(const float* theta, float* w, int I, int ld, cudaStream_t s) {
+    exp_theta_kernel<<<(ld + 255) / 256, 256, 0, s>>>(theta, w, I, ld);
+    return cudaGetLastError();
+}
+
+}  // namespace fr
