@@ -8,6 +8,13 @@ consumer per step, 500 ascent steps. One benchmark step is one whole solve: rese
 initial Sinkhorn solve and 500 ascent steps, i.e. 501 x 50 Sinkhorn iterations over every cell.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py --compare batch|unrolled|bf16 [--steps K]
+
+--compare runs one of the layered forms against the plain FP32 method on the same GPU and prints
+one JSON line: 256 markets batched vs solved one after another (|U| ~ U[100, 4000], |I| ~
+U[100, 2000], K in {5, 10, 20}); the unrolled adjoint gradient vs the implicit gradient (|U| =
+20000, |I| = 2000, K = 20, L = 100, checkpoints every 10); BF16 vs FP32 relevance storage (|U| =
+200000, |I| = 10^4, K = 20, rank-32 sigmoid relevance with 5% boosted items).
 
 Under torchrun (N > 1) every rank solves its own independent market (seed = rank): weak scaling
 with no collective on the data path; the timing is the max over ranks.
@@ -47,6 +54,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling driver: set up the workload, run this many ascent steps, exit")
+    ap.add_argument("--compare", choices=["batch", "unrolled", "bf16"], default=None,
+                    help="compare a layered form against the plain FP32 method (one JSON line)")
     return ap.parse_args()
 
 
@@ -310,8 +319,131 @@ def run_ours(args, w):
         dist.destroy_process_group()
 
 
+# ---- layered forms against the plain FP32 method ---------------------------------------------
+def _timed(fn):
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0
+
+
+def compare_batch(args):
+    """256 independent markets: one fr_batch (autotuned buckets, concurrent persistent launches
+    under a CUDA graph) against 256 FairRank contexts run one after another; the same S ascent
+    steps from theta = 0 in both, F of every market compared."""
+    from paper_2406_10262_gb300 import fairrank as fr
+    from paper_2406_10262_gb300 import synth
+    S, L = max(args.steps, 1) * 8, 50
+    ms = synth.markets(256, seed=0)
+    sizes = [(m.n_users, m.n_items, m.n_slots) for m in ms]
+    rs = [synth.relevance_lowrank_fast(m.n_users, m.n_items, seed=m.seed) for m in ms]
+    cells = sum(U * I * fr.num_cols(I, K) for U, I, K in sizes)
+    b = fr.FairRankBatch(sizes, sinkhorn_iters=L)
+    for j, ((U, I, K), r) in enumerate(zip(sizes, rs)):
+        b.set_relevance(j, r)
+        b.set_exposure(j, synth.dcg_exposure(K))
+    _, tune_s = _timed(b.autotune)
+    b.step(2, trace=False)  # warm-up (graph capture)
+    b.reset()
+    Fb, t_batch = _timed(lambda: b.step(S))
+    l0 = b.launch_count()
+    ctxs = []
+    for (U, I, K), r in zip(sizes, rs):
+        g = fr.FairRank(U, I, K, param=fr.PARAM_ITEM, sinkhorn_iters=L)
+        g.set_relevance(r)
+        g.set_exposure(synth.dcg_exposure(K))
+        g.step(S, trace=False)  # warm-up (graph capture)
+        g.reset()
+        ctxs.append(g)
+    Fs, t_seq = _timed(lambda: [g.step(S) for g in ctxs])
+    Fs = np.array(Fs).T
+    rel_F = float(np.max(np.abs(Fb[-1] - Fs[-1]) / np.abs(Fs[-1])))
+    cu = cells * L * (S + 1)
+    return {"compare": "batch", "markets": 256, "ascent_steps": S, "sinkhorn_iters": L,
+            "cells": cells, "cell_updates": cu, "batched_s": t_batch, "sequential_s": t_seq,
+            "speedup": t_seq / t_batch, "batched_cell_updates_per_s": cu / t_batch,
+            "sequential_cell_updates_per_s": cu / t_seq, "max_rel_F_diff_final": rel_F,
+            "autotune_s": tune_s, "buckets": b.tuning(), "launches_per_run": b.launch_count() - l0}
+
+
+def compare_unrolled(args):
+    """|U| = 20000, |I| = 2000, K = 20, L = 100: ascent driven by the unrolled adjoint gradient
+    (checkpoints every 10 iterations) against the implicit gradient, same S steps from theta = 0;
+    both gradients also taken at one common state."""
+    from paper_2406_10262_gb300 import fairrank as fr
+    from paper_2406_10262_gb300 import synth
+    U, I, K, L, S = 20000, 2000, 20, 100, max(args.steps, 1) * 4
+    r = synth.relevance_lowrank_fast(U, I, seed=7)
+    out = {"compare": "unrolled", "n_users": U, "n_items": I, "n_slots": K, "sinkhorn_iters": L,
+           "ckpt_every": 10, "ascent_steps": S}
+    res = {}
+    for name, mode in (("implicit", fr.GRAD_IMPLICIT), ("unrolled", fr.GRAD_UNROLLED)):
+        g = fr.FairRank(U, I, K, param=fr.PARAM_ITEM, sinkhorn_iters=L, grad_mode=mode,
+                        ckpt_every=10)
+        g.set_relevance(r)
+        g.set_exposure(synth.dcg_exposure(K))
+        g.step(2, trace=False)
+        g.reset()
+        F, t = _timed(lambda: g.step(S))
+        kms = g.time_kernels(3)
+        g.reset()
+        g.impacts()
+        res[name] = g.grad()
+        out[name] = {"s_per_run": t, "ms_per_step": t / S * 1e3, "F_final": float(F[-1]),
+                     "sweep_ms": kms[0], "reduce_ms": kms[1], "grad_ms": kms[2]}
+    a, c = res["implicit"].astype(np.float64), res["unrolled"].astype(np.float64)
+    out["rel_F_diff_final"] = abs(out["unrolled"]["F_final"] - out["implicit"]["F_final"]) / \
+        abs(out["implicit"]["F_final"])
+    out["grad_rel_l2_diff_at_theta0"] = float(np.linalg.norm(a - c) / np.linalg.norm(a))
+    out["grad_cosine_at_theta0"] = float(a @ c / (np.linalg.norm(a) * np.linalg.norm(c)))
+    out["unrolled_over_implicit_time"] = out["unrolled"]["s_per_run"] / out["implicit"]["s_per_run"]
+    return out
+
+
+def compare_bf16(args):
+    """|U| = 200000, |I| = 10^4, K = 20, L = 50: BF16 against FP32 relevance storage, same S steps
+    from theta = 0; F of both and the Sinkhorn kernel time."""
+    from paper_2406_10262_gb300 import fairrank as fr
+    from paper_2406_10262_gb300 import synth
+    U, I, K, L, S = 200000, 10000, 20, 50, max(args.steps, 1)
+    blk = 20000
+    r32 = np.empty((U, I), dtype=np.float32)
+    for u0 in range(0, U, blk):
+        r32[u0:u0 + blk] = synth.relevance_lowrank_fast(U, I, seed=0, boost_frac=0.05, row0=u0,
+                                                        rows=min(blk, U - u0))
+    out = {"compare": "bf16", "n_users": U, "n_items": I, "n_slots": K, "sinkhorn_iters": L,
+           "ascent_steps": S}
+    cu = U * I * fr.num_cols(I, K) * L
+    for name, dt in (("fp32", fr.F32), ("bf16", fr.BF16)):
+        g = fr.FairRank(U, I, K, param=fr.PARAM_ITEM, sinkhorn_iters=L, rel_dtype=dt)
+        g.set_relevance(r32 if dt == fr.F32 else synth.to_bf16_bits(r32))
+        g.set_exposure(synth.dcg_exposure(K))
+        g.impacts()
+        F, t = _timed(lambda: g.step(S))
+        kms = g.time_kernels(2)
+        out[name] = {"s_per_run": t, "ms_per_step": t / S * 1e3, "F_final": float(F[-1]),
+                     "sweep_ms": kms[0], "grad_ms": kms[2], "reduce_ms": kms[1],
+                     "sweep_cell_updates_per_s": cu / (kms[0] * 1e-3),
+                     "relevance_bytes": U * ((I + 7) // 8 * 8) * (4 if dt == fr.F32 else 2)}
+        del g
+    out["rel_F_diff_final"] = abs(out["bf16"]["F_final"] - out["fp32"]["F_final"]) / \
+        abs(out["fp32"]["F_final"])
+    out["sweep_speedup"] = out["fp32"]["sweep_ms"] / out["bf16"]["sweep_ms"]
+    return out
+
+
 def main():
     args = parse()
+    if args.compare:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        from paper_2406_10262_gb300 import build as frbuild
+        frbuild.build()
+        fn = {"batch": compare_batch, "unrolled": compare_unrolled, "bf16": compare_bf16}[args.compare]
+        print(json.dumps(fn(args)), flush=True)
+        return
     w = workload(args.workload)
     if args.impl == "reference":
         run_reference(args, w)

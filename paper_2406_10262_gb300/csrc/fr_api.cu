@@ -39,6 +39,11 @@ struct fr_ctx {
     // free costs: C, Adam moments [U][nc][ld]; per-item: theta, moments, w = exp(theta) [ld]
     float *C = nullptr, *m1 = nullptr, *m2 = nullptr;
     float *theta = nullptr, *tm1 = nullptr, *tm2 = nullptr, *w = nullptr, *gpart = nullptr;
+    // unrolled differentiation (per-item): checkpoints g^(j ce) of the last sweep [U][nck][nc],
+    // and the grid of the adjoint kernel (its dL/dtheta partials fill gpart[Gg][ld])
+    bool unrolled = false;
+    float* ck = nullptr;
+    int ce = 0, nck = 0, Gg = 0;
     double *ad_blk = nullptr, *gn2_one = nullptr;
     float *gL = nullptr, *gP = nullptr, *e = nullptr, *log2b = nullptr, *omega = nullptr,
           *part = nullptr;
@@ -118,12 +123,21 @@ P2Args p2_args(fr_ctx* c, float* part) {
     a.inv_eps_ln2 = (float)(1.0 / (c->cfg.epsilon * std::log(2.0)));
     a.inv_eps = (float)(1.0 / c->cfg.epsilon);
     a.warm = c->cfg.warm_start ? 1 : 0;
+    a.ck = c->ck; a.ce = c->ce; a.nck = c->nck;
     return a;
+}
+
+// Gradient of sum_i omega_i Imp_i onto the per-CTA dL/dtheta partials gpart: implicit (Sec. 3
+// optimality conditions) or through the unrolled iterations (adjoint kernel).
+cudaError_t launch_p2_grad(fr_ctx* c, P2Args a) {
+    a.part = c->gpart;
+    a.G = c->Gg;
+    return c->unrolled ? p2_launch_adj(c->var2, a, c->s) : p2_launch_grad(c->var2, a, c->s);
 }
 
 P2AdamArgs adam_args(fr_ctx* c, int apply, float* dtheta_out) {
     P2AdamArgs a{};
-    a.I = c->I; a.ld = c->ld; a.G = c->G; a.part = c->gpart;
+    a.I = c->I; a.ld = c->ld; a.G = c->Gg; a.part = c->gpart;
     a.theta = c->theta; a.m1 = c->tm1; a.m2 = c->tm2; a.w = c->w; a.dtheta_out = dtheta_out;
     a.gn2_out = c->gn2_one; a.blk = c->ad_blk; a.st = c->st;
     a.lr = (float)c->cfg.lr; a.beta1 = (float)c->cfg.beta1; a.beta2 = (float)c->cfg.beta2;
@@ -163,7 +177,7 @@ fr_status launch_solve(fr_ctx* ctx) {
 // One ascent step of Algorithm 1: gradient at the current policy, update, Sinkhorn, impacts.
 fr_status launch_one_step(fr_ctx* ctx) {
     if (ctx->p2) {
-        CU(p2_launch_grad(ctx->var2, p2_args(ctx, ctx->gpart), ctx->s));
+        CU(launch_p2_grad(ctx, p2_args(ctx, ctx->gpart)));
         CU(p2_launch_adam(adam_args(ctx, 1, nullptr), ctx->s));
         CU(p2_launch_sweep(ctx->var2, p2_args(ctx, ctx->part), ctx->s));
         ctx->launches += 3;
@@ -290,7 +304,7 @@ fr_status ensure_tmp(fr_ctx* ctx, size_t bytes) {
 void free_all(fr_ctx* c) {
     if (c->chunk_exec) cudaGraphExecDestroy(c->chunk_exec);
     float* fs[] = {c->C, c->m1, c->m2, c->theta, c->tm1, c->tm2, c->w, c->gpart, c->gL, c->gP,
-                   c->e, c->log2b, c->omega, c->part, c->tmp};
+                   c->e, c->log2b, c->omega, c->part, c->tmp, c->ck};
     for (float* p : fs) cudaFree(p);
     double* ds[] = {c->gn2_part, c->imp, c->blk, c->F_hist, c->gn_hist, c->ad_blk, c->gn2_one};
     for (double* p : ds) cudaFree(p);
@@ -385,8 +399,12 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
         return fail(nullptr, FR_EINVAL, "unknown param %d", c.param);
     if (c.grad_mode != FR_GRAD_IMPLICIT && c.grad_mode != FR_GRAD_UNROLLED)
         return fail(nullptr, FR_EINVAL, "unknown grad_mode %d", c.grad_mode);
-    if (c.grad_mode != FR_GRAD_IMPLICIT)
-        return fail(nullptr, FR_EUNSUPPORTED, "this build differentiates implicitly only");
+    if (c.grad_mode == FR_GRAD_UNROLLED && c.param != FR_PARAM_ITEM)
+        return fail(nullptr, FR_EUNSUPPORTED,
+                    "unrolled differentiation is built for FR_PARAM_ITEM; FR_PARAM_FULL_C "
+                    "differentiates implicitly");
+    if (c.grad_mode == FR_GRAD_UNROLLED && c.ckpt_every < 1)
+        return fail(nullptr, FR_EINVAL, "ckpt_every must be >= 1 (got %d)", c.ckpt_every);
     if (c.rel_dtype != FR_F32 && c.rel_dtype != FR_BF16)
         return fail(nullptr, FR_EINVAL, "rel_dtype must be FR_F32 or FR_BF16");
     if (c.param == FR_PARAM_FULL_C && c.rel_dtype != FR_F32)
@@ -403,6 +421,11 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
             return fail(nullptr, FR_EUNSUPPORTED,
                         "FR_PARAM_ITEM needs n_cols <= 32 and n_items <= 12288 (4096 unless "
                         "n_cols is 6, 11 or 21); got n_cols %d, n_items %d",
+                        nc, c.n_items);
+        if (c.grad_mode == FR_GRAD_UNROLLED && !p2_select_adj(nc, c.n_items, &var2))
+            return fail(nullptr, FR_EUNSUPPORTED,
+                        "unrolled differentiation needs n_items <= 6144 (2048 unless n_cols is 6, "
+                        "11 or 21) and n_cols <= 32; got n_cols %d, n_items %d",
                         nc, c.n_items);
     } else if (!p1_select(nc, c.n_items, &var)) {
         return fail(nullptr, FR_EUNSUPPORTED,
@@ -422,6 +445,11 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
     ctx->var2 = var2;
     ctx->r_bf16 = c.rel_dtype == FR_BF16 ? 1 : 0;
     ctx->user = (cudaStream_t)stream;
+    ctx->unrolled = c.grad_mode == FR_GRAD_UNROLLED;
+    if (ctx->unrolled) {
+        ctx->ce = std::min(c.ckpt_every, c.sinkhorn_iters);
+        ctx->nck = (c.sinkhorn_iters + ctx->ce - 1) / ctx->ce;
+    }
     auto bail = [&](fr_status st) {
         g_create_error = ctx->err;
         free_all(ctx);
@@ -449,7 +477,7 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
             return fail(ctx, FR_EUNSUPPORTED,
                         "shared memory %zu B exceeds the device limit %d B for this shape", b,
                         max_optin);
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+        cudaError_t e = raise_smem_limit(fn, b);
         if (e != cudaSuccess) return fail(ctx, FR_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
         return FR_OK;
     };
@@ -464,6 +492,14 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
         CUC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, var2.sweep, var2.threads, bs));
         CUC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, var2.grad, var2.threads, bg));
         occ = std::min(o1, o2);
+        int og = o2;
+        if (ctx->unrolled) {
+            const size_t ba = p2_adj_smem(var2, nc, ctx->ld, esz, ctx->ce);
+            if ((st = set_smem(var2.adj, ba)) != FR_OK) return bail(st);
+            CUC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&og, var2.adj, var2.adj_threads, ba));
+            if (og < 1) return bail(fail(ctx, FR_EUNSUPPORTED, "adjoint kernel does not fit on an SM"));
+        }
+        ctx->Gg = std::min(ctx->U, std::max(og, 1) * sms);
     } else {
         for (int m = 0; m < 3; ++m) {
             fr_status st = set_smem(var.fn[m], p1_smem_bytes(var, m, nc, ctx->ld));
@@ -483,7 +519,12 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
         CUC(cudaMalloc(&ctx->tm1, sizeof(float) * ld));
         CUC(cudaMalloc(&ctx->tm2, sizeof(float) * ld));
         CUC(cudaMalloc(&ctx->w, sizeof(float) * ld));
-        CUC(cudaMalloc(&ctx->gpart, sizeof(float) * (size_t)ctx->G * ld));
+        CUC(cudaMalloc(&ctx->gpart, sizeof(float) * (size_t)ctx->Gg * ld));
+        if (ctx->unrolled) {
+            const size_t nck = (size_t)ctx->U * ctx->nck * nc;
+            CUC(cudaMalloc(&ctx->ck, sizeof(float) * nck));
+            CUC(cudaMemset(ctx->ck, 0, sizeof(float) * nck));
+        }
         CUC(cudaMalloc(&ctx->ad_blk, sizeof(double) * p2_adam_blocks(ctx->I)));
         CUC(cudaMalloc(&ctx->gn2_one, sizeof(double)));
     } else {
@@ -680,7 +721,7 @@ fr_status fr_grad(fr_ctx* ctx, const float* omega, float* dparam, float* dr, int
         P2Args a = p2_args(ctx, ctx->gpart);
         a.omega = om;
         a.dr = dR;
-        CU(p2_launch_grad(ctx->var2, a, ctx->s));
+        CU(launch_p2_grad(ctx, a));
         CU(p2_launch_adam(adam_args(ctx, 0, dP), ctx->s));
         ctx->launches += 2;
     } else {
@@ -806,7 +847,7 @@ fr_status fr_time_kernels(fr_ctx* ctx, int32_t n_steps, double* ms) {
     for (int s = 0; s < n_steps; ++s) {
         CU(cudaEventRecord(ev[0], ctx->s));
         if (ctx->p2) {  // [gradient + theta update] [Sinkhorn] [reduction]
-            CU(p2_launch_grad(ctx->var2, p2_args(ctx, ctx->gpart), ctx->s));
+            CU(launch_p2_grad(ctx, p2_args(ctx, ctx->gpart)));
             CU(p2_launch_adam(adam_args(ctx, 1, nullptr), ctx->s));
             CU(cudaEventRecord(ev[1], ctx->s));
             CU(p2_launch_sweep(ctx->var2, p2_args(ctx, ctx->part), ctx->s));

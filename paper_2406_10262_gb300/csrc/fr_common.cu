@@ -1,6 +1,8 @@
 // fr_common.cu -- the cross-consumer impact reduction and the support kernels of libfairrank.
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "fr_device.cuh"
 #include "fr_internal.h"
 
@@ -16,12 +18,13 @@ constexpr int RED_WARPS = 8;   // warps splitting the per-CTA partials
 // finish (atomic ticket) combines the per-CTA partial sums of log Imp_i, of Imp_i (utility,
 // Sec. 4.1) and of the squared gradient norm in a fixed order, updates the step state and, for
 // fr_solve, raises the stop flag once the step's gradient norm is <= the threshold.
-__global__ void __launch_bounds__(RED_ITEMS* RED_WARPS) reduce_kernel(const ReduceArgs a) {
+// bid / nb: this CTA's index among the nb CTAs that reduce one problem.
+__device__ __forceinline__ void reduce_body(const ReduceArgs& a, int bid, int nb) {
     __shared__ double s_sum[RED_WARPS][RED_ITEMS];
     __shared__ int s_last;
     if (a.st->stop) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int item = blockIdx.x * RED_ITEMS + lane;
+    const int item = bid * RED_ITEMS + lane;
     double acc = 0.0;
     if (item < a.I)
         for (int g = warp; g < a.G; g += RED_WARPS) acc += (double)a.part[(size_t)g * a.ld + item];
@@ -44,18 +47,18 @@ __global__ void __launch_bounds__(RED_ITEMS* RED_WARPS) reduce_kernel(const Redu
             im += __shfl_xor_sync(FULL, im, o);
         }
         if (lane == 0) {
-            a.blk[2 * blockIdx.x] = lg;
-            a.blk[2 * blockIdx.x + 1] = im;
+            a.blk[2 * bid] = lg;
+            a.blk[2 * bid + 1] = im;
         }
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&a.st->counter, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) s_last = atomicAdd(&a.st->counter, 1u) == (unsigned)nb - 1;
     __syncthreads();
     if (!s_last || warp != 0) return;
     __threadfence();
     double F = 0.0, S = 0.0, g2 = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) {
+    for (int b = lane; b < nb; b += 32) {
         F += __ldcg(a.blk + 2 * b);
         S += __ldcg(a.blk + 2 * b + 1);
     }
@@ -88,6 +91,18 @@ __global__ void __launch_bounds__(RED_ITEMS* RED_WARPS) reduce_kernel(const Redu
         }
         st->counter = 0u;
     }
+}
+
+__global__ void __launch_bounds__(RED_ITEMS* RED_WARPS) reduce_kernel(const ReduceArgs a) {
+    reduce_body(a, blockIdx.x, gridDim.x);
+}
+
+// Batched markets: block j reduces block bmap[j].y of market bmap[j].x (a.nblk blocks each).
+__global__ void __launch_bounds__(RED_ITEMS* RED_WARPS)
+    reduce_batch_kernel(const ReduceArgs* __restrict__ ra, const int2* __restrict__ bmap) {
+    const int2 mb = bmap[blockIdx.x];
+    const ReduceArgs a = ra[mb.x];
+    reduce_body(a, mb.y, a.nblk);
 }
 
 // [U][I][nc] -> [U][nc][ld] (padding rows zero), times scale
@@ -205,8 +220,24 @@ int grid_for(long long n) {
 
 int reduce_blocks(int I) { return (I + RED_ITEMS - 1) / RED_ITEMS; }
 
+cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 cudaError_t reduce_launch(const ReduceArgs& a, cudaStream_t s) {
     reduce_kernel<<<reduce_blocks(a.I), RED_ITEMS * RED_WARPS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t reduce_launch_batch(const ReduceArgs* ra, const int2* bmap, int nblocks, cudaStream_t s) {
+    if (nblocks <= 0) return cudaSuccess;
+    reduce_batch_kernel<<<nblocks, RED_ITEMS * RED_WARPS, 0, s>>>(ra, bmap);
     return cudaGetLastError();
 }
 

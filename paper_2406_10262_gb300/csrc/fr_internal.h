@@ -73,6 +73,7 @@ struct ReduceArgs {
     double* gn_hist;
     int hist_cap;
     int after_update;     // 1 if the sweep followed an optimiser update
+    int nblk;             // batched launches: reduction blocks of this problem
 };
 
 // ---- per-item parametrisation c_uik = -r(u,i) e_k exp(theta_i) ----------------------------------
@@ -92,12 +93,32 @@ struct P2Args {
     DevState* st;
     float inv_eps_ln2, inv_eps;
     int warm;
+    float* ck;            // unrolled gradient: column-potential checkpoints [U][nck][nc] (nullable)
+    int ce, nck;          // checkpoint interval (iterations) and count ceil(L / ce)
+};
+
+// Batched markets: a launch processes a list of chunks, each a range of consumers of one market
+// with its own row of the market's partial buffer (mk[market].part + row * ld).
+struct P2Chunk {
+    int market, u0, u1, row;
+};
+
+struct P2Batch {
+    const P2Args* mk;     // device array of per-market arguments (nullptr: single-market launch)
+    const P2Chunk* ch;    // device array of this launch's chunks
+    int n_chunks;
+    int ld_max;           // largest ld of the chunks' markets (shared-memory layout)
+    int esz;              // bytes per stored relevance value (shared by all markets)
 };
 
 struct P2Variant {
     int ncb, rows, exact, threads;
     const void* sweep;
     const void* grad;
+    const void* sweep_b;  // batched-market forms of sweep / grad (argument: P2Batch)
+    const void* grad_b;
+    const void* adj;      // unrolled-gradient (adjoint) kernel, CTA of adj_threads (p2_select_adj)
+    int adj_threads;
 };
 
 // dL/dtheta from the per-CTA partials (FP64, fixed order), its squared norm, and optionally the
@@ -116,14 +137,32 @@ struct P2AdamArgs {
     float lr, beta1, beta2, adam_eps;
     int optimizer;        // 0 Adam, 1 SGD
     int apply;            // 0: gradient only
+    int nblk;             // batched launches: update blocks of this problem
 };
+
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` (never lowers it: the limit is
+// per function, shared by every context that launches it). Serialised by a process-wide lock.
+cudaError_t raise_smem_limit(const void* fn, size_t bytes);
 
 bool p2_select(int nc, int I, P2Variant* out);
 size_t p2_sweep_smem(const P2Variant& v, int nc, int ld, int esz);
 size_t p2_grad_smem(const P2Variant& v, int nc, int ld, int esz);
 cudaError_t p2_launch_sweep(const P2Variant& v, const P2Args& a, cudaStream_t s);
 cudaError_t p2_launch_grad(const P2Variant& v, const P2Args& a, cudaStream_t s);
+// batched launches: grid G, shared memory for ld_max (all markets of the launch share ncb)
+size_t p2_sweep_smem_batch(const P2Variant& v, int ld_max, int esz);
+size_t p2_grad_smem_batch(const P2Variant& v, int ld_max, int esz);
+cudaError_t p2_launch_sweep_batch(const P2Variant& v, const P2Batch& bt, int G, cudaStream_t s);
+cudaError_t p2_launch_grad_batch(const P2Variant& v, const P2Batch& bt, int G, cudaStream_t s);
+bool p2_select_adj(int nc, int I, P2Variant* v);  // sets adj / adj_threads
+bool p2_adj_k21(int R, int threads, P2Variant* v);
+bool p2_adj_k11_k6(int nc, int R, int threads, P2Variant* v);
+bool p2_adj_generic(int ncb, int threads, P2Variant* v);
+size_t p2_adj_smem(const P2Variant& v, int nc, int ld, int esz, int ce);
+cudaError_t p2_launch_adj(const P2Variant& v, const P2Args& a, cudaStream_t s);
 cudaError_t p2_launch_adam(const P2AdamArgs& a, cudaStream_t s);
+// batched markets: block j works on block bmap[j].y of market bmap[j].x (device arrays)
+cudaError_t p2_launch_adam_batch(const P2AdamArgs* aa, const int2* bmap, int nblocks, cudaStream_t s);
 cudaError_t launch_exp_theta(const float* theta, float* w, int I, int ld, cudaStream_t s);
 cudaError_t launch_p2_policy(const P2Args& a, int u0, int n_u, float* x, cudaStream_t s);
 int p2_adam_blocks(int I);
@@ -144,6 +183,7 @@ bool p1_select(int nc, int I, P1Variant* out);
 cudaError_t p1_launch(const P1Variant& v, int mode, const P1Args& a, cudaStream_t s);
 size_t p1_smem_bytes(const P1Variant& v, int mode, int nc, int ld);
 cudaError_t reduce_launch(const ReduceArgs& a, cudaStream_t s);
+cudaError_t reduce_launch_batch(const ReduceArgs* ra, const int2* bmap, int nblocks, cudaStream_t s);
 int reduce_blocks(int I);
 
 cudaError_t launch_pack_ikn_to_kni(const float* src, float* dst, int U, int I, int nc, int ld,

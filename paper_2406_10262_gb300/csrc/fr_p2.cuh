@@ -102,9 +102,85 @@ __device__ __forceinline__ void p2_stage(const P2Args& a, int un, int b, unsigne
              static_cast<const unsigned char*>(a.r) + (size_t)un * esz * a.ld, bytes, bars + b);
 }
 
+// One row of the policy in base 2: p_k = 2^(g'_k + s (e_k - e_max)) for the column pairs (p2) and
+// the unpaired last column (pt); returns 1 / sum_k p_k. A row whose sum leaves [2^-100, 2^100] is
+// recomputed with its exact maximum subtracted.
+template <int NCB, bool EXACT>
+__device__ __forceinline__ float p2_row(float sv, const f2* e2, float et, const f2* g2, float gt,
+                                        const float* eh, const float (&gk)[NCB], int nc, f2* p2,
+                                        float& pt) {
+    constexpr int NP = NCB / 2;
+    constexpr bool TAIL = NCB % 2 == 1;
+    const f2 sp = pk(sv, sv);
+    f2 S2 = 0ull;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+        float a0, a1;
+        upk(fma2(sp, e2[j], g2[j]), a0, a1);
+        p2[j] = pk(ex2(a0), ex2(a1));
+        S2 = add2(S2, p2[j]);
+    }
+    pt = TAIL ? ex2(fmaf(sv, et, gt)) : 0.f;
+    float S0, S1;
+    upk(S2, S0, S1);
+    float S = S0 + S1 + pt;
+    if (!(S >= 0x1p-100f && S <= 0x1p100f)) {  // exact max shift for this row
+        float M = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < NCB; ++k)
+            if (EXACT || k < nc) M = fmaxf(M, fmaf(sv, eh[k], gk[k]));
+        S2 = 0ull;
+        const f2 M2 = pk(M, M);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            float a0, a1;
+            upk(sub2(fma2(sp, e2[j], g2[j]), M2), a0, a1);
+            p2[j] = pk(ex2(a0), ex2(a1));
+            S2 = add2(S2, p2[j]);
+        }
+        pt = TAIL ? ex2(fmaf(sv, et, gt) - M) : 0.f;
+        upk(S2, S0, S1);
+        S = S0 + S1 + pt;
+    }
+    return rcp_approx(S);
+}
+
+// Column sums of per-thread vectors over the CTA, delivered to every warp: lane l of every warp
+// gets the sums of columns l, l+32, ... (fixed order). One __syncthreads on buffer `par`.
+template <int NCB, int GPL>
+__device__ __forceinline__ void column_sum(float (&cs)[NCB], float (&out)[GPL], int nc,
+                                           float* s_red, int par, int lane, int warp, int W) {
+    constexpr int P = pow2ceil(NCB);
+    constexpr int PER = P >= 32 ? P / 32 : 1;
+    float w[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) w[k] = k < NCB ? cs[k] : 0.f;
+    bool owner;
+    const int base = warp_reduce_scatter<P>(w, lane, owner);
+    float* buf = s_red + (size_t)par * W * P;
+    if (owner) {
+#pragma unroll
+        for (int q = 0; q < PER; ++q)
+            if (base + q < nc) buf[warp * P + base + q] = w[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < GPL; ++j) {
+        const int col = j * 32 + lane;
+        float sum = 0.f;
+        if (col < nc)
+            for (int ww = 0; ww < W; ++ww) sum += buf[ww * P + col];
+        out[j] = sum;
+    }
+}
+
+// Sinkhorn sweep of consumers u_first, u_first + u_step, ... < u_end of one market (one CTA), impact
+// partials of those consumers written to part_row[0 .. ld). Staging buffer index b, the mbarrier
+// phase bits and the reduction buffer parity carry over between calls of one CTA.
 template <int NCB, int R, bool EXACT>
-__global__ void __launch_bounds__(512) p2_sweep_kernel(const P2Args a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void sweep_consumers(const P2Args& a, int u_first, int u_end, int u_step,
+                                                float* __restrict__ part_row, const SweepSmem& s,
+                                                int& b, unsigned& phase_bits, int& par) {
     constexpr int GPL = (NCB + 31) / 32;
     constexpr int NP = NCB / 2;         // column pairs
     constexpr bool TAIL = NCB % 2 == 1;  // one unpaired last column
@@ -116,18 +192,8 @@ __global__ void __launch_bounds__(512) p2_sweep_kernel(const P2Args a) {
     const int i0 = tid * R;
     const bool bf16 = a.r_bf16 != 0;
     const int esz = bf16 ? 2 : 4;
-    SweepSmem s;
-    sweep_layout(NCB, nc, ld, W, esz, &s, smem_raw);
 
-    if (a.st->stop) return;
-
-    if (tid == 0) {
-        mbar_init(s.bar, 1);
-        mbar_init(s.bar + 1, 1);
-        fence_mbar_init();
-    }
-    __syncthreads();  // mbarriers initialised before any wait
-    if (tid == 0) p2_stage(a, blockIdx.x, 0, s.bar, s.rbuf, esz);
+    if (tid == 0) p2_stage(a, u_first, b, s.bar, s.rbuf, esz);
     for (int i = tid; i < ld; i += T) s.w[i] = i < I ? a.w[i] : 0.f;
 #pragma unroll
     for (int r = 0; r < R; ++r)
@@ -138,7 +204,7 @@ __global__ void __launch_bounds__(512) p2_sweep_kernel(const P2Args a) {
         s.l2b[k] = k < nc ? a.log2b[k] : 0.f;
     }
     __syncthreads();
-    // packed (e_k - e_max) pairs, constant for the launch
+    // packed (e_k - e_max) pairs, constant for the market
     f2 e2[NP > 0 ? NP : 1];
 #pragma unroll
     for (int j = 0; j < NP; ++j) e2[j] = pk(s.eh[2 * j], s.eh[2 * j + 1]);
@@ -148,10 +214,7 @@ __global__ void __launch_bounds__(512) p2_sweep_kernel(const P2Args a) {
 #pragma unroll
     for (int r = 0; r < R; ++r) vr[r] = i0 + r < I;
 
-    int par = 0;
-    unsigned phase_bits = 0u;  // bit b: expected phase parity of staging buffer b
-    int b = 0;
-    for (int u = blockIdx.x; u < a.U; u += gridDim.x, b ^= 1) {
+    for (int u = u_first; u < u_end; u += u_step, b ^= 1) {
         if (!mbar_wait(s.bar + b, (phase_bits >> b) & 1u, 1u << 26)) {
             if (tid == 0) atomicOr(&a.st->err, 4);
         }
@@ -169,10 +232,15 @@ __global__ void __launch_bounds__(512) p2_sweep_kernel(const P2Args a) {
         }
         for (int l = 0; l < a.L; ++l) {
             const bool last = l == a.L - 1;
-            if (last && warp == 0) {
+            if (warp == 0) {
 #pragma unroll
-                for (int j = 0; j < GPL; ++j)
-                    if (j * 32 + lane < nc) a.gP[(size_t)u * nc + j * 32 + lane] = gm[j];
+                for (int j = 0; j < GPL; ++j) {
+                    const int col = j * 32 + lane;
+                    if (col >= nc) continue;
+                    if (last) a.gP[(size_t)u * nc + col] = gm[j];
+                    if (a.ck && l % a.ce == 0)  // g^(l), the start of segment l / ce
+                        a.ck[((size_t)u * a.nck + l / a.ce) * nc + col] = gm[j];
+                }
             }
             float gk[NCB];
             bcast_g<NCB, GPL>(gm, gk);
@@ -192,39 +260,9 @@ __global__ void __launch_bounds__(512) p2_sweep_kernel(const P2Args a) {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (!vr[r]) continue;
-                const f2 sp = pk(sv[r], sv[r]);
                 f2 p2[NP > 0 ? NP : 1];
-                f2 S2 = 0ull;
-#pragma unroll
-                for (int j = 0; j < NP; ++j) {
-                    float a0, a1;
-                    upk(fma2(sp, e2[j], g2[j]), a0, a1);
-                    p2[j] = pk(ex2(a0), ex2(a1));
-                    S2 = add2(S2, p2[j]);
-                }
-                float pt = TAIL ? ex2(fmaf(sv[r], et, gt)) : 0.f;
-                float S0, S1;
-                upk(S2, S0, S1);
-                float S = S0 + S1 + pt;
-                if (!(S >= 0x1p-100f && S <= 0x1p100f)) {  // exact max shift for this row
-                    float M = -INFINITY;
-#pragma unroll
-                    for (int k = 0; k < NCB; ++k)
-                        if (EXACT || k < nc) M = fmaxf(M, fmaf(sv[r], s.eh[k], gk[k]));
-                    S2 = 0ull;
-                    const f2 M2 = pk(M, M);
-#pragma unroll
-                    for (int j = 0; j < NP; ++j) {
-                        float a0, a1;
-                        upk(sub2(fma2(sp, e2[j], g2[j]), M2), a0, a1);
-                        p2[j] = pk(ex2(a0), ex2(a1));
-                        S2 = add2(S2, p2[j]);
-                    }
-                    pt = TAIL ? ex2(fmaf(sv[r], et, gt) - M) : 0.f;
-                    upk(S2, S0, S1);
-                    S = S0 + S1 + pt;
-                }
-                const float inv = rcp_approx(S);
+                float pt;
+                const float inv = p2_row<NCB, EXACT>(sv[r], e2, et, g2, gt, s.eh, gk, nc, p2, pt);
                 const f2 inv2 = pk(inv, inv);
 #pragma unroll
                 for (int j = 0; j < NP; ++j) cs2[j] = fma2(p2[j], inv2, cs2[j]);
@@ -252,7 +290,8 @@ __global__ void __launch_bounds__(512) p2_sweep_kernel(const P2Args a) {
             const float gref = __shfl_sync(FULL, gm[ref / 32], ref % 32);
 #pragma unroll
             for (int j = 0; j < GPL; ++j) gm[j] -= gref;
-            if (l == 0 && tid == 0) p2_stage(a, u + gridDim.x, b ^ 1, s.bar, s.rbuf, esz);
+            if (l == 0 && tid == 0 && u + u_step < u_end)
+                p2_stage(a, u + u_step, b ^ 1, s.bar, s.rbuf, esz);
         }
         if (warp == 0) {
 #pragma unroll
@@ -262,7 +301,56 @@ __global__ void __launch_bounds__(512) p2_sweep_kernel(const P2Args a) {
     }
 #pragma unroll
     for (int r = 0; r < R; ++r)
-        if (i0 + r < ld) a.part[(size_t)blockIdx.x * ld + i0 + r] = s.acc[i0 + r];
+        if (i0 + r < ld) part_row[i0 + r] = s.acc[i0 + r];
+    __syncthreads();  // shared arrays and the idle staging buffer are free for the next call
+}
+
+// Single market: CTA g sweeps consumers g, g + G, ... and writes partial row g.
+template <int NCB, int R, bool EXACT>
+__global__ void __launch_bounds__(512) p2_sweep_kernel(const P2Args a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SweepSmem s;
+    sweep_layout(NCB, EXACT ? NCB : a.nc, a.ld, blockDim.x >> 5, a.r_bf16 ? 2 : 4, &s, smem_raw);
+    if (a.st->stop) return;
+    if (threadIdx.x == 0) {
+        mbar_init(s.bar, 1);
+        mbar_init(s.bar + 1, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();  // mbarriers initialised before any wait
+    int par = 0, b = 0;
+    unsigned phase_bits = 0u;  // bit b: expected phase parity of staging buffer b
+    sweep_consumers<NCB, R, EXACT>(a, blockIdx.x, a.U, gridDim.x, a.part + (size_t)blockIdx.x * a.ld,
+                                   s, b, phase_bits, par);
+}
+
+// Batched markets: CTA g takes chunks g, g + G, ... of the launch's chunk list, each a range of
+// consumers of one market with its own partial row. The chunk's market arguments are staged in
+// shared memory and read from there.
+template <int NCB, int R, bool EXACT>
+__global__ void __launch_bounds__(512) p2_sweep_batch_kernel(const P2Batch bt) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ P2Args s_args;
+    SweepSmem s;
+    sweep_layout(NCB, NCB, bt.ld_max, blockDim.x >> 5, bt.esz, &s, smem_raw);
+    if (threadIdx.x == 0) {
+        mbar_init(s.bar, 1);
+        mbar_init(s.bar + 1, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();  // mbarriers initialised before any wait
+    int par = 0, b = 0;
+    unsigned phase_bits = 0u;
+    for (int c = blockIdx.x; c < bt.n_chunks; c += gridDim.x) {
+        const P2Chunk ch = bt.ch[c];
+        if (threadIdx.x == 0) s_args = bt.mk[ch.market];
+        __syncthreads();
+        if (!s_args.st->stop)
+            sweep_consumers<NCB, R, EXACT>(s_args, ch.u0, ch.u1, 1,
+                                           s_args.part + (size_t)ch.row * s_args.ld, s, b,
+                                           phase_bits, par);
+        __syncthreads();  // s_args is rewritten for the next chunk
+    }
 }
 
 // ---- implicit gradient -------------------------------------------------------------------------
@@ -360,36 +448,27 @@ __device__ __forceinline__ void gram_passes(const GradSmem& s, const P2Args& a,
     }
 }
 
-template <int NCB, int R, bool EXACT>
-__global__ void __launch_bounds__(512) p2_grad_kernel(const P2Args a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+// Implicit gradient of consumers u_first, u_first + u_step, ... < u_end of one market (one CTA);
+// dL/dtheta partials of those consumers written to part_row[0 .. ld).
+template <int NCB, bool EXACT>
+__device__ __forceinline__ void grad_consumers(const P2Args& a, int u_first, int u_end, int u_step,
+                                               float* __restrict__ part_row, const GradSmem& s,
+                                               int& b, unsigned& phase_bits) {
     const int nc = EXACT ? NCB : a.nc;
     const int np_ = ncp(nc), nx = ncx(nc, NCB), n = nc - 1;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int T = blockDim.x;
     const int I = a.I, ld = a.ld;
     const bool bf16 = a.r_bf16 != 0;
     const int esz = bf16 ? 2 : 4;
-    GradSmem s;
-    grad_layout(NCB, nc, ld, W, esz, &s, smem_raw);
 
-    if (a.st->stop) return;
-
-    if (tid == 0) {
-        mbar_init(s.bar, 1);
-        mbar_init(s.bar + 1, 1);
-        fence_mbar_init();
-    }
-    __syncthreads();  // mbarriers initialised before any wait
-    if (tid == 0) p2_stage(a, blockIdx.x, 0, s.bar, s.rbuf, esz);
+    if (tid == 0) p2_stage(a, u_first, b, s.bar, s.rbuf, esz);
     for (int i = tid; i < ld; i += T) s.acc[i] = 0.f;
     for (int k = tid; k < nx; k += T) {
         s.e[k] = k < nc ? a.e[k] : 0.f;
         s.eh[k] = k < nc ? a.e[k] - a.emax : 0.f;
     }
-    unsigned phase_bits = 0u;  // bit b: expected phase parity of staging buffer b
-    int b = 0;
-    for (int u = blockIdx.x; u < a.U; u += gridDim.x, b ^= 1) {
+    for (int u = u_first; u < u_end; u += u_step, b ^= 1) {
         if (!mbar_wait(s.bar + b, (phase_bits >> b) & 1u, 1u << 26)) {
             if (tid == 0) atomicOr(&a.st->err, 4);
         }
@@ -477,20 +556,67 @@ __global__ void __launch_bounds__(512) p2_grad_kernel(const P2Args a) {
             if (a.dr) a.dr[(size_t)u * I + i] = oi * v + wi * rho * a.inv_eps;
         }
         __syncthreads();  // staging buffer b^1 and the row arrays are free for the next consumer
-        if (tid == 0) p2_stage(a, u + gridDim.x, b ^ 1, s.bar, s.rbuf, esz);
+        if (tid == 0 && u + u_step < u_end) p2_stage(a, u + u_step, b ^ 1, s.bar, s.rbuf, esz);
     }
-    for (int i = tid; i < ld; i += T) a.part[(size_t)blockIdx.x * ld + i] = s.acc[i];
+    for (int i = tid; i < ld; i += T) part_row[i] = s.acc[i];
+    __syncthreads();  // shared arrays are free for the next call
+}
+
+// Launch structures as the sweep kernels: one market with CTA-strided consumers, or a chunk list.
+template <int NCB, int R, bool EXACT>
+__global__ void __launch_bounds__(512) p2_grad_kernel(const P2Args a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    GradSmem s;
+    grad_layout(NCB, EXACT ? NCB : a.nc, a.ld, blockDim.x >> 5, a.r_bf16 ? 2 : 4, &s, smem_raw);
+    if (a.st->stop) return;
+    if (threadIdx.x == 0) {
+        mbar_init(s.bar, 1);
+        mbar_init(s.bar + 1, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();  // mbarriers initialised before any wait
+    int b = 0;
+    unsigned phase_bits = 0u;
+    grad_consumers<NCB, EXACT>(a, blockIdx.x, a.U, gridDim.x, a.part + (size_t)blockIdx.x * a.ld, s,
+                               b, phase_bits);
+}
+
+template <int NCB, int R, bool EXACT>
+__global__ void __launch_bounds__(512) p2_grad_batch_kernel(const P2Batch bt) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ P2Args s_args;
+    GradSmem s;
+    grad_layout(NCB, NCB, bt.ld_max, blockDim.x >> 5, bt.esz, &s, smem_raw);
+    if (threadIdx.x == 0) {
+        mbar_init(s.bar, 1);
+        mbar_init(s.bar + 1, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();  // mbarriers initialised before any wait
+    int b = 0;
+    unsigned phase_bits = 0u;
+    for (int c = blockIdx.x; c < bt.n_chunks; c += gridDim.x) {
+        const P2Chunk ch = bt.ch[c];
+        if (threadIdx.x == 0) s_args = bt.mk[ch.market];
+        __syncthreads();
+        if (!s_args.st->stop)
+            grad_consumers<NCB, EXACT>(s_args, ch.u0, ch.u1, 1,
+                                       s_args.part + (size_t)ch.row * s_args.ld, s, b, phase_bits);
+        __syncthreads();
+    }
 }
 
 template <int NCB, int R, bool EXACT>
 P2Variant p2_make(int threads) {
-    P2Variant v;
+    P2Variant v{};
     v.ncb = NCB;
     v.rows = R;
     v.exact = EXACT;
     v.threads = threads;
     v.sweep = (const void*)p2_sweep_kernel<NCB, R, EXACT>;
     v.grad = (const void*)p2_grad_kernel<NCB, R, EXACT>;
+    v.sweep_b = (const void*)p2_sweep_batch_kernel<NCB, R, EXACT>;
+    v.grad_b = (const void*)p2_grad_batch_kernel<NCB, R, EXACT>;
     return v;
 }
 

@@ -14,12 +14,13 @@ constexpr int AD_ITEMS = 32, AD_WARPS = 8;
 
 // dL/dtheta_i = sum over the per-CTA partials (FP64, fixed order); its squared norm; the ascent
 // step of Algorithm 1 on theta (Adam as in PyTorch with maximize=True, or SGD) and w = exp(theta).
-__global__ void __launch_bounds__(AD_ITEMS* AD_WARPS) p2_adam_kernel(const P2AdamArgs a) {
+// bid / nb: this CTA's index among the nb CTAs that update one problem.
+__device__ __forceinline__ void adam_body(const P2AdamArgs& a, int bid, int nb) {
     __shared__ double s_sum[AD_WARPS][AD_ITEMS];
     __shared__ int s_last;
     if (a.st->stop) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int item = blockIdx.x * AD_ITEMS + lane;
+    const int item = bid * AD_ITEMS + lane;
     double acc = 0.0;
     if (item < a.I)
         for (int g = warp; g < a.G; g += AD_WARPS) acc += (double)a.part[(size_t)g * a.ld + item];
@@ -54,22 +55,34 @@ __global__ void __launch_bounds__(AD_ITEMS* AD_WARPS) p2_adam_kernel(const P2Ada
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) g2 += __shfl_xor_sync(FULL, g2, o);
-        if (lane == 0) a.blk[blockIdx.x] = g2;
+        if (lane == 0) a.blk[bid] = g2;
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&a.st->counter, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) s_last = atomicAdd(&a.st->counter, 1u) == (unsigned)nb - 1;
     __syncthreads();
     if (!s_last || warp != 0) return;
     __threadfence();
     double t = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(a.blk + b);
+    for (int b = lane; b < nb; b += 32) t += __ldcg(a.blk + b);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
     if (lane == 0) {
         *a.gn2_out = t;
         a.st->counter = 0u;
     }
+}
+
+__global__ void __launch_bounds__(AD_ITEMS* AD_WARPS) p2_adam_kernel(const P2AdamArgs a) {
+    adam_body(a, blockIdx.x, gridDim.x);
+}
+
+// Batched markets: block j updates block bmap[j].y of market bmap[j].x (a.nblk blocks each).
+__global__ void __launch_bounds__(AD_ITEMS* AD_WARPS)
+    p2_adam_batch_kernel(const P2AdamArgs* __restrict__ aa, const int2* __restrict__ bmap) {
+    const int2 mb = bmap[blockIdx.x];
+    const P2AdamArgs a = aa[mb.x];
+    adam_body(a, mb.y, a.nblk);
 }
 
 // Policy of consumers u0.. (one CTA each): x_ik = softmax_k(g^(L-1)'_k + s_i (e_k - e_max)),
@@ -141,8 +154,34 @@ cudaError_t p2_launch_grad(const P2Variant& v, const P2Args& a, cudaStream_t s) 
                             p2_grad_smem(v, a.nc, a.ld, a.r_bf16 ? 2 : 4), s);
 }
 
+size_t p2_sweep_smem_batch(const P2Variant& v, int ld_max, int esz) {
+    return p2::sweep_layout(v.ncb, v.ncb, ld_max, v.threads / 32, esz, nullptr, nullptr);
+}
+
+size_t p2_grad_smem_batch(const P2Variant& v, int ld_max, int esz) {
+    return p2::grad_layout(v.ncb, v.ncb, ld_max, v.threads / 32, esz, nullptr, nullptr);
+}
+
+cudaError_t p2_launch_sweep_batch(const P2Variant& v, const P2Batch& bt, int G, cudaStream_t s) {
+    void* args[] = {const_cast<P2Batch*>(&bt)};
+    return cudaLaunchKernel(v.sweep_b, dim3(G), dim3(v.threads), args,
+                            p2_sweep_smem_batch(v, bt.ld_max, bt.esz), s);
+}
+
+cudaError_t p2_launch_grad_batch(const P2Variant& v, const P2Batch& bt, int G, cudaStream_t s) {
+    void* args[] = {const_cast<P2Batch*>(&bt)};
+    return cudaLaunchKernel(v.grad_b, dim3(G), dim3(v.threads), args,
+                            p2_grad_smem_batch(v, bt.ld_max, bt.esz), s);
+}
+
 cudaError_t p2_launch_adam(const P2AdamArgs& a, cudaStream_t s) {
     p2_adam_kernel<<<p2_adam_blocks(a.I), AD_ITEMS * AD_WARPS, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t p2_launch_adam_batch(const P2AdamArgs* aa, const int2* bmap, int nblocks, cudaStream_t s) {
+    if (nblocks <= 0) return cudaSuccess;
+    p2_adam_batch_kernel<<<nblocks, AD_ITEMS * AD_WARPS, 0, s>>>(aa, bmap);
     return cudaGetLastError();
 }
 

@@ -73,6 +73,19 @@ def lib():
             "fr_launch_count": (i64, [_vp]),
             "fr_measure_ex2_rate": (i32, [_dp]),
             "fr_time_kernels": (i32, [_vp, i32, _dp]),
+            "fr_batch_create": (i32, [ct.POINTER(Config), i32, _vp, ct.POINTER(_vp)]),
+            "fr_batch_destroy": (i32, [_vp]),
+            "fr_batch_reset": (i32, [_vp]),
+            "fr_batch_set_relevance": (i32, [_vp, i32, _vp, i32, i64, i32]),
+            "fr_batch_set_exposure": (i32, [_vp, i32, _dp, i32]),
+            "fr_batch_autotune": (i32, [_vp]),
+            "fr_batch_step": (i32, [_vp, i32, _dp]),
+            "fr_batch_impacts": (i32, [_vp, i32, _dp, _dp, _dp]),
+            "fr_batch_policy": (i32, [_vp, i32, i32, i32, _vp, i32]),
+            "fr_batch_get_theta": (i32, [_vp, i32, _vp]),
+            "fr_batch_tuning": (i32, [_vp, ct.POINTER(i32), _vp, i32]),
+            "fr_batch_last_error": (ct.c_char_p, [_vp]),
+            "fr_batch_launch_count": (i64, [_vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -256,3 +269,97 @@ class FairRank:
 
     def launch_count(self) -> int:
         return lib().fr_launch_count(self.h)
+
+
+class FairRankBatch:
+    """Many independent FR_PARAM_ITEM markets advanced together (wraps an fr_batch).
+
+    sizes: sequence of (n_users, n_items, n_slots); overrides apply to every market's config."""
+
+    def __init__(self, sizes, **overrides):
+        L = lib()
+        n = len(sizes)
+        cfgs = (Config * n)()
+        for j, (U, I, K) in enumerate(sizes):
+            L.fr_config_default(ct.byref(cfgs[j]), U, I, K, PARAM_ITEM)
+            for k, v in overrides.items():
+                if not hasattr(cfgs[j], k):
+                    raise KeyError(k)
+                setattr(cfgs[j], k, v)
+        self.sizes = [tuple(x) for x in sizes]
+        self.M = n
+        h = ct.c_void_p()
+        st = L.fr_batch_create(cfgs, n, _current_stream(), ct.byref(h))
+        if st:
+            raise FairRankError(st, L.fr_batch_last_error(None).decode())
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().fr_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st:
+            raise FairRankError(st, lib().fr_batch_last_error(self.h).decode())
+
+    def set_relevance(self, market, r):
+        kind = str(getattr(r, "dtype", ""))
+        dt = {"float32": F32, "float64": F64, "uint16": BF16, "torch.float32": F32,
+              "torch.float64": F64, "torch.bfloat16": BF16}.get(kind)
+        if dt is None:
+            raise TypeError(f"unsupported relevance dtype {kind}")
+        p, dev, keep = _ptr(r)
+        self._check(lib().fr_batch_set_relevance(self.h, market, p, dt, r.shape[1], dev))
+
+    def set_exposure(self, market, e):
+        e = np.ascontiguousarray(e, dtype=np.float64)
+        self._check(lib().fr_batch_set_exposure(self.h, market, e.ctypes.data_as(_dp), e.shape[0]))
+
+    def reset(self):
+        self._check(lib().fr_batch_reset(self.h))
+
+    def autotune(self):
+        self._check(lib().fr_batch_autotune(self.h))
+
+    def step(self, n: int, trace: bool = True):
+        F = np.zeros((max(n, 1), self.M))
+        self._check(lib().fr_batch_step(self.h, n, F.ctypes.data_as(_dp) if trace else None))
+        return F[:n] if trace else None
+
+    def impacts(self, market):
+        imp = np.zeros(self.sizes[market][1])
+        util, F = ct.c_double(), ct.c_double()
+        self._check(lib().fr_batch_impacts(self.h, market, imp.ctypes.data_as(_dp), ct.byref(util),
+                                           ct.byref(F)))
+        return imp, util.value, F.value
+
+    def policy(self, market, u0=0, n_u=None):
+        U, I, K = self.sizes[market]
+        n_u = U - u0 if n_u is None else n_u
+        out = np.zeros((n_u, I, num_cols(I, K)), dtype=np.float32)
+        self._check(lib().fr_batch_policy(self.h, market, u0, n_u, ct.c_void_p(out.ctypes.data), 0))
+        return out
+
+    def theta(self, market):
+        out = np.zeros(self.sizes[market][1], dtype=np.float32)
+        self._check(lib().fr_batch_get_theta(self.h, market, ct.c_void_p(out.ctypes.data)))
+        return out
+
+    def tuning(self):
+        n = ct.c_int32()
+        self._check(lib().fr_batch_tuning(self.h, ct.byref(n), None, 0))
+        t = np.zeros((max(n.value, 1), 6), dtype=np.int32)
+        self._check(lib().fr_batch_tuning(self.h, ct.byref(n), ct.c_void_p(t.ctypes.data), n.value))
+        keys = ["n_cols_kernel", "markets", "max_items", "rows_per_thread", "threads",
+                "consumers_per_chunk"]
+        return [dict(zip(keys, map(int, row))) for row in t[:n.value]]
+
+    def launch_count(self) -> int:
+        return lib().fr_batch_launch_count(self.h)

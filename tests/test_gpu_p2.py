@@ -138,3 +138,15 @@ def test_bf16_precision_scale_sample():
     assert rel(F, oF) < NSW_RTOL
     for u in (0, 9, 15):
         np.testing.assert_allclose(g.policy(u, 1), o.policy(u, 1), atol=X_ATOL)
+
+
+def test_two_live_contexts_sharing_a_kernel():
+    """Two contexts whose shapes select the same kernel with different shared-memory sizes: the
+    larger one still launches after the smaller one was created (the limit is per kernel)."""
+    ra = synth.relevance_lowrank(4, 1000, seed=1).astype(np.float32)
+    rb = synth.relevance_lowrank(4, 300, seed=2).astype(np.float32)
+    a, oa = pair_item(4, 1000, 20, ra, sinkhorn_iters=20)
+    b, _ = pair_item(4, 300, 20, rb, sinkhorn_iters=20)
+    b.step(1)
+    Fa = a.step(2)
+    np.testing.assert_allclose(Fa, oa.step(2)[0], rtol=NSW_RTOL)
