@@ -347,8 +347,9 @@ def compare_batch(args):
     _, tune_s = _timed(b.autotune)
     b.step(2, trace=False)  # warm-up (graph capture)
     b.reset()
-    Fb, t_batch = _timed(lambda: b.step(S))
     l0 = b.launch_count()
+    Fb, t_batch = _timed(lambda: b.step(S))
+    launches = b.launch_count() - l0
     ctxs = []
     for (U, I, K), r in zip(sizes, rs):
         g = fr.FairRank(U, I, K, param=fr.PARAM_ITEM, sinkhorn_iters=L)
@@ -365,7 +366,7 @@ def compare_batch(args):
             "cells": cells, "cell_updates": cu, "batched_s": t_batch, "sequential_s": t_seq,
             "speedup": t_seq / t_batch, "batched_cell_updates_per_s": cu / t_batch,
             "sequential_cell_updates_per_s": cu / t_seq, "max_rel_F_diff_final": rel_F,
-            "autotune_s": tune_s, "buckets": b.tuning(), "launches_per_run": b.launch_count() - l0}
+            "autotune_s": tune_s, "buckets": b.tuning(), "launches_per_run": launches}
 
 
 def compare_unrolled(args):

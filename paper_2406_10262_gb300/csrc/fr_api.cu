@@ -36,6 +36,7 @@ struct fr_ctx {
     P2Variant var2{};
     int r_bf16 = 0;
     float emax = 0.f;
+    double esum = 0.0;  // sum of the K real exposures (uniform-policy impacts of the metrics)
     // free costs: C, Adam moments [U][nc][ld]; per-item: theta, moments, w = exp(theta) [ld]
     float *C = nullptr, *m1 = nullptr, *m2 = nullptr;
     float *theta = nullptr, *tm1 = nullptr, *tm2 = nullptr, *w = nullptr, *gpart = nullptr;
@@ -623,6 +624,8 @@ fr_status fr_set_exposure(fr_ctx* ctx, const double* e, int32_t K) {
     CU(cudaMemcpyAsync(ctx->log2b, lb.data(), sizeof(float) * ctx->nc, cudaMemcpyHostToDevice, ctx->s));
     CU(cudaStreamSynchronize(ctx->s));
     ctx->emax = emax;
+    ctx->esum = 0.0;
+    for (int k = 0; k < K; ++k) ctx->esum += e[k];
     ctx->have_e = true;
     ctx->fresh = false;
     return FR_OK;
@@ -829,9 +832,36 @@ fr_status fr_get_state(fr_ctx* ctx, float* param, float* m1, float* m2, float* g
 
 fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* better_pct,
                      double* worse_pct) {
-    (void)utility; (void)mean_envy; (void)better_pct; (void)worse_pct;
     if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
-    return fail(ctx, FR_EUNSUPPORTED, "evaluation metrics are not built yet");
+    Join j(ctx);
+    fr_status st = ensure_fresh(ctx);
+    if (st != FR_OK) return st;
+    // scratch in tmp: V [U][ld] floats | rmax [tiles][ld] floats | diag [ld] floats | ru [ld]
+    // doubles | out [3] doubles (16-byte aligned pieces)
+    const size_t ld = ctx->ld, nt = envy_tiles(ctx->I);
+    auto al = [](size_t b) { return (b + 15) / 16 * 16; };
+    const size_t oV = 0, oM = oV + al(4 * (size_t)ctx->U * ld), oD = oM + al(4 * nt * ld),
+                 oR = oD + al(4 * ld), oO = oR + al(8 * ld), need = oO + al(8 * 3);
+    if ((st = ensure_tmp(ctx, need)) != FR_OK) return st;
+    unsigned char* base = reinterpret_cast<unsigned char*>(ctx->tmp);
+    float* V = reinterpret_cast<float*>(base + oV);
+    double* out = reinterpret_cast<double*>(base + oO);
+    if (ctx->p2)
+        CU(launch_v_p2(p2_args(ctx, ctx->part), V, ctx->s));
+    else
+        CU(launch_v_p1(p1_args(ctx), V, ctx->s));
+    CU(launch_envy(ctx->r, ctx->r_bf16, V, ctx->U, ctx->I, ctx->ld, ctx->imp, ctx->esum,
+                   reinterpret_cast<float*>(base + oM), reinterpret_cast<float*>(base + oD),
+                   reinterpret_cast<double*>(base + oR), out, ctx->s));
+    ctx->launches += 4;
+    double h[3];
+    CU(cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, ctx->s));
+    if ((st = read_state(ctx)) != FR_OK) return st;
+    if (utility) *utility = ctx->st_host->utility;
+    if (mean_envy) *mean_envy = h[0];
+    if (better_pct) *better_pct = h[1];
+    if (worse_pct) *worse_pct = h[2];
+    return FR_OK;
 }
 
 fr_status fr_time_kernels(fr_ctx* ctx, int32_t n_steps, double* ms) {

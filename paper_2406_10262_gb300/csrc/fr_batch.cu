@@ -50,7 +50,7 @@ struct BBucket {
     int ncb = 0, exact = 0, warps8 = 0, I_max = 0, ld_max = 0;
     std::vector<int> markets;
     P2Variant var{};
-    int R = 8, cpc = kCpcMin, n_chunks = 0, G_sweep = 0, G_grad = 0;
+    int R = 8, cpc = kCpcMin, n_chunks = 0, G_sweep = 0, G_grad = 0, occ_sweep = 0, occ_grad = 0;
     P2Chunk* d_chunks = nullptr;
     size_t smem_sweep = 0, smem_grad = 0;
 };
@@ -224,6 +224,11 @@ fr_status configure_bucket(fr_batch* b, BBucket& k, int R, int cpc) {
     if (o1 < 1 || o2 < 1) return bfail(b, FR_EUNSUPPORTED, "bucket kernel does not fit on an SM");
     const std::vector<P2Chunk> ch = make_chunks(b, k, cpc);
     k.n_chunks = (int)ch.size();
+    k.occ_sweep = o1;
+    k.occ_grad = o2;
+    // every bucket's grid fills the GPU: concurrent launches of different shapes rarely share an
+    // SM (each needs its own shared-memory carveout), so grids sized as shares of the SMs were
+    // measured 3x slower than full grids whose tails overlap the next bucket's launch
     k.G_sweep = std::min(k.n_chunks, o1 * b->sms);
     k.G_grad = std::min(k.n_chunks, o2 * b->sms);
     cudaFree(k.d_chunks);

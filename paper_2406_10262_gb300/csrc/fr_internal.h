@@ -200,4 +200,15 @@ cudaError_t launch_relevance_check(const void* r, int r_bf16, int U, int I, int 
 cudaError_t launch_policy(const P1Args& a, int u0, int n_u, float* x_out, cudaStream_t s);
 cudaError_t launch_ex2_bench(float* sink, int blocks, int threads, int iters, cudaStream_t s);
 
+// evaluation metrics (fr_metrics.cu): v_ui = sum_{k<K} e_k x_uik into V [U][ld]; then the envy
+// contraction E = R^T V with its row-max epilogue, column sums of r and the ratio tests. out[3]:
+// mean max envy, % better off, % worse off. Scratch: rmax [envy_tiles(I)][ld] floats, diag [ld]
+// floats, ru [ld] doubles.
+int envy_tiles(int I);
+cudaError_t launch_v_p1(const P1Args& a, float* V, cudaStream_t s);
+cudaError_t launch_v_p2(const P2Args& a, float* V, cudaStream_t s);
+cudaError_t launch_envy(const void* r, int r_bf16, const float* V, int U, int I, int ld,
+                        const double* imp, double esum, float* rmax, float* diag, double* ru,
+                        double* out, cudaStream_t s);
+
 }  // namespace fr

@@ -1,0 +1,87 @@
+"""GPU evaluation metrics of Sec. 4.1 (fr_metrics: utility, mean max envy from the E = R^T V
+contraction with its fused row-max epilogue, better / worse off against the uniform policy) against
+the FP64 oracle's metrics on the same inputs and step counts."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import require_gpu
+from paper_2406_10262_gb300 import fairrank as fr
+from paper_2406_10262_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def problem(U, I, K, r, param, steps, **kw):
+    e = synth.dcg_exposure(K)
+    g = fr.FairRank(U, I, K, param=param, **kw)
+    g.set_relevance(np.ascontiguousarray(r, dtype=np.float32))
+    g.set_exposure(e)
+    okw = {"iters": kw["sinkhorn_iters"]} if "sinkhorn_iters" in kw else {}
+    o = oracle.Oracle(U, I, K, param=param, **okw)
+    o.set_relevance(np.asarray(r, dtype=np.float32).astype(np.float64))
+    o.set_exposure(e)
+    if steps:
+        g.step(steps)
+        o.step(steps)
+    return g, o
+
+
+def check(g, o, r, K):
+    m = g.metrics()
+    om = o.metrics()
+    imp, _, _ = o.impacts()
+    assert abs(m["utility"] - om["utility"]) <= 1e-6 * abs(om["utility"])
+    assert abs(m["mean_envy"] - om["mean_envy"]) <= 1e-5 * imp.mean() + 1e-6 * om["mean_envy"]
+    assert m["mean_envy"] >= 0.0
+    # ratio tests: items whose oracle ratio lies within 1e-5 of a threshold may go either way
+    unif = np.asarray(r, np.float64).sum(0) * synth.dcg_exposure(K).sum() / imp.size
+    ratio = imp / unif
+    amb = np.sum((np.abs(ratio / 1.1 - 1) < 1e-5) | (np.abs(ratio / 0.9 - 1) < 1e-5))
+    tol = 100.0 * amb / imp.size + 1e-9
+    assert abs(m["better_pct"] - om["better_pct"]) <= tol
+    assert abs(m["worse_pct"] - om["worse_pct"]) <= tol
+    return m, om
+
+
+@pytest.mark.parametrize("U,I,K,steps", [(30, 120, 10, 20), (9, 40, 40, 15), (5, 37, 3, 0)])
+def test_metrics_free_costs(U, I, K, steps):
+    r = synth.relevance_lowrank(U, I, seed=U + I)
+    g, o = problem(U, I, K, r, fr.PARAM_FULL_C, steps)
+    check(g, o, r, K)
+
+
+@pytest.mark.parametrize("U,I,K,steps,bf16", [(25, 300, 20, 10, False), (12, 129, 5, 5, True)])
+def test_metrics_item_param(U, I, K, steps, bf16):
+    r = synth.relevance_lowrank(U, I, seed=3 * U + I).astype(np.float32)
+    if bf16:
+        bits = synth.to_bf16_bits(r)
+        g = fr.FairRank(U, I, K, param=fr.PARAM_ITEM, rel_dtype=fr.BF16)
+        g.set_relevance(bits)
+        g.set_exposure(synth.dcg_exposure(K))
+        r = synth.bf16_bits_to_f64(bits)
+        o = oracle.Oracle(U, I, K, param=oracle.PARAM_ITEM)
+        o.set_relevance(r)
+        o.set_exposure(synth.dcg_exposure(K))
+        g.step(steps)
+        o.step(steps)
+    else:
+        g, o = problem(U, I, K, r, fr.PARAM_ITEM, steps)
+    check(g, o, r, K)
+
+
+def test_metrics_plain_workload_after_solve():
+    """2000 consumers x 1000 items, K = 10: metrics of the initial policy and after 30 steps."""
+    U, I, K = 2000, 1000, 10
+    r = synth.workload_relevance("plain2000x1000").astype(np.float32)
+    g, o = problem(U, I, K, r, fr.PARAM_FULL_C, 0)
+    m, om = check(g, o, r, K)
+    assert m["worse_pct"] == om["worse_pct"] == 0.0  # the uniform policy itself
+    g.step(30)
+    o.step(30)
+    check(g, o, r, K)
