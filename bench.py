@@ -176,6 +176,28 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+# ---- multi-rank host logic (independent markets per rank, weak scaling) -----------------------
+def rank_relevance(w, rank):
+    """Rank `rank`'s market: the workload's relevance generator with seed = rank."""
+    from paper_2406_10262_gb300 import synth
+    return synth.relevance_lowrank(w["n_users"], w["n_items"], seed=rank).astype(np.float32)
+
+
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time: the whole job ends when the last rank does."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Units all ranks processed per second (every rank does the same work)."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 # ---- our arm ------------------------------------------------------------------------------
 def run_ours(args, w):
     import torch
@@ -195,7 +217,7 @@ def run_ours(args, w):
 
     U, I, K, L, S = w["n_users"], w["n_items"], w["n_slots"], w["iters"], w["steps"]
     nc = w["n_cols"]
-    r = synth.relevance_lowrank(U, I, seed=rank).astype(np.float32)
+    r = rank_relevance(w, rank)
     e = synth.dcg_exposure(K)
     g = fr.FairRank(U, I, K, sinkhorn_iters=L, lr=0.1)
     g.set_relevance(r)
@@ -232,12 +254,8 @@ def run_ours(args, w):
     barrier()
     launches = g.launch_count() - l0
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * cu_per_solve / (ms * 1e-3)
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dist, "cuda")
+    value = whole_job_rate(cu_per_solve, world, ms)
 
     # ---- time to NSW within 1e-5 of the FP64 oracle's F after the full step budget ----------
     F_ref = golden_F_ref(args.workload) if rank == 0 else None
@@ -305,7 +323,7 @@ def run_ours(args, w):
             "time_to_nsw_s": ttn, "time_to_nsw_step": first, "nsw_final": float(trace[-1]),
             "nsw_ref_fp64": F_ref,
             "nsw_rel_err_final": None if F_ref is None else abs(float(trace[-1]) - F_ref) / abs(F_ref),
-            "e2e": {"value": world * cu_per_solve / (e2e_ms * 1e-3), "unit": UNIT,
+            "e2e": {"value": whole_job_rate(cu_per_solve, world, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": launches, "roofline": roof, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -115,6 +115,12 @@ __device__ __forceinline__ void ldv(float (&d)[R], const float* p) {
     } else if constexpr (R == 4) {
         float4 v = *reinterpret_cast<const float4*>(p);
         d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+    } else if constexpr (R == 6) {  // 24-byte stride: three 8-byte loads
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float2 v = reinterpret_cast<const float2*>(p)[j];
+            d[2 * j] = v.x; d[2 * j + 1] = v.y;
+        }
     } else {
         static_assert(R == 8, "R");
         float4 v = reinterpret_cast<const float4*>(p)[0];
@@ -132,6 +138,9 @@ __device__ __forceinline__ void stv(float* p, const float (&d)[R]) {
         *reinterpret_cast<float2*>(p) = make_float2(d[0], d[1]);
     } else if constexpr (R == 4) {
         *reinterpret_cast<float4*>(p) = make_float4(d[0], d[1], d[2], d[3]);
+    } else if constexpr (R == 6) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) reinterpret_cast<float2*>(p)[j] = make_float2(d[2 * j], d[2 * j + 1]);
     } else {
         static_assert(R == 8, "R");
         reinterpret_cast<float4*>(p)[0] = make_float4(d[0], d[1], d[2], d[3]);
