@@ -56,6 +56,11 @@ def parse():
                     help="profiling driver: set up the workload, run this many ascent steps, exit")
     ap.add_argument("--compare", choices=["batch", "unrolled", "bf16"], default=None,
                     help="compare a layered form against the plain FP32 method (one JSON line)")
+    ap.add_argument("--profile-item", choices=["implicit", "unrolled", "bf16", "batch"], default=None,
+                    help="profiling driver for the per-item forms: set up the workload, run "
+                         "--profile-steps ascent steps, exit")
+    ap.add_argument("--profile-users", type=int, default=0,
+                    help="with --profile-item: override the number of consumers (small captures)")
     return ap.parse_args()
 
 
@@ -453,8 +458,48 @@ def compare_bf16(args):
     return out
 
 
+def profile_item(args):
+    """Sets up one per-item workload and runs --profile-steps ascent steps (for ncu captures):
+    implicit / unrolled: 20000 x 2000, K = 20, L = 100 (checkpoints every 10); bf16: 200000 x 10^4,
+    K = 20, L = 50, BF16 relevance; batch: the 256-market workload, L = 50."""
+    import torch
+    from paper_2406_10262_gb300 import fairrank as fr
+    from paper_2406_10262_gb300 import synth
+    n = max(args.profile_steps, 1)
+    if args.profile_item == "batch":
+        ms = synth.markets(256, seed=0)
+        sizes = [(m.n_users, m.n_items, m.n_slots) for m in ms]
+        b = fr.FairRankBatch(sizes, sinkhorn_iters=50)
+        for j, m in enumerate(ms):
+            b.set_relevance(j, synth.relevance_lowrank_fast(m.n_users, m.n_items, seed=m.seed))
+            b.set_exposure(j, synth.dcg_exposure(m.n_slots))
+        b.step(n, trace=False)
+        launches = b.launch_count()
+    else:
+        bf16 = args.profile_item == "bf16"
+        U, I, K, L = (200000, 10000, 20, 50) if bf16 else (20000, 2000, 20, 100)
+        U = args.profile_users or U
+        r = synth.relevance_lowrank_fast(U, I, seed=0, boost_frac=0.05 if bf16 else 0.0)
+        mode = fr.GRAD_UNROLLED if args.profile_item == "unrolled" else fr.GRAD_IMPLICIT
+        g = fr.FairRank(U, I, K, param=fr.PARAM_ITEM, sinkhorn_iters=L, grad_mode=mode,
+                        ckpt_every=10, rel_dtype=fr.BF16 if bf16 else fr.F32)
+        g.set_relevance(synth.to_bf16_bits(r) if bf16 else r)
+        g.set_exposure(synth.dcg_exposure(K))
+        g.step(n, trace=False)
+        launches = g.launch_count()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_item": args.profile_item, "profile_steps": n, "launches": launches}))
+
+
 def main():
     args = parse()
+    if args.profile_item:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        from paper_2406_10262_gb300 import build as frbuild
+        frbuild.build()
+        profile_item(args)
+        return
     if args.compare:
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))

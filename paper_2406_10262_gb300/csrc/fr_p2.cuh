@@ -124,7 +124,7 @@ __device__ __forceinline__ float p2_row(float sv, const f2* e2, float et, const 
     float S0, S1;
     upk(S2, S0, S1);
     float S = S0 + S1 + pt;
-    if (!(S >= 0x1p-100f && S <= 0x1p100f)) {  // exact max shift for this row
+    if (__builtin_expect(!(S >= 0x1p-100f && S <= 0x1p100f), 0)) {  // exact max shift for this row
         float M = -INFINITY;
 #pragma unroll
         for (int k = 0; k < NCB; ++k)
@@ -172,6 +172,79 @@ __device__ __forceinline__ void column_sum(float (&cs)[NCB], float (&out)[GPL], 
             for (int ww = 0; ww < W; ++ww) sum += buf[ww * P + col];
         out[j] = sum;
     }
+}
+
+// One Sinkhorn iteration of one consumer (LAST: also the policy's impact contributions and gP).
+template <int NCB, int R, bool EXACT, bool LAST>
+__device__ __forceinline__ void sweep_iter(const P2Args& a, const SweepSmem& s, int l, int u,
+                                           int u_step, int u_end, int b, int esz, bool bf16,
+                                           const unsigned char* rrow, const f2* e2, float et,
+                                           const float (&sv)[R], const bool (&vr)[R],
+                                           float (&gm)[(NCB + 31) / 32], int& par, int i0, int nc,
+                                           int lane, int warp, int W, int tid) {
+    constexpr int GPL = (NCB + 31) / 32;
+    constexpr int NP = NCB / 2;
+    constexpr bool TAIL = NCB % 2 == 1;
+    const int ref = nc - 1;
+    if (warp == 0) {
+#pragma unroll
+        for (int j = 0; j < GPL; ++j) {
+            const int col = j * 32 + lane;
+            if (col >= nc) continue;
+            if (LAST) a.gP[(size_t)u * nc + col] = gm[j];
+            if (a.ck && l % a.ce == 0)  // g^(l), the start of segment l / ce
+                a.ck[((size_t)u * a.nck + l / a.ce) * nc + col] = gm[j];
+        }
+    }
+    float gk[NCB];
+    bcast_g<NCB, GPL>(gm, gk);
+    if (!EXACT) {
+#pragma unroll
+        for (int k = 0; k < NCB; ++k)
+            if (k >= nc) gk[k] = -INFINITY;  // padding columns: 2^(-inf) = 0
+    }
+    f2 g2[NP > 0 ? NP : 1];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) g2[j] = pk(gk[2 * j], gk[2 * j + 1]);
+    const float gt = TAIL ? gk[NCB - 1] : 0.f;
+    f2 cs2[NP > 0 ? NP : 1];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) cs2[j] = 0ull;
+    float cst = 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (!vr[r]) continue;
+        f2 p2[NP > 0 ? NP : 1];
+        float pt;
+        const float inv = p2_row<NCB, EXACT>(sv[r], e2, et, g2, gt, s.eh, gk, nc, p2, pt);
+        const f2 inv2 = pk(inv, inv);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) cs2[j] = fma2(p2[j], inv2, cs2[j]);
+        cst = fmaf(pt, inv, cst);
+        if (LAST) {
+            float v = 0.f;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                float p0, p1;
+                upk(p2[j], p0, p1);
+                if (2 * j < a.K) v += s.e[2 * j] * p0;
+                if (2 * j + 1 < a.K) v += s.e[2 * j + 1] * p1;
+            }
+            if (TAIL && NCB - 1 < a.K) v += s.e[NCB - 1] * pt;
+            s.acc[i0 + r] += load_r(rrow, i0 + r, bf16) * (v * inv);
+        }
+    }
+    float cs[NCB];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) upk(cs2[j], cs[2 * j], cs[2 * j + 1]);
+    if (TAIL) cs[NCB - 1] = cst;
+    column_update<NCB, GPL>(cs, gm, nc, s.red, s.l2b, par, lane, warp, W);
+    par ^= 1;
+    // re-reference the potentials to the last column (x is invariant to a common shift)
+    const float gref = __shfl_sync(FULL, gm[ref / 32], ref % 32);
+#pragma unroll
+    for (int j = 0; j < GPL; ++j) gm[j] -= gref;
+    if (l == 0 && tid == 0 && u + u_step < u_end) p2_stage(a, u + u_step, b ^ 1, s.bar, s.rbuf, esz);
 }
 
 // Sinkhorn sweep of consumers u_first, u_first + u_step, ... < u_end of one market (one CTA), impact
@@ -230,69 +303,11 @@ __device__ __forceinline__ void sweep_consumers(const P2Args& a, int u_first, in
             const int col = j * 32 + lane;
             gm[j] = (a.warm && col < nc) ? a.gL[(size_t)u * nc + col] : 0.f;
         }
-        for (int l = 0; l < a.L; ++l) {
-            const bool last = l == a.L - 1;
-            if (warp == 0) {
-#pragma unroll
-                for (int j = 0; j < GPL; ++j) {
-                    const int col = j * 32 + lane;
-                    if (col >= nc) continue;
-                    if (last) a.gP[(size_t)u * nc + col] = gm[j];
-                    if (a.ck && l % a.ce == 0)  // g^(l), the start of segment l / ce
-                        a.ck[((size_t)u * a.nck + l / a.ce) * nc + col] = gm[j];
-                }
-            }
-            float gk[NCB];
-            bcast_g<NCB, GPL>(gm, gk);
-            if (!EXACT) {
-#pragma unroll
-                for (int k = 0; k < NCB; ++k)
-                    if (k >= nc) gk[k] = -INFINITY;  // padding columns: 2^(-inf) = 0
-            }
-            f2 g2[NP > 0 ? NP : 1];
-#pragma unroll
-            for (int j = 0; j < NP; ++j) g2[j] = pk(gk[2 * j], gk[2 * j + 1]);
-            const float gt = TAIL ? gk[NCB - 1] : 0.f;
-            f2 cs2[NP > 0 ? NP : 1];
-#pragma unroll
-            for (int j = 0; j < NP; ++j) cs2[j] = 0ull;
-            float cst = 0.f;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if (!vr[r]) continue;
-                f2 p2[NP > 0 ? NP : 1];
-                float pt;
-                const float inv = p2_row<NCB, EXACT>(sv[r], e2, et, g2, gt, s.eh, gk, nc, p2, pt);
-                const f2 inv2 = pk(inv, inv);
-#pragma unroll
-                for (int j = 0; j < NP; ++j) cs2[j] = fma2(p2[j], inv2, cs2[j]);
-                cst = fmaf(pt, inv, cst);
-                if (last) {
-                    float v = 0.f;
-#pragma unroll
-                    for (int j = 0; j < NP; ++j) {
-                        float p0, p1;
-                        upk(p2[j], p0, p1);
-                        if (2 * j < a.K) v += s.e[2 * j] * p0;
-                        if (2 * j + 1 < a.K) v += s.e[2 * j + 1] * p1;
-                    }
-                    if (TAIL && NCB - 1 < a.K) v += s.e[NCB - 1] * pt;
-                    s.acc[i0 + r] += load_r(rrow, i0 + r, bf16) * (v * inv);
-                }
-            }
-            float cs[NCB];
-#pragma unroll
-            for (int j = 0; j < NP; ++j) upk(cs2[j], cs[2 * j], cs[2 * j + 1]);
-            if (TAIL) cs[NCB - 1] = cst;
-            column_update<NCB, GPL>(cs, gm, nc, s.red, s.l2b, par, lane, warp, W);
-            par ^= 1;
-            // re-reference the potentials to the last column (x is invariant to a common shift)
-            const float gref = __shfl_sync(FULL, gm[ref / 32], ref % 32);
-#pragma unroll
-            for (int j = 0; j < GPL; ++j) gm[j] -= gref;
-            if (l == 0 && tid == 0 && u + u_step < u_end)
-                p2_stage(a, u + u_step, b ^ 1, s.bar, s.rbuf, esz);
-        }
+        for (int l = 0; l < a.L - 1; ++l)
+            sweep_iter<NCB, R, EXACT, false>(a, s, l, u, u_step, u_end, b, esz, bf16, rrow, e2, et, sv,
+                                             vr, gm, par, i0, nc, lane, warp, W, tid);
+        sweep_iter<NCB, R, EXACT, true>(a, s, a.L - 1, u, u_step, u_end, b, esz, bf16, rrow, e2, et,
+                                        sv, vr, gm, par, i0, nc, lane, warp, W, tid);
         if (warp == 0) {
 #pragma unroll
             for (int j = 0; j < GPL; ++j)
