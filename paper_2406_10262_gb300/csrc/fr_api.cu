@@ -838,7 +838,7 @@ fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* be
     if (st != FR_OK) return st;
     // scratch in tmp: V [U][ld] floats | rmax [tiles][ld] floats | diag [ld] floats | ru [ld]
     // doubles | out [3] doubles (16-byte aligned pieces)
-    const size_t ld = ctx->ld, nt = envy_tiles(ctx->I);
+    const size_t ld = ctx->ld, nt = std::max(envy_tiles(ctx->I), envy_tc_tiles(ctx->I));
     auto al = [](size_t b) { return (b + 15) / 16 * 16; };
     const size_t oV = 0, oM = oV + al(4 * (size_t)ctx->U * ld), oD = oM + al(4 * nt * ld),
                  oR = oD + al(4 * ld), oO = oR + al(8 * ld), need = oO + al(8 * 3);
@@ -850,13 +850,17 @@ fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* be
         CU(launch_v_p2(p2_args(ctx, ctx->part), V, ctx->s));
     else
         CU(launch_v_p1(p1_args(ctx), V, ctx->s));
+    CU(cudaMemsetAsync(ctx->flags, 0, sizeof(int) * 4, ctx->s));
     CU(launch_envy(ctx->r, ctx->r_bf16, V, ctx->U, ctx->I, ctx->ld, ctx->imp, ctx->esum,
                    reinterpret_cast<float*>(base + oM), reinterpret_cast<float*>(base + oD),
-                   reinterpret_cast<double*>(base + oR), out, ctx->s));
+                   reinterpret_cast<double*>(base + oR), out, ctx->flags, true, ctx->s));
     ctx->launches += 4;
     double h[3];
+    int hf[4];
     CU(cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, ctx->s));
+    CU(cudaMemcpyAsync(hf, ctx->flags, sizeof hf, cudaMemcpyDeviceToHost, ctx->s));
     if ((st = read_state(ctx)) != FR_OK) return st;
+    if (hf[0] & 4) return fail(ctx, FR_ETIMEOUT, "a bounded wait of the envy contraction expired");
     if (utility) *utility = ctx->st_host->utility;
     if (mean_envy) *mean_envy = h[0];
     if (better_pct) *better_pct = h[1];

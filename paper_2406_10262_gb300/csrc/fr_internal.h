@@ -204,11 +204,17 @@ cudaError_t launch_ex2_bench(float* sink, int blocks, int threads, int iters, cu
 // contraction E = R^T V with its row-max epilogue, column sums of r and the ratio tests. out[3]:
 // mean max envy, % better off, % worse off. Scratch: rmax [envy_tiles(I)][ld] floats, diag [ld]
 // floats, ru [ld] doubles.
+// tensor_cores: the tcgen05 contraction (fr_envy_tc.cu, 128-item tiles, three TF32 products,
+// bounded waits report bit 4 in *err) instead of the FP32 SIMT one (64-item tiles).
 int envy_tiles(int I);
+int envy_tc_tiles(int I);
+size_t envy_tc_smem();
 cudaError_t launch_v_p1(const P1Args& a, float* V, cudaStream_t s);
 cudaError_t launch_v_p2(const P2Args& a, float* V, cudaStream_t s);
+cudaError_t launch_envy_tc(const void* r, int r_bf16, const float* V, int U, int I, int ld,
+                           float* rmax, float* diag, int* err, cudaStream_t s);
 cudaError_t launch_envy(const void* r, int r_bf16, const float* V, int U, int I, int ld,
                         const double* imp, double esum, float* rmax, float* diag, double* ru,
-                        double* out, cudaStream_t s);
+                        double* out, int* err, bool tensor_cores, cudaStream_t s);
 
 }  // namespace fr

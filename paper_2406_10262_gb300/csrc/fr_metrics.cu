@@ -209,10 +209,17 @@ cudaError_t launch_v_p2(const P2Args& a, float* V, cudaStream_t s) {
 
 cudaError_t launch_envy(const void* r, int r_bf16, const float* V, int U, int I, int ld,
                         const double* imp, double esum, float* rmax, float* diag, double* ru,
-                        double* out, cudaStream_t s) {
-    const int nt = envy_tiles(I);
-    envy_gemm_kernel<<<dim3(nt, nt), 256, 0, s>>>(r, r_bf16, V, U, I, ld, rmax, diag);
-    cudaError_t e = cudaGetLastError();
+                        double* out, int* err, bool tensor_cores, cudaStream_t s) {
+    int nt;
+    cudaError_t e;
+    if (tensor_cores) {
+        nt = envy_tc_tiles(I);
+        e = launch_envy_tc(r, r_bf16, V, U, I, ld, rmax, diag, err, s);
+    } else {
+        nt = envy_tiles(I);
+        envy_gemm_kernel<<<dim3(nt, nt), 256, 0, s>>>(r, r_bf16, V, U, I, ld, rmax, diag);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return e;
     colsum_kernel<<<(I + 255) / 256, 256, 0, s>>>(r, r_bf16, U, I, ld, ru);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
