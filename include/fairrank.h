@@ -150,7 +150,11 @@ FR_API fr_status fr_get_state(fr_ctx* ctx, float* param, float* m1, float* m2, f
 
 /* Evaluation metrics of Sec. 4.1 at the current policy (host doubles, each nullable): user
    utility, mean max envy (1/|I|) sum_i max_j (Imp_i(X_j) - Imp_i(X_i)), and the percentage of
-   items whose impact is more than 10% above / below that of the uniform policy x_uik = b_k/|I|. */
+   items whose impact is more than 10% above / below that of the uniform policy x_uik = b_k/|I|.
+   Imp_i(X_j) = sum_u r(u,i) sum_{k<K} e_k x_ujk is formed on the tensor cores from three TF32
+   products per term (hi*hi + hi*lo + lo*hi of each operand's TF32 split), accumulated in FP32: the
+   error is that of an FP32 contraction. Needs n_users x n_items x 4 bytes of scratch (allocated on
+   first use). FR_ETIMEOUT if a bounded device wait of the contraction expired. */
 FR_API fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* better_pct,
                      double* worse_pct);
 

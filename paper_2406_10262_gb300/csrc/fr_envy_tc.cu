@@ -10,7 +10,7 @@
 // kind::tf32) and tracked by an mbarrier through tcgen05.commit. Operands live in shared memory in
 // the K-major, no-swizzle canonical layout: 8-row x 16-byte core matrices, core matrices adjacent
 // in K 128 bytes apart (leading byte offset), 8-row groups 1024 bytes apart (stride byte offset).
-// The CTA's 128 threads stage the next 32 consumers (two buffers) while the tensor cores work on the
+// The CTA's 512 threads stage the next 32 consumers (two buffers) while the tensor cores work on the
 // current ones. The epilogue reads the accumulator rows back from tensor memory (tcgen05.ld,
 // 32 lanes per warp) and keeps only the row maxima over the tile's valid columns and, on diagonal
 // tiles, E_ii: the |I|^2 matrix is never written.
@@ -36,6 +36,8 @@ constexpr int LBO = 128;                      // bytes between K-adjacent core m
 constexpr int SBO = (TK / 4) * 128;           // bytes between 8-row groups
 constexpr unsigned kPolls = 1u << 20;
 constexpr unsigned kTmemCols = 128;           // FP32 accumulator: one column per tile column
+constexpr int NTHREADS = 512;                 // staging threads (warps 0-3 also run the epilogue)
+constexpr int KGROUPS = NTHREADS / TM;        // groups of 4 consumers per stage per thread row
 
 static_assert(TM == 128 && TN % 16 == 0 && TN >= 16 && TN <= 256, "MMA shape");
 static_assert(TN == TM, "square tiles (diagonal capture)");
@@ -85,14 +87,15 @@ __device__ __forceinline__ void mma_commit(unsigned long long* bar) {
 }
 
 // Stage 32 consumers of the tile: A[m][k] = r(u0 + k, i0 + m), B[n][k] = v(u0 + k, j0 + n), each
-// split into TF32 hi and lo parts. Thread t owns row t of both operands; 4 consumers per 16-byte
-// store.
+// split into TF32 hi and lo parts. Thread t owns row t % 128 of both operands and the groups of 4
+// consumers g = t / 128 + KGROUPS q; one 16-byte store per group and part.
 __device__ __forceinline__ void stage_tile(unsigned char* st, const void* r, int r_bf16,
                                            const float* V, int U, int ld, int i0, int j0, int u0) {
-    const int t = threadIdx.x;
+    const int t = threadIdx.x % TM, g0 = threadIdx.x / TM;
     const int i = i0 + t, j = j0 + t;
 #pragma unroll
-    for (int k4 = 0; k4 < TK; k4 += 4) {
+    for (int q2 = 0; q2 < TK / 4 / KGROUPS; ++q2) {
+        const int k4 = 4 * (g0 + KGROUPS * q2);
         float ra[4], va[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -117,7 +120,7 @@ __device__ __forceinline__ void stage_tile(unsigned char* st, const void* r, int
     }
 }
 
-__global__ void __launch_bounds__(TM, 1) envy_tc_kernel(const void* __restrict__ r, int r_bf16,
+__global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const void* __restrict__ r, int r_bf16,
                                                         const float* __restrict__ V, int U, int I,
                                                         int ld, float* __restrict__ rmax,
                                                         float* __restrict__ diag, int* err) {
@@ -184,7 +187,7 @@ __global__ void __launch_bounds__(TM, 1) envy_tc_kernel(const void* __restrict__
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!__syncthreads_and(ok)) {
         if (tid == 0) atomicOr(err, 4);
-    } else {
+    } else if (warp < TM / 32) {
         // epilogue: warp w reads accumulator lanes 32w .. 32w + 31 (tile rows), 32 columns at a time
         const int il = warp * 32 + lane;
         const int i = i0 + il;
@@ -233,7 +236,8 @@ cudaError_t launch_envy_tc(const void* r, int r_bf16, const float* V, int U, int
     const int nt = envy_tc_tiles(I);
     cudaError_t e = raise_smem_limit((const void*)envy_tc_kernel, envy_tc_smem());
     if (e != cudaSuccess) return e;
-    envy_tc_kernel<<<dim3(nt, nt), TM, envy_tc_smem(), s>>>(r, r_bf16, V, U, I, ld, rmax, diag, err);
+    envy_tc_kernel<<<dim3(nt, nt), NTHREADS, envy_tc_smem(), s>>>(r, r_bf16, V, U, I, ld, rmax, diag,
+                                                                 err);
     return cudaGetLastError();
 }
 
