@@ -8,13 +8,15 @@ consumer per step, 500 ascent steps. One benchmark step is one whole solve: rese
 initial Sinkhorn solve and 500 ascent steps, i.e. 501 x 50 Sinkhorn iterations over every cell.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-    python bench.py --compare batch|unrolled|bf16 [--steps K]
+    python bench.py --compare batch|unrolled|bf16|paper-shapes [--steps K]
 
 --compare runs one of the layered forms against the plain FP32 method on the same GPU and prints
 one JSON line: 256 markets batched vs solved one after another (|U| ~ U[100, 4000], |I| ~
 U[100, 2000], K in {5, 10, 20}); the unrolled adjoint gradient vs the implicit gradient (|U| =
 20000, |I| = 2000, K = 20, L = 100, checkpoints every 10); BF16 vs FP32 relevance storage (|U| =
-200000, |I| = 10^4, K = 20, rank-32 sigmoid relevance with 5% boosted items).
+200000, |I| = 10^4, K = 20, rank-32 sigmoid relevance with 5% boosted items); paper-shapes times
+the free-cost method on the shapes of the paper's timing figure (|U|, |I| around 250, K = 10)
+next to the FP64 oracle on the host cores.
 
 Under torchrun (N > 1) every rank solves its own independent market (seed = rank): weak scaling
 with no collective on the data path; the timing is the max over ranks.
@@ -54,7 +56,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling driver: set up the workload, run this many ascent steps, exit")
-    ap.add_argument("--compare", choices=["batch", "unrolled", "bf16"], default=None,
+    ap.add_argument("--compare", choices=["batch", "unrolled", "bf16", "paper-shapes"], default=None,
                     help="compare a layered form against the plain FP32 method (one JSON line)")
     ap.add_argument("--profile-item", choices=["implicit", "unrolled", "bf16", "batch"], default=None,
                     help="profiling driver for the per-item forms: set up the workload, run "
@@ -73,7 +75,8 @@ def workload(name):
 
 def recorded_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the kernel
-    sources changed since that capture (their SHA-256 no longer matches)."""
+    sources changed since that capture (their SHA-256 no longer matches). A source "file#Name"
+    hashes only struct Name of that file."""
     import hashlib
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
@@ -83,7 +86,12 @@ def recorded_traffic(kernel):
         return None
     h = hashlib.sha256()
     for src in rec["sources"]:
-        h.update(open(os.path.join(ROOT, src), "rb").read())
+        path, _, block = src.partition("#")
+        text = open(os.path.join(ROOT, path), "rb").read()
+        if block:  # only the named struct of a shared header (the kernel's argument / state layout)
+            start = text.index(("struct " + block + " {").encode())
+            text = text[start:text.index(b"};", start) + 2]
+        h.update(text)
     return rec["dram_bytes_per_launch"] if h.hexdigest() == rec["sources_sha256"] else None
 
 
@@ -458,6 +466,42 @@ def compare_bf16(args):
     return out
 
 
+def compare_paper_shapes(args):
+    """Computation time per ascent step of the free-cost method (the paper's Algorithm 1, K = 10,
+    m = 11, L = 50) on the shapes of the paper's timing figure: |U| swept at |I| = 250 and |I|
+    swept at |U| = 250, the GPU (100 steps under the step graphs) next to the FP64 oracle on the
+    host cores (cpu_baseline leg: 3 steps per shape, per-step time)."""
+    import oracle
+    from paper_2406_10262_gb300 import fairrank as fr
+    from paper_2406_10262_gb300 import synth
+    K, L, S = 10, 50, 100
+    cores = os.cpu_count() or 1
+    shapes = [(U, 250) for U in (250, 500, 1000, 2000, 4000)] + [(250, I) for I in (500, 1000, 2000)]
+    points = []
+    for U, I in shapes:
+        r = synth.relevance_lowrank(U, I, seed=5).astype(np.float32)
+        e = synth.dcg_exposure(K)
+        g = fr.FairRank(U, I, K, sinkhorn_iters=L, lr=0.1)
+        g.set_relevance(r)
+        g.set_exposure(e)
+        g.step(S, trace=False)  # warm-up, graph capture
+        g.reset()
+        g.impacts()
+        _, t_gpu = _timed(lambda: g.step(S, trace=False))
+        o = oracle.Oracle(U, I, K, iters=L, lr=0.1, threads=cores)
+        o.set_relevance(r.astype(np.float64))
+        o.set_exposure(e)
+        o.impacts()
+        t0 = time.perf_counter()
+        o.step(3)
+        t_cpu = (time.perf_counter() - t0) / 3
+        points.append({"n_users": U, "n_items": I, "gpu_ms_per_step": t_gpu / S * 1e3,
+                       "cpu_ms_per_step": t_cpu * 1e3, "speedup": t_cpu / (t_gpu / S)})
+        del g, o
+    return {"compare": "paper-shapes", "n_slots": K, "n_cols": K + 1, "sinkhorn_iters": L,
+            "cpu_cores": cores, "cpu": "FP64 oracle, OpenMP over consumers", "points": points}
+
+
 def profile_item(args):
     """Sets up one per-item workload and runs --profile-steps ascent steps (for ncu captures):
     implicit / unrolled: 20000 x 2000, K = 20, L = 100 (checkpoints every 10); bf16: 200000 x 10^4,
@@ -505,7 +549,8 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         from paper_2406_10262_gb300 import build as frbuild
         frbuild.build()
-        fn = {"batch": compare_batch, "unrolled": compare_unrolled, "bf16": compare_bf16}[args.compare]
+        fn = {"batch": compare_batch, "unrolled": compare_unrolled, "bf16": compare_bf16,
+              "paper-shapes": compare_paper_shapes}[args.compare]
         print(json.dumps(fn(args)), flush=True)
         return
     w = workload(args.workload)

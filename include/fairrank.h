@@ -120,7 +120,9 @@ FR_API fr_status fr_step(fr_ctx* ctx, int32_t n_steps, double* nsw_trace);
 
 /* Algorithm 1 with threshold t on ||grad F||_2 (gradient with respect to the optimised variable):
    runs steps until one whose gradient norm is <= t (that step's update is applied) or max_steps.
-   *steps_done and *nsw_out (nullable) report the steps run and the final F. */
+   *steps_done and *nsw_out (nullable) report the steps run and the final F. The loop runs on the
+   device: one CUDA graph launch whose conditional while node repeats chunks of steps until the
+   stop flag raised by the FP64 reduction, with no host round trip per step or chunk. */
 FR_API fr_status fr_solve(fr_ctx* ctx, double t, int32_t max_steps, int32_t* steps_done,
                    double* nsw_out);
 
@@ -157,6 +159,14 @@ FR_API fr_status fr_get_state(fr_ctx* ctx, float* param, float* m1, float* m2, f
    first use). FR_ETIMEOUT if a bounded device wait of the contraction expired. */
 FR_API fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* better_pct,
                      double* worse_pct);
+
+/* Optimality certificate of the current policy (host doubles, each nullable). F is concave in X
+   and each X_u ranges over the polytope of Eqs. (1)-(3), so F* - F(X) <= max_Y <grad F(X), Y - X>;
+   with e non-increasing the maximising Y_u ranks the items by r(u,i)/Imp_i (rearrangement), giving
+   gap = sum_u [sum_{k<K} e_k (k-th largest r(u,i)/Imp_i) - sum_{i,k<K} (r(u,i)/Imp_i) e_k x_uik].
+   The bound holds for exactly feasible X; the emitted X has exact rows and a column residual
+   max_{u,k} |sum_i x_uik - b_k|, reported beside it. Needs e non-increasing for the bound. */
+FR_API fr_status fr_certificate(fr_ctx* ctx, double* gap, double* col_residual);
 
 /* Message of the last failing call on ctx (or of the last failing fr_create on this thread when
    ctx is NULL). Valid until the next call on ctx. */

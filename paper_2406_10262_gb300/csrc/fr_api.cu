@@ -58,6 +58,8 @@ struct fr_ctx {
     int* flags = nullptr;
     bool have_r = false, have_e = false, fresh = false;
     cudaGraphExec_t chunk_exec = nullptr;
+    cudaGraphExec_t solve_exec = nullptr;  // fr_solve: device-side while loop over step chunks
+    int* solve_ctl = nullptr;              // [2] body iterations, cap
     int64_t launches = 0;
     std::string err;
 };
@@ -218,6 +220,53 @@ fr_status ensure_hist(fr_ctx* ctx, int n) {
         cudaGraphExecDestroy(ctx->chunk_exec);
         ctx->chunk_exec = nullptr;
     }
+    if (ctx->solve_exec) {
+        cudaGraphExecDestroy(ctx->solve_exec);
+        ctx->solve_exec = nullptr;
+    }
+    return FR_OK;
+}
+
+// fr_solve's graph: a conditional while node whose body is kChunk ascent steps followed by
+// solve_cond_kernel, which keeps the loop running until the reduction raises the stop flag (the
+// gradient-norm threshold or the step cap) -- no host round trip per chunk.
+fr_status ensure_solve_graph(fr_ctx* ctx) {
+    if (ctx->solve_exec) return FR_OK;
+    if (!ctx->solve_ctl) CU(cudaMalloc(&ctx->solve_ctl, sizeof(int) * 2));
+    cudaGraph_t g = nullptr;
+    CU(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams p{};
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) {
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = h;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p);
+    }
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        CU(e);
+    }
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    const int64_t before = ctx->launches;
+    CU(cudaStreamBeginCaptureToGraph(ctx->s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    fr_status st = FR_OK;
+    for (int j = 0; j < kChunk && st == FR_OK; ++j) st = launch_one_step(ctx);
+    if (st == FR_OK) st = launch_solve_cond(ctx->st, ctx->solve_ctl, h, ctx->s) == cudaSuccess ? FR_OK : FR_ECUDA;
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(ctx->s, &captured);
+    ctx->launches = before;  // captured, not launched
+    if (st != FR_OK || e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        if (st != FR_OK) return fail(ctx, st, "capturing the solve loop failed");
+        CU(e);
+    }
+    e = cudaGraphInstantiate(&ctx->solve_exec, g, 0);
+    cudaGraphDestroy(g);
+    CU(e);
     return FR_OK;
 }
 
@@ -244,7 +293,7 @@ fr_status ensure_graph(fr_ctx* ctx) {
 }
 
 // Writes selected host-side fields of the device step state.
-fr_status set_run_state(fr_ctx* ctx, double thresh) {
+fr_status set_run_state(fr_ctx* ctx, double thresh, int max_steps = 0) {
     DevState* h = ctx->st_host;
     CU(cudaMemcpyAsync(h, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->s));
     CU(cudaStreamSynchronize(ctx->s));
@@ -252,6 +301,7 @@ fr_status set_run_state(fr_ctx* ctx, double thresh) {
     h->stop = 0;
     h->steps_done = 0;
     h->thresh = thresh;
+    h->max_steps = max_steps;
     CU(cudaMemcpyAsync(ctx->st, h, sizeof(DevState), cudaMemcpyHostToDevice, ctx->s));
     return FR_OK;
 }
@@ -268,7 +318,7 @@ fr_status read_state(fr_ctx* ctx) {
 }
 
 // Runs n steps: whole chunks by graph replay, the remainder by direct launches.
-fr_status run_steps(fr_ctx* ctx, int n, bool check_stop) {
+fr_status run_steps(fr_ctx* ctx, int n) {
     int done = 0;
     if (n >= kChunk) {
         fr_status st = ensure_graph(ctx);
@@ -278,11 +328,6 @@ fr_status run_steps(fr_ctx* ctx, int n, bool check_stop) {
         CU(cudaGraphLaunch(ctx->chunk_exec, ctx->s));
         ctx->launches += (int64_t)kernels_per_step(ctx) * kChunk;
         done += kChunk;
-        if (check_stop) {
-            fr_status st = read_state(ctx);
-            if (st != FR_OK) return st;
-            if (ctx->st_host->stop) return FR_OK;
-        }
     }
     for (; done < n; ++done) {
         fr_status st = launch_one_step(ctx);
@@ -304,6 +349,8 @@ fr_status ensure_tmp(fr_ctx* ctx, size_t bytes) {
 
 void free_all(fr_ctx* c) {
     if (c->chunk_exec) cudaGraphExecDestroy(c->chunk_exec);
+    if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
+    cudaFree(c->solve_ctl);
     float* fs[] = {c->C, c->m1, c->m2, c->theta, c->tm1, c->tm2, c->w, c->gpart, c->gL, c->gP,
                    c->e, c->log2b, c->omega, c->part, c->tmp, c->ck};
     for (float* p : fs) cudaFree(p);
@@ -639,7 +686,7 @@ fr_status fr_step(fr_ctx* ctx, int32_t n_steps, double* nsw_trace) {
     if (st != FR_OK) return st;
     if ((st = ensure_hist(ctx, n_steps)) != FR_OK) return st;
     if ((st = set_run_state(ctx, -1.0)) != FR_OK) return st;
-    if ((st = run_steps(ctx, n_steps, false)) != FR_OK) return st;
+    if ((st = run_steps(ctx, n_steps)) != FR_OK) return st;
     if ((st = read_state(ctx)) != FR_OK) return st;
     if (nsw_trace && n_steps > 0) {
         CU(cudaMemcpyAsync(nsw_trace, ctx->F_hist, sizeof(double) * n_steps, cudaMemcpyDeviceToHost,
@@ -656,8 +703,17 @@ fr_status fr_solve(fr_ctx* ctx, double t, int32_t max_steps, int32_t* steps_done
     fr_status st = ensure_fresh(ctx);
     if (st != FR_OK) return st;
     if ((st = ensure_hist(ctx, max_steps)) != FR_OK) return st;
-    if ((st = set_run_state(ctx, t)) != FR_OK) return st;
-    if ((st = run_steps(ctx, max_steps, true)) != FR_OK) return st;
+    if ((st = set_run_state(ctx, t, max_steps)) != FR_OK) return st;
+    if (max_steps > 0) {
+        if ((st = ensure_solve_graph(ctx)) != FR_OK) return st;
+        const int ctl[2] = {0, (max_steps + kChunk - 1) / kChunk};  // hard cap on body iterations
+        CU(cudaMemcpyAsync(ctx->solve_ctl, ctl, sizeof ctl, cudaMemcpyHostToDevice, ctx->s));
+        CU(cudaGraphLaunch(ctx->solve_exec, ctx->s));
+        int done_ctl[2];
+        CU(cudaMemcpyAsync(done_ctl, ctx->solve_ctl, sizeof done_ctl, cudaMemcpyDeviceToHost, ctx->s));
+        CU(cudaStreamSynchronize(ctx->s));
+        ctx->launches += (int64_t)done_ctl[0] * (kernels_per_step(ctx) * kChunk + 1);
+    }
     if ((st = read_state(ctx)) != FR_OK) return st;
     if (steps_done) *steps_done = ctx->st_host->steps_done;
     if (nsw_out) *nsw_out = ctx->st_host->F;
@@ -865,6 +921,39 @@ fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* be
     if (mean_envy) *mean_envy = h[0];
     if (better_pct) *better_pct = h[1];
     if (worse_pct) *worse_pct = h[2];
+    return FR_OK;
+}
+
+fr_status fr_certificate(fr_ctx* ctx, double* gap, double* col_residual) {
+    if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
+    Join j(ctx);
+    fr_status st = ensure_fresh(ctx);
+    if (st != FR_OK) return st;
+    int sms = 0;
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int G = cert_grid(ctx->U, sms);
+    // scratch: gap partials [G] doubles | residual partials [G] floats | out [2] doubles
+    const size_t oR = 8 * (size_t)G, oO = (oR + 4 * (size_t)G + 15) / 16 * 16;
+    if ((st = ensure_tmp(ctx, oO + 16)) != FR_OK) return st;
+    unsigned char* base = reinterpret_cast<unsigned char*>(ctx->tmp);
+    double* out = reinterpret_cast<double*>(base + oO);
+    if (ctx->p2) {
+        const P2Args a = p2_args(ctx, ctx->part);
+        CU(launch_certificate(nullptr, &a, ctx->imp, ctx->nc, ctx->I, G,
+                              reinterpret_cast<double*>(base), reinterpret_cast<float*>(base + oR), out,
+                              ctx->s));
+    } else {
+        const P1Args a = p1_args(ctx);
+        CU(launch_certificate(&a, nullptr, ctx->imp, ctx->nc, ctx->I, G,
+                              reinterpret_cast<double*>(base), reinterpret_cast<float*>(base + oR), out,
+                              ctx->s));
+    }
+    ctx->launches += 2;
+    double h[2];
+    CU(cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, ctx->s));
+    if ((st = read_state(ctx)) != FR_OK) return st;
+    if (gap) *gap = h[0];
+    if (col_residual) *col_residual = h[1];
     return FR_OK;
 }
 

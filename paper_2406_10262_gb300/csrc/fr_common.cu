@@ -88,6 +88,7 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a, int bid, int nb
             }
             st->hist_idx = h + 1;
             if (st->thresh >= 0.0 && gn <= st->thresh) st->stop = 1;
+            if (st->max_steps > 0 && st->steps_done >= st->max_steps) st->stop = 1;
         }
         st->counter = 0u;
     }
@@ -211,6 +212,13 @@ __global__ void ex2_bench_kernel(float* sink, int iters) {
     if (s == 12345.f) sink[blockIdx.x] = s;
 }
 
+__global__ void solve_cond_kernel(const DevState* st, int* ctl, cudaGraphConditionalHandle h) {
+    const int it = ctl[0] + 1;
+    ctl[0] = it;
+    const bool more = st->stop == 0 && st->err == 0 && it < ctl[1];
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
 int grid_for(long long n) {
     long long b = (n + 255) / 256;
     return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
@@ -274,6 +282,12 @@ cudaError_t launch_relevance_check(const void* r, int r_bf16, int U, int I, int 
 cudaError_t launch_policy(const P1Args& a, int u0, int n_u, float* x_out, cudaStream_t s) {
     if (n_u <= 0) return cudaSuccess;
     policy_kernel<<<n_u, 256, 0, s>>>(a, u0, x_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_cond(const DevState* st, int* ctl, cudaGraphConditionalHandle h,
+                              cudaStream_t s) {
+    solve_cond_kernel<<<1, 1, 0, s>>>(st, ctl, h);
     return cudaGetLastError();
 }
 

@@ -288,10 +288,12 @@ __device__ inline void warp_cholesky_solve(double* A, double* rhs, int n, int la
 // warp in single precision: lane i keeps row i of A in registers; right-looking Cholesky with the
 // pivot column broadcast by shuffles, forward substitution in registers, back substitution from a
 // transposed copy of L in shared memory (Lt, n*n floats). Pivots below `floor` are raised to it.
-// Writes beta[0..n).
+// Each pivot costs one reciprocal square root (rsqrt.approx) and the divisions by L_jj become
+// multiplications by it: the n pivots form a sequential chain, and IEEE square root and division
+// are long software sequences. Writes beta[0..n).
 template <int NM>
 __device__ inline void warp_cholesky_solve_f32(const float* A, const float* rhs, int n, float* Lt,
-                                        float* beta, int lane) {
+                                               float* beta, int lane) {
     float row[NM];
 #pragma unroll
     for (int k = 0; k < NM; ++k) row[k] = (lane < n && k < n) ? A[lane * n + k] : 0.f;
@@ -300,25 +302,28 @@ __device__ inline void warp_cholesky_solve_f32(const float* A, const float* rhs,
     for (int j = 0; j < NM; ++j)
         if (j < n) dmax = fmaxf(dmax, __shfl_sync(FULL, row[j], j));
     const float floor_ = 1e-12f * fmaxf(dmax, 1e-30f);
+    float rinv = 0.f;  // lane j: 1 / L_jj
 #pragma unroll
     for (int j = 0; j < NM; ++j) {
         if (j >= n) break;
-        const float ljj = sqrtf(fmaxf(__shfl_sync(FULL, row[j], j), floor_));
-        const float lij = lane > j ? row[j] / ljj : (lane == j ? ljj : 0.f);
+        const float d = fmaxf(__shfl_sync(FULL, row[j], j), floor_);
+        const float ri = rsqrtf(d);
+        const float lij = lane > j ? row[j] * ri : (lane == j ? d * ri : 0.f);
+        if (lane == j) rinv = ri;
         row[j] = lij;
 #pragma unroll
         for (int k = j + 1; k < NM; ++k) {
             const float lkj = __shfl_sync(FULL, lij, k);
-            if (lane > j) row[k] -= lij * lkj;
+            if (lane > j) row[k] = fmaf(-lij, lkj, row[k]);
         }
     }
     float y = lane < n ? rhs[lane] : 0.f;  // L y = rhs: lane i holds y_i
 #pragma unroll
     for (int j = 0; j < NM; ++j) {
         if (j >= n) break;
-        const float yj = __shfl_sync(FULL, y, j) / __shfl_sync(FULL, row[j], j);
+        const float yj = __shfl_sync(FULL, y * rinv, j);
         if (lane == j) y = yj;
-        if (lane > j) y -= row[j] * yj;
+        if (lane > j) y = fmaf(-row[j], yj, y);
     }
     if (lane < n) {  // Lt[k][i] = L[i][k]
 #pragma unroll
@@ -328,9 +333,9 @@ __device__ inline void warp_cholesky_solve_f32(const float* A, const float* rhs,
     __syncwarp();
     float z = y;  // L^T z = y
     for (int j = n - 1; j >= 0; --j) {
-        const float zj = __shfl_sync(FULL, z, j) / Lt[j * n + j];
+        const float zj = __shfl_sync(FULL, z * rinv, j);
         if (lane == j) z = zj;
-        if (lane < j) z -= Lt[lane * n + j] * zj;  // (L^T)[i][j] = L[j][i]
+        if (lane < j) z = fmaf(-Lt[lane * n + j], zj, z);  // (L^T)[i][j] = L[j][i]
     }
     if (lane < n) beta[lane] = z;
 }

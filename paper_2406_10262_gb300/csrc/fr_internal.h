@@ -30,7 +30,7 @@ struct DevState {
     int err;              // bit 0: non-positive or non-finite impact; bit 1: non-finite gradient
     int steps_done;       // steps applied since the host last cleared it
     unsigned int counter; // last-block-done counter of the reduction (returns to 0)
-    int pad_;
+    int max_steps;        // > 0: the reduction raises stop once steps_done reaches it
     double F, utility, gnorm;
     double thresh;        // < 0: never stop
 };
@@ -199,6 +199,10 @@ cudaError_t launch_relevance_check(const void* r, int r_bf16, int U, int I, int 
                                    cudaStream_t s);
 cudaError_t launch_policy(const P1Args& a, int u0, int n_u, float* x_out, cudaStream_t s);
 cudaError_t launch_ex2_bench(float* sink, int blocks, int threads, int iters, cudaStream_t s);
+// Body end of fr_solve's device-side while loop: ctl[0] counts body iterations, ctl[1] caps them;
+// sets the loop's condition to continue while no stop / error flag is raised and the cap is not hit.
+cudaError_t launch_solve_cond(const DevState* st, int* ctl, cudaGraphConditionalHandle h,
+                              cudaStream_t s);
 
 // evaluation metrics (fr_metrics.cu): v_ui = sum_{k<K} e_k x_uik into V [U][ld]; then the envy
 // contraction E = R^T V with its row-max epilogue, column sums of r and the ratio tests. out[3]:
@@ -216,5 +220,11 @@ cudaError_t launch_envy_tc(const void* r, int r_bf16, const float* V, int U, int
 cudaError_t launch_envy(const void* r, int r_bf16, const float* V, int U, int I, int ld,
                         const double* imp, double esum, float* rmax, float* diag, double* ru,
                         double* out, int* err, bool tensor_cores, cudaStream_t s);
+// Frank-Wolfe certificate (fr_metrics.cu): one of a1 / a2 non-null (the policy's form); G CTAs
+// (cert_grid), per-CTA partials gap_part [G] doubles and res_part [G] floats; out[0] = gap,
+// out[1] = column residual.
+int cert_grid(int U, int sms);
+cudaError_t launch_certificate(const P1Args* a1, const P2Args* a2, const double* imp, int nc, int I,
+                               int G, double* gap_part, float* res_part, double* out, cudaStream_t s);
 
 }  // namespace fr

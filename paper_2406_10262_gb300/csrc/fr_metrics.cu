@@ -227,4 +227,186 @@ cudaError_t launch_envy(const void* r, int r_bf16, const float* V, int U, int I,
     return cudaGetLastError();
 }
 
+
+// ---- Frank-Wolfe certificate -------------------------------------------------------------------
+// F is concave in X and every X_u lies in the transportation polytope of Eqs. (1)-(3), so
+//   F* - F(X) <= max_Y <grad F(X), Y - X>,  dF/dx_uik = r(u,i) e_k / Imp_i  (e_k = 0 for the dummy).
+// With e non-increasing the maximising Y_u puts the K items with the largest rho_ui = r(u,i)/Imp_i
+// into slots 1..K in that order (rearrangement inequality), so per consumer
+//   gap_u = sum_{k<K} e_k rho_u(k) - sum_i rho_ui sum_{k<K} e_k x_uik,
+// and gap = sum_u gap_u >= F* - F(X) for exactly feasible X. The emitted X has exact rows and a
+// small column residual, reported beside it: max_{u,k} |sum_i x_uik - b_k|.
+namespace {
+
+template <int MAXM>
+__global__ void __launch_bounds__(256) cert_kernel(const P1Args a1, const P2Args a2, int p2,
+                                                   const double* __restrict__ imp,
+                                                   double* __restrict__ gap_part,
+                                                   float* __restrict__ res_part) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int U = p2 ? a2.U : a1.U, I = p2 ? a2.I : a1.I, K = p2 ? a2.K : a1.K;
+    const int nc = p2 ? a2.nc : a1.nc, ld = p2 ? a2.ld : a1.ld;
+    const float* e = p2 ? a2.e : a1.e;
+    double* rho = reinterpret_cast<double*>(smem_raw);             // [I]
+    float* csw = reinterpret_cast<float*>(rho + I);                 // [W][MAXM]
+    __shared__ double s_red[32];
+    __shared__ int s_idx[32];
+    __shared__ float s_resm;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
+    double gap_acc = 0.0;
+    float res_max = 0.f;
+    for (int u = blockIdx.x; u < U; u += gridDim.x) {
+        const float* gp = (p2 ? a2.gP : a1.gP) + (size_t)u * nc;
+        float cs[MAXM];
+#pragma unroll
+        for (int k = 0; k < MAXM; ++k) cs[k] = 0.f;
+        double lin = 0.0;
+        for (int i = tid; i < I; i += blockDim.x) {
+            float z[MAXM];
+            float M = -INFINITY;
+            float si = 0.f;
+            if (p2) {
+                const float ri = p2 ? (a2.r_bf16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(a2.r)[(size_t)u * ld + i])
+                                                 : static_cast<const float*>(a2.r)[(size_t)u * ld + i])
+                                    : 0.f;
+                si = ri * a2.w[i] * a2.inv_eps_ln2;
+            }
+#pragma unroll
+            for (int k = 0; k < MAXM; ++k) {
+                if (k < nc) {
+                    z[k] = p2 ? fmaf(si, e[k] - a2.emax, gp[k])
+                              : gp[k] - a1.C[((size_t)u * nc + k) * ld + i] * a1.inv_eps_ln2;
+                    M = fmaxf(M, z[k]);
+                } else {
+                    z[k] = -INFINITY;
+                }
+            }
+            float S = 0.f;
+#pragma unroll
+            for (int k = 0; k < MAXM; ++k) {
+                z[k] = k < nc ? ex2(z[k] - M) : 0.f;
+                S += z[k];
+            }
+            const float inv = 1.f / S;
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < MAXM; ++k) {
+                const float x = z[k] * inv;
+                cs[k] += x;
+                if (k < K) v += (double)e[k] * x;
+            }
+            const float r = p2 ? (a2.r_bf16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(a2.r)[(size_t)u * ld + i])
+                                            : static_cast<const float*>(a2.r)[(size_t)u * ld + i])
+                               : a1.r[(size_t)u * ld + i];
+            const double rh = (double)r / imp[i];
+            rho[i] = rh;
+            lin += rh * v;
+        }
+        // column sums: warp shuffles, then per-warp partials in shared memory (fixed order)
+#pragma unroll
+        for (int k = 0; k < MAXM; ++k) {
+            float c = cs[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+            if (lane == 0) csw[warp * MAXM + k] = c;
+        }
+        // lin: block sum in fixed order
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lin += __shfl_xor_sync(FULL, lin, o);
+        if (lane == 0) s_red[warp] = lin;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < W; ++w) t += s_red[w];
+            gap_acc -= t;
+            float rm = 0.f;
+            for (int k = 0; k < nc; ++k) {
+                float c = 0.f;
+                for (int w = 0; w < W; ++w) c += csw[w * MAXM + k];
+                const float bk = k < K ? 1.f : (float)(I - K);  // Eq. (2) and the dummy mass
+                rm = fmaxf(rm, fabsf(c - bk));
+            }
+            s_resm = rm;
+        }
+        __syncthreads();
+        if (tid == 0) res_max = fmaxf(res_max, s_resm);
+        // top-K of rho by K rounds of a CTA-wide arg-max (taken entries become -inf)
+        for (int k = 0; k < K; ++k) {
+            double best = -INFINITY;
+            int bi = -1;
+            for (int i = tid; i < I; i += blockDim.x)
+                if (rho[i] > best) { best = rho[i]; bi = i; }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ob = __shfl_xor_sync(FULL, best, o);
+                const int oi = __shfl_xor_sync(FULL, bi, o);
+                if (ob > best || (ob == best && oi >= 0 && (bi < 0 || oi < bi))) { best = ob; bi = oi; }
+            }
+            if (lane == 0) { s_red[warp] = best; s_idx[warp] = bi; }
+            __syncthreads();
+            if (tid == 0) {
+                double bb = -INFINITY;
+                int ii = -1;
+                for (int w = 0; w < W; ++w)
+                    if (s_red[w] > bb || (s_red[w] == bb && s_idx[w] >= 0 && (ii < 0 || s_idx[w] < ii))) {
+                        bb = s_red[w];
+                        ii = s_idx[w];
+                    }
+                if (ii >= 0) {
+                    gap_acc += (double)e[k] * bb;
+                    rho[ii] = -INFINITY;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (tid == 0) {
+        gap_part[blockIdx.x] = gap_acc;
+        res_part[blockIdx.x] = res_max;
+    }
+}
+
+__global__ void cert_final_kernel(const double* __restrict__ gap_part,
+                                  const float* __restrict__ res_part, int G, double* out) {
+    if (threadIdx.x != 0) return;
+    double g = 0.0;
+    float r = 0.f;
+    for (int j = 0; j < G; ++j) {
+        g += gap_part[j];
+        r = fmaxf(r, res_part[j]);
+    }
+    out[0] = g;
+    out[1] = (double)r;
+}
+
+}  // namespace
+
+int cert_grid(int U, int sms) { return U < 4 * sms ? U : 4 * sms; }
+
+size_t cert_smem(int I) { return sizeof(double) * (size_t)I + sizeof(float) * 8 * 64; }
+
+cudaError_t launch_certificate(const P1Args* a1, const P2Args* a2, const double* imp, int nc, int I,
+                               int G, double* gap_part, float* res_part, double* out, cudaStream_t s) {
+    const P1Args z1{};
+    const P2Args z2{};
+    const P1Args& p1 = a1 ? *a1 : z1;
+    const P2Args& q2 = a2 ? *a2 : z2;
+    const int p2 = a2 != nullptr;
+    const size_t sm = cert_smem(I);
+    cudaError_t e;
+    if (nc <= 16) {
+        if ((e = raise_smem_limit((const void*)cert_kernel<16>, sm)) != cudaSuccess) return e;
+        cert_kernel<16><<<G, 256, sm, s>>>(p1, q2, p2, imp, gap_part, res_part);
+    } else if (nc <= 32) {
+        if ((e = raise_smem_limit((const void*)cert_kernel<32>, sm)) != cudaSuccess) return e;
+        cert_kernel<32><<<G, 256, sm, s>>>(p1, q2, p2, imp, gap_part, res_part);
+    } else {
+        if ((e = raise_smem_limit((const void*)cert_kernel<64>, sm)) != cudaSuccess) return e;
+        cert_kernel<64><<<G, 256, sm, s>>>(p1, q2, p2, imp, gap_part, res_part);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    cert_final_kernel<<<1, 32, 0, s>>>(gap_part, res_part, G, out);
+    return cudaGetLastError();
+}
+
 }  // namespace fr

@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
             }
             __syncthreads();
             // gradient and Adam over the tile, four consecutive items per step (float4)
-            const float step_size = s.coef[0], bc2s = s.coef[1];
+            const float step_size = s.coef[0], inv_bc2s = 1.f / s.coef[1];
             const int g4 = ld / 4;
             float* __restrict__ Cg = a.C;
             float* __restrict__ m1g = a.m1;
@@ -391,7 +391,10 @@ __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
                         for (int j = 0; j < 4; ++j) {
                             mm[j] = a.beta1 * mm[j] + (1.f - a.beta1) * gr[j];
                             vv[j] = a.beta2 * vv[j] + (1.f - a.beta2) * gr[j] * gr[j];
-                            cv[j] += step_size * mm[j] / (sqrtf(vv[j]) / bc2s + a.adam_eps);
+                            // sqrt(v) / bc2s + eps with MUFU rsqrt / rcp (IEEE sqrt and division
+                            // are long instruction sequences on the per-cell path)
+                            const float sq = vv[j] > 0.f ? vv[j] * rsqrtf(vv[j]) : 0.f;
+                            cv[j] += __fdividef(step_size * mm[j], fmaf(sq, inv_bc2s, a.adam_eps));
                         }
                         *reinterpret_cast<float4*>(m1g + off) = make_float4(mm[0], mm[1], mm[2], mm[3]);
                         *reinterpret_cast<float4*>(m2g + off) = make_float4(vv[0], vv[1], vv[2], vv[3]);

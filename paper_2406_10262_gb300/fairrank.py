@@ -69,6 +69,7 @@ def lib():
             "fr_set_state": (i32, [_vp, _vp, _vp, _vp, _vp, i64, i32]),
             "fr_get_state": (i32, [_vp, _vp, _vp, _vp, _vp, ct.POINTER(i64), i32]),
             "fr_metrics": (i32, [_vp, _dp, _dp, _dp, _dp]),
+            "fr_certificate": (i32, [_vp, _dp, _dp]),
             "fr_last_error": (ct.c_char_p, [_vp]),
             "fr_launch_count": (i64, [_vp]),
             "fr_measure_ex2_rate": (i32, [_dp]),
@@ -261,6 +262,12 @@ class FairRank:
         vals = [ct.c_double() for _ in range(4)]
         self._check(lib().fr_metrics(self.h, *[ct.byref(v) for v in vals]))
         return dict(zip(["utility", "mean_envy", "better_pct", "worse_pct"], [v.value for v in vals]))
+
+    def certificate(self):
+        """(gap, column residual): Frank-Wolfe bound on F* - F at the current policy."""
+        gap, res = ct.c_double(), ct.c_double()
+        self._check(lib().fr_certificate(self.h, ct.byref(gap), ct.byref(res)))
+        return gap.value, res.value
 
     def time_kernels(self, n_steps: int):
         ms = np.zeros(3)

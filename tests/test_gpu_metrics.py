@@ -85,3 +85,35 @@ def test_metrics_plain_workload_after_solve():
     g.step(30)
     o.step(30)
     check(g, o, r, K)
+
+
+@pytest.mark.parametrize("param,U,I,K,steps", [
+    (fr.PARAM_FULL_C, 30, 120, 10, 20),
+    (fr.PARAM_FULL_C, 9, 40, 40, 10),      # square, no dummy column
+    (fr.PARAM_ITEM, 25, 300, 20, 10),
+    (fr.PARAM_ITEM, 6, 1500, 5, 3),
+])
+def test_certificate_matches_oracle(param, U, I, K, steps):
+    """Frank-Wolfe gap and column residual of the emitted policy against the oracle's; the two terms
+    of the gap sum to O(|I|) (sum_u sum_i rho_ui v_ui = |I|), so the tolerance is 1e-5 |I|."""
+    r = synth.relevance_lowrank(U, I, seed=7 * U + I)
+    g, o = problem(U, I, K, r, param, steps)
+    gap, res = g.certificate()
+    ogap, ores = o.certificate()
+    assert abs(gap - ogap) <= 1e-5 * I
+    assert abs(res - ores) <= 1e-5 * I
+    assert gap >= -1e-5 * I
+
+
+def test_certificate_plain_workload_decreases():
+    """2000 x 1000, K = 10: the certificate of the initial policy against the oracle, then after 40
+    more GPU steps the bound has shrunk."""
+    U, I, K = 2000, 1000, 10
+    r = synth.workload_relevance("plain2000x1000").astype(np.float32)
+    g, o = problem(U, I, K, r, fr.PARAM_FULL_C, 0)
+    gap0, res0 = g.certificate()
+    ogap, ores = o.certificate()
+    assert abs(gap0 - ogap) <= 1e-5 * I and abs(res0 - ores) <= 1e-5 * I
+    g.step(40)
+    gap1, _ = g.certificate()
+    assert 0.0 <= gap1 < gap0
