@@ -46,7 +46,7 @@ struct fr_ctx {
     float* ck = nullptr;
     int ce = 0, nck = 0, Gg = 0;
     double *ad_blk = nullptr, *gn2_one = nullptr;
-    float *gL = nullptr, *gP = nullptr, *e = nullptr, *log2b = nullptr, *omega = nullptr,
+    float *gL = nullptr, *gP = nullptr, *e = nullptr, *invb = nullptr, *omega = nullptr,
           *part = nullptr;
     void* r = nullptr;  // [U][ld] float or bfloat16
     float* tmp = nullptr;  // staging for host transfers
@@ -105,7 +105,7 @@ P1Args p1_args(fr_ctx* c) {
     a.U = c->U; a.I = c->I; a.K = c->K; a.nc = c->nc; a.ld = c->ld;
     a.L = c->cfg.sinkhorn_iters; a.G = c->G;
     a.C = c->C; a.m1 = c->m1; a.m2 = c->m2; a.gL = c->gL; a.gP = c->gP;
-    a.r = static_cast<const float*>(c->r); a.e = c->e; a.log2b = c->log2b; a.omega = c->omega;
+    a.r = static_cast<const float*>(c->r); a.e = c->e; a.invb = c->invb; a.omega = c->omega;
     a.part = c->part; a.gn2_part = c->gn2_part; a.st = c->st;
     a.inv_eps_ln2 = (float)(1.0 / (c->cfg.epsilon * std::log(2.0)));
     a.inv_eps = (float)(1.0 / c->cfg.epsilon);
@@ -120,7 +120,7 @@ P2Args p2_args(fr_ctx* c, float* part) {
     P2Args a{};
     a.U = c->U; a.I = c->I; a.K = c->K; a.nc = c->nc; a.ld = c->ld;
     a.L = c->cfg.sinkhorn_iters; a.G = c->G;
-    a.r = c->r; a.r_bf16 = c->r_bf16; a.w = c->w; a.e = c->e; a.log2b = c->log2b;
+    a.r = c->r; a.r_bf16 = c->r_bf16; a.w = c->w; a.e = c->e; a.invb = c->invb;
     a.emax = c->emax; a.gL = c->gL; a.gP = c->gP; a.part = part; a.omega = c->omega;
     a.dr = nullptr; a.st = c->st;
     a.inv_eps_ln2 = (float)(1.0 / (c->cfg.epsilon * std::log(2.0)));
@@ -352,7 +352,7 @@ void free_all(fr_ctx* c) {
     if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
     cudaFree(c->solve_ctl);
     float* fs[] = {c->C, c->m1, c->m2, c->theta, c->tm1, c->tm2, c->w, c->gpart, c->gL, c->gP,
-                   c->e, c->log2b, c->omega, c->part, c->tmp, c->ck};
+                   c->e, c->invb, c->omega, c->part, c->tmp, c->ck};
     for (float* p : fs) cudaFree(p);
     double* ds[] = {c->gn2_part, c->imp, c->blk, c->F_hist, c->gn_hist, c->ad_blk, c->gn2_one};
     for (double* p : ds) cudaFree(p);
@@ -587,7 +587,7 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
     CUC(cudaMalloc(&ctx->gL, sizeof(float) * ctx->U * nc));
     CUC(cudaMalloc(&ctx->gP, sizeof(float) * ctx->U * nc));
     CUC(cudaMalloc(&ctx->e, sizeof(float) * nc));
-    CUC(cudaMalloc(&ctx->log2b, sizeof(float) * nc));
+    CUC(cudaMalloc(&ctx->invb, sizeof(float) * nc));
     CUC(cudaMalloc(&ctx->omega, sizeof(float) * ld));
     CUC(cudaMemset(ctx->omega, 0, sizeof(float) * ld));
     CUC(cudaMalloc(&ctx->part, sizeof(float) * (size_t)ctx->G * ld));
@@ -657,7 +657,7 @@ fr_status fr_set_exposure(fr_ctx* ctx, const double* e, int32_t K) {
     if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
     if (!e) return fail(ctx, FR_EINVAL, "e is NULL");
     if (K != ctx->K) return fail(ctx, FR_EINVAL, "K %d != n_slots %d", K, ctx->K);
-    std::vector<float> ep(ctx->nc, 0.f), lb(ctx->nc, 0.f);
+    std::vector<float> ep(ctx->nc, 0.f), lb(ctx->nc, 1.f);  // lb: 1 / b_k
     float emax = 0.f;
     for (int k = 0; k < K; ++k) {
         if (!(e[k] > 0.0) || !std::isfinite(e[k]))
@@ -665,10 +665,10 @@ fr_status fr_set_exposure(fr_ctx* ctx, const double* e, int32_t K) {
         ep[k] = (float)e[k];
         emax = std::max(emax, ep[k]);
     }
-    if (ctx->nc > K) lb[K] = (float)std::log2((double)(ctx->I - K));  // dummy mass |I| - K
+    if (ctx->nc > K) lb[K] = (float)(1.0 / (double)(ctx->I - K));  // dummy mass |I| - K
     Join j(ctx);
     CU(cudaMemcpyAsync(ctx->e, ep.data(), sizeof(float) * ctx->nc, cudaMemcpyHostToDevice, ctx->s));
-    CU(cudaMemcpyAsync(ctx->log2b, lb.data(), sizeof(float) * ctx->nc, cudaMemcpyHostToDevice, ctx->s));
+    CU(cudaMemcpyAsync(ctx->invb, lb.data(), sizeof(float) * ctx->nc, cudaMemcpyHostToDevice, ctx->s));
     CU(cudaStreamSynchronize(ctx->s));
     ctx->emax = emax;
     ctx->esum = 0.0;

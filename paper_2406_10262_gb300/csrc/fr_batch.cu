@@ -39,7 +39,7 @@ struct BMarket {
     bool have_r = false, have_e = false;
     void* r = nullptr;
     float *theta = nullptr, *tm1 = nullptr, *tm2 = nullptr, *w = nullptr, *gL = nullptr,
-          *gP = nullptr, *e = nullptr, *log2b = nullptr, *omega = nullptr, *part = nullptr,
+          *gP = nullptr, *e = nullptr, *invb = nullptr, *omega = nullptr, *part = nullptr,
           *gpart = nullptr;
     double *imp = nullptr, *blk = nullptr, *ad_blk = nullptr, *gn2 = nullptr, *F_hist = nullptr,
            *gn_hist = nullptr;
@@ -141,7 +141,7 @@ P2Args market_args(const fr_batch* b, const BMarket& m, float* part) {
     P2Args a{};
     a.U = m.U; a.I = m.I; a.K = m.K; a.nc = m.nc; a.ld = m.ld; a.L = b->cfg.sinkhorn_iters;
     a.G = m.rows;
-    a.r = m.r; a.r_bf16 = b->esz == 2; a.w = m.w; a.e = m.e; a.log2b = m.log2b; a.emax = m.emax;
+    a.r = m.r; a.r_bf16 = b->esz == 2; a.w = m.w; a.e = m.e; a.invb = m.invb; a.emax = m.emax;
     a.gL = m.gL; a.gP = m.gP; a.part = part; a.omega = m.omega; a.dr = nullptr; a.st = m.st;
     a.inv_eps_ln2 = (float)(1.0 / (b->cfg.epsilon * std::log(2.0)));
     a.inv_eps = (float)(1.0 / b->cfg.epsilon);
@@ -643,7 +643,7 @@ fr_status fr_batch_create(const fr_config* cfgs, int32_t n_markets, void* stream
         m.r = base + o.r;
         m.theta = (float*)(base + o.th); m.tm1 = (float*)(base + o.m1); m.tm2 = (float*)(base + o.m2);
         m.w = (float*)(base + o.w); m.gL = (float*)(base + o.gL); m.gP = (float*)(base + o.gP);
-        m.e = (float*)(base + o.e); m.log2b = (float*)(base + o.lb); m.omega = (float*)(base + o.om);
+        m.e = (float*)(base + o.e); m.invb = (float*)(base + o.lb); m.omega = (float*)(base + o.om);
         m.part = (float*)(base + o.part); m.gpart = (float*)(base + o.gpart);
         m.imp = (double*)(base + o.imp); m.blk = (double*)(base + o.blk);
         m.ad_blk = (double*)(base + o.ad); m.gn2 = (double*)(base + o.gn2);
@@ -733,7 +733,7 @@ fr_status fr_batch_set_exposure(fr_batch* b, int32_t market, const double* e, in
     BMarket& m = b->mk[market];
     if (!e) return bfail(b, FR_EINVAL, "e is NULL");
     if (K != m.K) return bfail(b, FR_EINVAL, "market %d: K %d != n_slots %d", market, K, m.K);
-    std::vector<float> ep(m.nc, 0.f), lb(m.nc, 0.f);
+    std::vector<float> ep(m.nc, 0.f), lb(m.nc, 1.f);  // lb: 1 / b_k
     float emax = 0.f;
     for (int k = 0; k < K; ++k) {
         if (!(e[k] > 0.0) || !std::isfinite(e[k]))
@@ -741,10 +741,10 @@ fr_status fr_batch_set_exposure(fr_batch* b, int32_t market, const double* e, in
         ep[k] = (float)e[k];
         emax = std::max(emax, ep[k]);
     }
-    if (m.nc > K) lb[K] = (float)std::log2((double)(m.I - K));  // dummy mass |I| - K
+    if (m.nc > K) lb[K] = (float)(1.0 / (double)(m.I - K));  // dummy mass |I| - K
     BJoin j(b);
     BCU(cudaMemcpyAsync(m.e, ep.data(), sizeof(float) * m.nc, cudaMemcpyHostToDevice, b->s));
-    BCU(cudaMemcpyAsync(m.log2b, lb.data(), sizeof(float) * m.nc, cudaMemcpyHostToDevice, b->s));
+    BCU(cudaMemcpyAsync(m.invb, lb.data(), sizeof(float) * m.nc, cudaMemcpyHostToDevice, b->s));
     BCU(cudaStreamSynchronize(b->s));
     if (m.emax != emax) {  // the sweep arguments carry e_max
         m.emax = emax;

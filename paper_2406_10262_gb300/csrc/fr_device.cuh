@@ -351,7 +351,7 @@ __device__ __forceinline__ void bcast_g(const float (&gm)[GPL], float (&gk)[NCB]
 // the per-warp partials of its lanes' columns and updates its copy of g'.
 template <int NCB, int GPL>
 __device__ __forceinline__ void column_update(float (&cs)[NCB], float (&gm)[GPL], int nc,
-                                              float* s_red, const float* s_l2b, int par, int lane,
+                                              float* s_red, const float* s_ib, int par, int lane,
                                               int warp, int W) {
     constexpr int P = pow2ceil(NCB);
     constexpr int PER = P >= 32 ? P / 32 : 1;
@@ -373,7 +373,10 @@ __device__ __forceinline__ void column_update(float (&cs)[NCB], float (&gm)[GPL]
         if (col < nc) {
             float sum = 0.f;
             for (int ww = 0; ww < W; ++ww) sum += buf[ww * P + col];
-            gm[j] += s_l2b[col] - log2f(fmaxf(sum, 1e-37f));
+            // log2 b - log2 cs = -log2(cs / b): the argument is near 1, so the log2 and the one
+            // rounding of cs / b are accurate to ~1e-7 absolute (two logs of ~log2 |I| each would
+            // carry ~5e-7 of rounding into every iteration's potentials)
+            gm[j] -= log2f(fmaxf(sum * s_ib[col], 1e-37f));
         }
     }
 }

@@ -86,31 +86,46 @@ __device__ __forceinline__ void mma_commit(unsigned long long* bar) {
         : "memory");
 }
 
-// Stage 32 consumers of the tile: A[m][k] = r(u0 + k, i0 + m), B[n][k] = v(u0 + k, j0 + n), each
-// split into TF32 hi and lo parts. Thread t owns row t % 128 of both operands and the groups of 4
-// consumers g = t / 128 + KGROUPS q; one 16-byte store per group and part.
-__device__ __forceinline__ void stage_tile(unsigned char* st, const void* r, int r_bf16,
-                                           const float* V, int U, int ld, int i0, int j0, int u0) {
+// One stage = 32 consumers of the tile: A[m][k] = r(u0 + k, i0 + m), B[n][k] = v(u0 + k, j0 + n).
+// Thread t owns row t % 128 of both operands and the groups of 4 consumers g0 + KGROUPS q,
+// g0 = t / 128. load_stage reads them into registers (issued one stage ahead, so the global-memory
+// latency overlaps the tensor cores' work); store_stage splits each value into TF32 hi and lo parts
+// and writes one 16-byte vector per group and part.
+constexpr int QG = TK / 4 / KGROUPS;  // groups per thread per stage
+
+struct StageRegs {
+    float r[QG][4], v[QG][4];
+};
+
+__device__ __forceinline__ void load_stage(StageRegs& R, const void* r, int r_bf16, const float* V,
+                                           int U, int ld, int i0, int j0, int u0) {
     const int t = threadIdx.x % TM, g0 = threadIdx.x / TM;
     const int i = i0 + t, j = j0 + t;
 #pragma unroll
-    for (int q2 = 0; q2 < TK / 4 / KGROUPS; ++q2) {
+    for (int q2 = 0; q2 < QG; ++q2) {
         const int k4 = 4 * (g0 + KGROUPS * q2);
-        float ra[4], va[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int u = u0 + k4 + q;
-            ra[q] = (u < U && i < ld) ? rval_tc(r, r_bf16, (size_t)u * ld + i) : 0.f;
-            va[q] = (u < U && j < ld) ? V[(size_t)u * ld + j] : 0.f;
+            R.r[q2][q] = (u < U && i < ld) ? rval_tc(r, r_bf16, (size_t)u * ld + i) : 0.f;
+            R.v[q2][q] = (u < U && j < ld) ? V[(size_t)u * ld + j] : 0.f;
         }
+    }
+}
+
+__device__ __forceinline__ void store_stage(unsigned char* st, const StageRegs& R) {
+    const int t = threadIdx.x % TM, g0 = threadIdx.x / TM;
+#pragma unroll
+    for (int q2 = 0; q2 < QG; ++q2) {
+        const int k4 = 4 * (g0 + KGROUPS * q2);
         uint4 rh, rl, vh, vl;
         unsigned* prh = &rh.x; unsigned* prl = &rl.x; unsigned* pvh = &vh.x; unsigned* pvl = &vl.x;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            prh[q] = to_tf32(ra[q]);
-            prl[q] = to_tf32(ra[q] - __uint_as_float(prh[q]));
-            pvh[q] = to_tf32(va[q]);
-            pvl[q] = to_tf32(va[q] - __uint_as_float(pvh[q]));
+            prh[q] = to_tf32(R.r[q2][q]);
+            prl[q] = to_tf32(R.r[q2][q] - __uint_as_float(prh[q]));
+            pvh[q] = to_tf32(R.v[q2][q]);
+            pvl[q] = to_tf32(R.v[q2][q] - __uint_as_float(pvh[q]));
         }
         const int o = oper_off(t, k4);
         *reinterpret_cast<uint4*>(st + 0 * OPER_BYTES + o) = rh;
@@ -151,6 +166,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const void* __rest
     const int nk = (U + TK - 1) / TK;
     bool ok = true;
     int issued = -1;  // last stage whose MMAs were committed
+    StageRegs regs;
+    load_stage(regs, r, r_bf16, V, U, ld, i0, j0, 0);
     for (int kc = 0; kc < nk; ++kc) {
         const int st = kc & 1;
         unsigned char* sbuf = stages + st * STAGE_BYTES;
@@ -161,7 +178,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const void* __rest
             ok = false;
             break;
         }
-        stage_tile(sbuf, r, r_bf16, V, U, ld, i0, j0, kc * TK);
+        store_stage(sbuf, regs);
+        if (kc + 1 < nk) load_stage(regs, r, r_bf16, V, U, ld, i0, j0, (kc + 1) * TK);
         fence_proxy_async_smem();  // generic-proxy stores -> the tensor cores' (async proxy) reads
         __syncthreads();
         if (tid == 0) {

@@ -46,7 +46,7 @@ struct P1Args {
     float* gP;
     const float* r;
     const float* e;       // [nc] exposure, dummy = 0
-    const float* log2b;   // [nc] log2 of the column marginals
+    const float* invb;    // [nc] 1 / b_k of the column marginals
     const float* omega;   // [ld]
     float* part;          // [G][ld]
     double* gn2_part;     // [G]
@@ -83,7 +83,7 @@ struct P2Args {
     int r_bf16;
     const float* w;       // [ld] exp(theta)
     const float* e;       // [nc] exposure, dummy = 0
-    const float* log2b;   // [nc]
+    const float* invb;    // [nc] 1 / b_k
     float emax;           // max_k e_k
     float* gL;            // [U][nc] log2-unit potentials (re-referenced to the last column)
     float* gP;

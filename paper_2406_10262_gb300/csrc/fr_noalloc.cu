@@ -35,16 +35,16 @@ void* g_scratch_ptr[kMaxDevices] = {};
 
 struct ExposurePack {
     float e[64];
-    float log2b[64];
+    float invb[64];
 };
 
 // Writes the padded exposure / log2 marginals and clears the step-state record (its reduction
 // ticket must start at zero on every call, since the array keeps the previous call's contents).
-__global__ void noalloc_prepare(ExposurePack p, int nc, float* e, float* l2b, DevState* st) {
+__global__ void noalloc_prepare(ExposurePack p, int nc, float* e, float* ib, DevState* st) {
     const int k = threadIdx.x;
     if (k < nc) {
         e[k] = p.e[k];
-        l2b[k] = p.log2b[k];
+        ib[k] = p.invb[k];
     }
     if (k == 0) {
         DevState z{};
@@ -91,7 +91,8 @@ extern "C" fr_status fr_nsw_eval_noalloc(const float* C, const float* r, int64_t
             return bad(FR_EINVAL, "fr_nsw_eval_noalloc: exposure must be positive and finite");
         pack.e[k] = (float)e[k];
     }
-    if (nc > n_slots) pack.log2b[n_slots] = (float)std::log2((double)(n_items - n_slots));
+    for (int k = 0; k < nc; ++k) pack.invb[k] = 1.f;  // 1 / b_k
+    if (nc > n_slots) pack.invb[n_slots] = (float)(1.0 / (double)(n_items - n_slots));
     P1Variant var;
     if (!p1_select(nc, n_items, &var)) {
         set_thread_error("fr_nsw_eval_noalloc: n_cols / n_items outside the compiled kernel variants");
@@ -117,7 +118,7 @@ extern "C" fr_status fr_nsw_eval_noalloc(const float* C, const float* r, int64_t
             cudaSuccess || occ < 1)
         return FR_EUNSUPPORTED;
 
-    // scratch layout: state | e | log2b | omega | blk | gn2_part | gL | gP | part
+    // scratch layout: state | e | invb | omega | blk | gn2_part | gL | gP | part
     const int nblk = reduce_blocks(n_items);
     const size_t fixed = align256(sizeof(DevState)) + 2 * align256(sizeof(float) * 64) +
                          align256(sizeof(float) * ld) + align256(sizeof(double) * 2 * nblk) +
@@ -141,7 +142,7 @@ extern "C" fr_status fr_nsw_eval_noalloc(const float* C, const float* r, int64_t
     };
     DevState* st = reinterpret_cast<DevState*>(take(sizeof(DevState)));
     float* ed = reinterpret_cast<float*>(take(sizeof(float) * 64));
-    float* l2b = reinterpret_cast<float*>(take(sizeof(float) * 64));
+    float* ib = reinterpret_cast<float*>(take(sizeof(float) * 64));
     float* omega = reinterpret_cast<float*>(take(sizeof(float) * ld));
     double* blk = reinterpret_cast<double*>(take(sizeof(double) * 2 * nblk));
     double* gn2 = reinterpret_cast<double*>(take(sizeof(double) * G));
@@ -151,14 +152,14 @@ extern "C" fr_status fr_nsw_eval_noalloc(const float* C, const float* r, int64_t
     if (off > kScratchBytes) return FR_EUNSUPPORTED;
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    noalloc_prepare<<<1, 64, 0, s>>>(pack, nc, ed, l2b, st);
+    noalloc_prepare<<<1, 64, 0, s>>>(pack, nc, ed, ib, st);
     if (cudaGetLastError() != cudaSuccess) return FR_ECUDA;
 
     P1Args a{};
     a.U = n_users; a.I = n_items; a.K = n_slots; a.nc = nc; a.ld = (int)ld;
     a.L = sinkhorn_iters; a.G = G;
     a.C = const_cast<float*>(C);
-    a.gL = gL; a.gP = gP; a.r = r; a.e = ed; a.log2b = l2b; a.omega = omega;
+    a.gL = gL; a.gP = gP; a.r = r; a.e = ed; a.invb = ib; a.omega = omega;
     a.part = part; a.gn2_part = gn2; a.st = st;
     a.inv_eps_ln2 = (float)(1.0 / (epsilon * std::log(2.0)));
     a.inv_eps = (float)(1.0 / epsilon);

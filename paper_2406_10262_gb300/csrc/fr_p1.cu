@@ -46,7 +46,7 @@ namespace {
 
 struct Smem {
     float* gp;    // [ncx] g^(L-1)' of the previous solve (update modes)
-    float* l2b;   // [ncx] log2 b
+    float* ib;    // [ncx] 1 / b_k
     float* e;     // [ncx] exposure
     float* beta;  // [ncx]
     float* coef;  // [2] Adam step size and sqrt of the second bias correction
@@ -91,7 +91,7 @@ __host__ __device__ inline size_t smem_layout(int ncb, int nc, int ld, int W, in
     const bool upd = mode != MODE_SWEEP;
     size_t red_f = (size_t)W * 3 * P;
     if ((size_t)W * PG > red_f) red_f = (size_t)W * PG;
-    const size_t o_gp = take(sizeof(float) * ncx), o_l2b = take(sizeof(float) * ncx);
+    const size_t o_gp = take(sizeof(float) * ncx), o_ib = take(sizeof(float) * ncx);
     const size_t o_e = take(sizeof(float) * ncx), o_beta = take(sizeof(float) * ncx);
     const size_t o_coef = take(sizeof(float) * 2), o_bar = take(sizeof(unsigned long long));
     const size_t o_red = take(sizeof(float) * red_f);
@@ -112,7 +112,7 @@ __host__ __device__ inline size_t smem_layout(int ncb, int nc, int ld, int W, in
     }
     if (s) {
         s->gp = (float*)(base + o_gp);
-        s->l2b = (float*)(base + o_l2b);
+        s->ib = (float*)(base + o_ib);
         s->e = (float*)(base + o_e);
         s->beta = (float*)(base + o_beta);
         s->coef = (float*)(base + o_coef);
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
         s.coef[1] = bc2s;
     }
     for (int k = tid; k < ncx; k += T) {
-        s.l2b[k] = k < nc ? a.log2b[k] : 0.f;
+        s.ib[k] = k < nc ? a.invb[k] : 0.f;
         s.e[k] = k < nc ? a.e[k] : 0.f;
     }
     if (MODE != MODE_SWEEP)
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
             if (tid == 0) atomicOr(&a.st->err, 4);
         }
         phase ^= 1u;
-        __syncthreads();  // s.gp / s.e / s.l2b / s.om / s.coef visible
+        __syncthreads();  // s.gp / s.e / s.ib / s.om / s.coef visible
 
         if constexpr (MODE != MODE_SWEEP) {
             // ---------------- gradient of F at the previous policy ------------------------------
@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
                         x[k] = ex2(x[k] - M);
                         S += x[k];
                     }
-                    const float inv = 1.f / S;
+                    const float inv = rcp_approx(S);  // S in [1, m]: the row max contributes 1
                     const float wr = s.om[i] * s.r[i];  // dF/dx_ik = wr_i e_k
                     float hh = 0.f, vi = 0.f;
 #pragma unroll
@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
                             if (EXACT || k < nc) s.X[k * ld + i] = x[k];
                         }
                     }
-                    s.lse[i] = M + log2f(S);
+                    s.lse[i] = M + lg2_approx(S);
                     s.h[i] = hh;
                     if (MODE == MODE_GRAD) s.vimp[i] = vi;
                 }
@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
                     upk(cs2[k], lo, hi);
                     cs[k] = lo + hi;
                 }
-                column_update<NCB, GPL>(cs, gm, nc, s.red, s.l2b, par, lane, warp, W);
+                column_update<NCB, GPL>(cs, gm, nc, s.red, s.ib, par, lane, warp, W);
                 par ^= 1;
                 if (l == 0 && tid == 0)
                     stage_consumer(a, u + gridDim.x, nc, ld, s, MODE == MODE_UPDATE_SWEEP && a.optimizer == 0);
@@ -595,7 +595,7 @@ __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
                         acc_imp[r] += rr[r] * (v * inv);
                     }
                 }
-                column_update<NCB, GPL>(cs, gm, nc, s.red, s.l2b, par, lane, warp, W);
+                column_update<NCB, GPL>(cs, gm, nc, s.red, s.ib, par, lane, warp, W);
                 par ^= 1;
                 if (l == 0 && tid == 0)
                     stage_consumer(a, u + gridDim.x, nc, ld, s, MODE == MODE_UPDATE_SWEEP && a.optimizer == 0);

@@ -53,7 +53,7 @@ struct SweepSmem {
     unsigned char* rbuf;  // [2][ld] staged relevance rows (float or bf16)
     float* e;     // [ncx]
     float* eh;    // [ncx] e_k - e_max (0 beyond nc)
-    float* l2b;   // [ncx]
+    float* ib;    // [ncx] 1 / b_k
     float* red;   // [2 * W * P]
     unsigned long long* bar;  // [2]
 };
@@ -71,7 +71,7 @@ __host__ __device__ inline size_t sweep_layout(int ncb, int nc, int ld, int W, i
     const size_t o_w = take(sizeof(float) * ld), o_acc = take(sizeof(float) * ld);
     const size_t o_rb = take((size_t)2 * esz * ld);
     const size_t o_e = take(sizeof(float) * nx), o_eh = take(sizeof(float) * nx);
-    const size_t o_l2b = take(sizeof(float) * nx);
+    const size_t o_ib = take(sizeof(float) * nx);
     const size_t o_red = take(sizeof(float) * 2 * W * P);
     if (s) {
         s->bar = (unsigned long long*)(base + o_bar);
@@ -80,7 +80,7 @@ __host__ __device__ inline size_t sweep_layout(int ncb, int nc, int ld, int W, i
         s->rbuf = base + o_rb;
         s->e = (float*)(base + o_e);
         s->eh = (float*)(base + o_eh);
-        s->l2b = (float*)(base + o_l2b);
+        s->ib = (float*)(base + o_ib);
         s->red = (float*)(base + o_red);
     }
     return off;
@@ -238,7 +238,7 @@ __device__ __forceinline__ void sweep_iter(const P2Args& a, const SweepSmem& s, 
 #pragma unroll
     for (int j = 0; j < NP; ++j) upk(cs2[j], cs[2 * j], cs[2 * j + 1]);
     if (TAIL) cs[NCB - 1] = cst;
-    column_update<NCB, GPL>(cs, gm, nc, s.red, s.l2b, par, lane, warp, W);
+    column_update<NCB, GPL>(cs, gm, nc, s.red, s.ib, par, lane, warp, W);
     par ^= 1;
     // re-reference the potentials to the last column (x is invariant to a common shift)
     const float gref = __shfl_sync(FULL, gm[ref / 32], ref % 32);
@@ -274,7 +274,7 @@ __device__ __forceinline__ void sweep_consumers(const P2Args& a, int u_first, in
     for (int k = tid; k < nx; k += T) {
         s.e[k] = k < nc ? a.e[k] : 0.f;
         s.eh[k] = k < nc ? a.e[k] - a.emax : 0.f;
-        s.l2b[k] = k < nc ? a.log2b[k] : 0.f;
+        s.ib[k] = k < nc ? a.invb[k] : 0.f;
     }
     __syncthreads();
     // packed (e_k - e_max) pairs, constant for the market
@@ -512,7 +512,7 @@ __device__ __forceinline__ void grad_consumers(const P2Args& a, int u_first, int
                     x[k] = ex2(x[k] - M);
                     S += x[k];
                 }
-                const float inv = 1.f / S;
+                const float inv = rcp_approx(S);  // S in [1, m]: the row max contributes 1
                 const float wr = __ldg(a.omega + i) * ri;  // dL/dx_ik = wr_i e_k (k < K)
                 float hh = 0.f;
 #pragma unroll
@@ -526,7 +526,7 @@ __device__ __forceinline__ void grad_consumers(const P2Args& a, int u_first, int
                     acc[1][k] += x[k];
                     acc[2][k] += x[k] * hh;
                 }
-                s.lse[i] = M + log2f(S);
+                s.lse[i] = M + lg2_approx(S);
                 s.h[i] = hh;
             }
             cta_reduce<NCB, 3>(acc, nc, s.red, s.out, np_);  // [q | cs | X^T h]

@@ -37,7 +37,7 @@ struct AdjSmem {
     unsigned char* rbuf;  // [2][ld] staged relevance rows
     float* e;     // [ncx]
     float* eh;    // [ncx] e_k - e_max (0 beyond nc)
-    float* l2b;   // [ncx]
+    float* ib;    // [ncx] 1 / b_k
     float* gs;    // [ce][ncp] g^(l-1) of the segment
     float* cs;    // [ce][ncp] cs^(l) of the segment
     float* red;   // [2 * W * P]
@@ -57,7 +57,7 @@ __host__ __device__ inline size_t adj_layout(int ncb, int nc, int ld, int W, int
     const size_t o_acc = take(sizeof(float) * ld), o_drt = take(sizeof(float) * ld);
     const size_t o_rb = take((size_t)2 * esz * ld);
     const size_t o_e = take(sizeof(float) * nx), o_eh = take(sizeof(float) * nx);
-    const size_t o_l2b = take(sizeof(float) * nx);
+    const size_t o_ib = take(sizeof(float) * nx);
     const size_t o_gs = take(sizeof(float) * (size_t)ce * np);
     const size_t o_cs = take(sizeof(float) * (size_t)ce * np);
     const size_t o_red = take(sizeof(float) * 2 * W * P);
@@ -68,7 +68,7 @@ __host__ __device__ inline size_t adj_layout(int ncb, int nc, int ld, int W, int
         s->rbuf = base + o_rb;
         s->e = (float*)(base + o_e);
         s->eh = (float*)(base + o_eh);
-        s->l2b = (float*)(base + o_l2b);
+        s->ib = (float*)(base + o_ib);
         s->gs = (float*)(base + o_gs);
         s->cs = (float*)(base + o_cs);
         s->red = (float*)(base + o_red);
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(256) p2_adj_kernel(const P2Args a) {
     for (int k = tid; k < nx; k += T) {
         s.e[k] = k < nc ? a.e[k] : 0.f;
         s.eh[k] = k < nc ? a.e[k] - a.emax : 0.f;
-        s.l2b[k] = k < nc ? a.log2b[k] : 0.f;
+        s.ib[k] = k < nc ? a.invb[k] : 0.f;
     }
     __syncthreads();
     f2 e2[NPA];
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) p2_adj_kernel(const P2Args a) {
                 for (int j = 0; j < GPL; ++j) {
                     const int col = j * 32 + lane;
                     if (col < nc) {
-                        gm[j] += s.l2b[col] - log2f(fmaxf(csum[j], 1e-37f));
+                        gm[j] -= log2f(fmaxf(csum[j] * s.ib[col], 1e-37f));  // as the sweep
                         if (warp == 0) s.cs[q * np_ + col] = csum[j];
                     }
                 }

@@ -12,6 +12,13 @@ from paper_2406_10262_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
+# Batch against single-market contexts: two FP32 paths that differ only in the order of the
+# cross-CTA partial sums, each within NSW_RTOL of the FP64 oracle, so within 2 NSW_RTOL of each
+# other. theta after Adam steps: Adam divides each coordinate's step by its own gradient scale, so
+# the summation-order noise of coordinates with small gradients reaches theta almost undamped.
+PAIR_RTOL = 2 * NSW_RTOL
+THETA_ATOL = 3e-5
+
 
 @pytest.fixture(scope="module", autouse=True)
 def _gpu():
@@ -52,9 +59,9 @@ def test_batch_matches_single_contexts_and_oracle():
     for j, ((U, I, K), r) in enumerate(zip(SIZES, rs)):
         g = single(U, I, K, r, sinkhorn_iters=L)
         Fs = g.step(steps)
-        np.testing.assert_allclose(F[:, j], Fs, rtol=NSW_RTOL)
+        np.testing.assert_allclose(F[:, j], Fs, rtol=PAIR_RTOL)
         np.testing.assert_allclose(b.policy(j), g.policy(), atol=X_ATOL)
-        np.testing.assert_allclose(b.theta(j), g.get_state()[0], atol=1e-5, rtol=1e-5)
+        np.testing.assert_allclose(b.theta(j), g.get_state()[0], atol=THETA_ATOL, rtol=1e-5)
         if U * I <= 20000:
             o = oracle.Oracle(U, I, K, param=oracle.PARAM_ITEM, iters=L)
             o.set_relevance(r.astype(np.float64))
@@ -84,7 +91,7 @@ def test_autotune_choices_and_state_preserved():
     F2 = b.step(2)
     c = make_batch(sizes, rs, sinkhorn_iters=15)
     Fc = c.step(5)
-    np.testing.assert_allclose(np.vstack([F1, F2]), Fc, rtol=NSW_RTOL)
+    np.testing.assert_allclose(np.vstack([F1, F2]), Fc, rtol=PAIR_RTOL)
 
 
 def test_batch_bf16_matches_single_bf16():
@@ -94,20 +101,22 @@ def test_batch_bf16_matches_single_bf16():
     F = b.step(4)
     for j, ((U, I, K), r) in enumerate(zip(sizes, bits)):
         g = single(U, I, K, r, rel_dtype=fr.BF16, sinkhorn_iters=20)
-        np.testing.assert_allclose(F[:, j], g.step(4), rtol=NSW_RTOL)
+        np.testing.assert_allclose(F[:, j], g.step(4), rtol=PAIR_RTOL)
 
 
 def test_batching_workload_size_sample():
     """24 markets drawn from the batching workload's size distribution, 2 steps, every market
-    against its single-market context; the two smallest also against the oracle."""
+    against its single-market context; the two smallest and the median one also against the
+    oracle."""
     ms = synth.markets(24, seed=3)
     sizes = [(m.n_users, m.n_items, m.n_slots) for m in ms]
     rs = [synth.relevance_lowrank_fast(m.n_users, m.n_items, seed=m.seed) for m in ms]
     b = make_batch(sizes, rs, sinkhorn_iters=50)
     F = b.step(2)
     for j, ((U, I, K), r) in enumerate(zip(sizes, rs)):
-        np.testing.assert_allclose(F[:, j], single(U, I, K, r).step(2), rtol=NSW_RTOL)
-    for j in np.argsort([U * I for U, I, K in sizes])[:2]:
+        np.testing.assert_allclose(F[:, j], single(U, I, K, r).step(2), rtol=PAIR_RTOL)
+    order = np.argsort([U * I for U, I, K in sizes])
+    for j in list(order[:2]) + [order[len(order) // 2]]:  # the two smallest and the median market
         U, I, K = sizes[j]
         o = oracle.Oracle(U, I, K, param=oracle.PARAM_ITEM, iters=50)
         o.set_relevance(rs[j].astype(np.float64))
