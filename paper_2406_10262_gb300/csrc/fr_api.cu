@@ -894,7 +894,7 @@ fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* be
     if (st != FR_OK) return st;
     // scratch in tmp: V [U][ld] floats | rmax [tiles][ld] floats | diag [ld] floats | ru [ld]
     // doubles | out [3] doubles (16-byte aligned pieces)
-    const size_t ld = ctx->ld, nt = std::max(envy_tiles(ctx->I), envy_tc_tiles(ctx->I));
+    const size_t ld = ctx->ld, nt = envy_tc_tiles(ctx->I);
     auto al = [](size_t b) { return (b + 15) / 16 * 16; };
     const size_t oV = 0, oM = oV + al(4 * (size_t)ctx->U * ld), oD = oM + al(4 * nt * ld),
                  oR = oD + al(4 * ld), oO = oR + al(8 * ld), need = oO + al(8 * 3);
@@ -909,7 +909,7 @@ fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* be
     CU(cudaMemsetAsync(ctx->flags, 0, sizeof(int) * 4, ctx->s));
     CU(launch_envy(ctx->r, ctx->r_bf16, V, ctx->U, ctx->I, ctx->ld, ctx->imp, ctx->esum,
                    reinterpret_cast<float*>(base + oM), reinterpret_cast<float*>(base + oD),
-                   reinterpret_cast<double*>(base + oR), out, ctx->flags, true, ctx->s));
+                   reinterpret_cast<double*>(base + oR), out, ctx->flags, ctx->s));
     ctx->launches += 4;
     double h[3];
     int hf[4];

@@ -206,11 +206,10 @@ cudaError_t launch_solve_cond(const DevState* st, int* ctl, cudaGraphConditional
 
 // evaluation metrics (fr_metrics.cu): v_ui = sum_{k<K} e_k x_uik into V [U][ld]; then the envy
 // contraction E = R^T V with its row-max epilogue, column sums of r and the ratio tests. out[3]:
-// mean max envy, % better off, % worse off. Scratch: rmax [envy_tiles(I)][ld] floats, diag [ld]
+// mean max envy, % better off, % worse off. Scratch: rmax [envy_tc_tiles(I)][ld] floats, diag [ld]
 // floats, ru [ld] doubles.
-// tensor_cores: the tcgen05 contraction (fr_envy_tc.cu, 128-item tiles, three TF32 products,
-// bounded waits report bit 4 in *err) instead of the FP32 SIMT one (64-item tiles).
-int envy_tiles(int I);
+// The contraction runs on the tensor cores (fr_envy_tc.cu: 128-item tiles, three TF32 products;
+// an expired bounded wait sets bit 4 of *err); rmax holds envy_tc_tiles(I) rows.
 int envy_tc_tiles(int I);
 size_t envy_tc_smem();
 cudaError_t launch_v_p1(const P1Args& a, float* V, cudaStream_t s);
@@ -219,7 +218,7 @@ cudaError_t launch_envy_tc(const void* r, int r_bf16, const float* V, int U, int
                            float* rmax, float* diag, int* err, cudaStream_t s);
 cudaError_t launch_envy(const void* r, int r_bf16, const float* V, int U, int I, int ld,
                         const double* imp, double esum, float* rmax, float* diag, double* ru,
-                        double* out, int* err, bool tensor_cores, cudaStream_t s);
+                        double* out, int* err, cudaStream_t s);
 // Frank-Wolfe certificate (fr_metrics.cu): one of a1 / a2 non-null (the policy's form); G CTAs
 // (cert_grid), per-CTA partials gap_part [G] doubles and res_part [G] floats; out[0] = gap,
 // out[1] = column residual.

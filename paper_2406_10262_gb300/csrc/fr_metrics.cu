@@ -6,9 +6,8 @@
 //   Imp^unif_i = (sum_u r(u,i)) (sum_{k<K} e_k) / |I|     the uniform policy x_uik = b_k / |I|
 //   better / worse: Imp_i > 1.1 Imp^unif_i / Imp_i < 0.9 Imp^unif_i (strict)
 //
-// The contraction is an FP32 SIMT GEMM (E = R^T V, 64 x 64 tiles, 4 x 4 per thread, consumers
-// streamed through shared memory 16 at a time) whose epilogue keeps only the row maxima of its
-// tile and, on diagonal tiles, E_ii: the |I|^2 matrix is never written.
+// The contraction runs on the tensor cores (fr_envy_tc.cu); its epilogue keeps only the row maxima
+// of each tile and, on diagonal tiles, E_ii: the |I|^2 matrix is never written.
 #include <cuda_bf16.h>
 
 #include "fr_device.cuh"
@@ -17,10 +16,6 @@
 namespace fr {
 
 namespace {
-
-constexpr int ET = 64;   // tile edge (items)
-constexpr int EU = 16;   // consumers per shared-memory stage
-constexpr int EMT = 4;   // micro tile edge per thread
 
 __device__ __forceinline__ float rval(const void* r, int bf16, size_t o) {
     return bf16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(r)[o])
@@ -70,70 +65,6 @@ __global__ void v_p2_kernel(const P2Args a, float* __restrict__ V) {
             v = num / S;
         }
         V[(size_t)u * a.ld + i] = v;
-    }
-}
-
-// Tile (bi, bj) of E = R^T V: rows i in [64 bi, 64 bi + 64), columns j in [64 bj, ...). Writes the
-// row maxima over the tile's valid columns to rmax[bj][i] and, on diagonal tiles, E_ii to diag[i].
-__global__ void __launch_bounds__(256) envy_gemm_kernel(const void* __restrict__ r, int r_bf16,
-                                                        const float* __restrict__ V, int U, int I,
-                                                        int ld, float* __restrict__ rmax,
-                                                        float* __restrict__ diag) {
-    __shared__ __align__(16) float sr[EU][ET];
-    __shared__ __align__(16) float sv[EU][ET];
-    __shared__ float red[ET][ET / EMT + 1];
-    const int tid = threadIdx.x;
-    const int tx = tid % (ET / EMT), ty = tid / (ET / EMT);  // 16 x 16 threads
-    const int i0 = blockIdx.y * ET, j0 = blockIdx.x * ET;
-    float acc[EMT][EMT];
-#pragma unroll
-    for (int a = 0; a < EMT; ++a)
-#pragma unroll
-        for (int b = 0; b < EMT; ++b) acc[a][b] = 0.f;
-    for (int u0 = 0; u0 < U; u0 += EU) {
-        // 16 consumers x 64 items of r and of V; thread t loads 4 consecutive items of one row
-        for (int q = tid; q < EU * ET / 4; q += blockDim.x) {
-            const int uu = q / (ET / 4), c4 = (q % (ET / 4)) * 4;
-            const int u = u0 + uu;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int ii = i0 + c4 + c, jj = j0 + c4 + c;
-                sr[uu][c4 + c] = (u < U && ii < ld) ? rval(r, r_bf16, (size_t)u * ld + ii) : 0.f;
-                sv[uu][c4 + c] = (u < U && jj < ld) ? V[(size_t)u * ld + jj] : 0.f;
-            }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int uu = 0; uu < EU; ++uu) {
-            const float4 ra = *reinterpret_cast<const float4*>(&sr[uu][ty * EMT]);
-            const float4 va = *reinterpret_cast<const float4*>(&sv[uu][tx * EMT]);
-            const float rr[4] = {ra.x, ra.y, ra.z, ra.w}, vv[4] = {va.x, va.y, va.z, va.w};
-#pragma unroll
-            for (int a = 0; a < EMT; ++a)
-#pragma unroll
-                for (int b = 0; b < EMT; ++b) acc[a][b] = fmaf(rr[a], vv[b], acc[a][b]);
-        }
-        __syncthreads();
-    }
-    // epilogue: per-thread row maxima over its 4 columns, then over the 16 column groups
-#pragma unroll
-    for (int a = 0; a < EMT; ++a) {
-        const int il = ty * EMT + a;
-        float m = -INFINITY;
-#pragma unroll
-        for (int b = 0; b < EMT; ++b) {
-            const int j = j0 + tx * EMT + b;
-            if (j < I) m = fmaxf(m, acc[a][b]);
-            if (blockIdx.x == blockIdx.y && j == i0 + il && j < I) diag[j] = acc[a][b];
-        }
-        red[il][tx] = m;
-    }
-    __syncthreads();
-    if (tid < ET) {
-        float m = -INFINITY;
-        for (int t = 0; t < ET / EMT; ++t) m = fmaxf(m, red[tid][t]);
-        const int i = i0 + tid;
-        if (i < I) rmax[(size_t)blockIdx.x * ld + i] = m;
     }
 }
 
@@ -195,8 +126,6 @@ __global__ void __launch_bounds__(1024) envy_final_kernel(const float* __restric
 
 }  // namespace
 
-int envy_tiles(int I) { return (I + ET - 1) / ET; }
-
 cudaError_t launch_v_p1(const P1Args& a, float* V, cudaStream_t s) {
     v_p1_kernel<<<a.U, 256, 0, s>>>(a, V);
     return cudaGetLastError();
@@ -209,17 +138,9 @@ cudaError_t launch_v_p2(const P2Args& a, float* V, cudaStream_t s) {
 
 cudaError_t launch_envy(const void* r, int r_bf16, const float* V, int U, int I, int ld,
                         const double* imp, double esum, float* rmax, float* diag, double* ru,
-                        double* out, int* err, bool tensor_cores, cudaStream_t s) {
-    int nt;
-    cudaError_t e;
-    if (tensor_cores) {
-        nt = envy_tc_tiles(I);
-        e = launch_envy_tc(r, r_bf16, V, U, I, ld, rmax, diag, err, s);
-    } else {
-        nt = envy_tiles(I);
-        envy_gemm_kernel<<<dim3(nt, nt), 256, 0, s>>>(r, r_bf16, V, U, I, ld, rmax, diag);
-        e = cudaGetLastError();
-    }
+                        double* out, int* err, cudaStream_t s) {
+    const int nt = envy_tc_tiles(I);
+    cudaError_t e = launch_envy_tc(r, r_bf16, V, U, I, ld, rmax, diag, err, s);
     if (e != cudaSuccess) return e;
     colsum_kernel<<<(I + 255) / 256, 256, 0, s>>>(r, r_bf16, U, I, ld, ru);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
