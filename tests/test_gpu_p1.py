@@ -189,3 +189,85 @@ def test_full_size_plain_workload_sampled_parity():
     assert rel(Fg[0], Fo[0]) < NSW_RTOL
     x0 = g.policy(1234, 1)[0]
     np.testing.assert_allclose(x0, o.policy(1234, 1)[0], atol=X_ATOL)
+
+
+def _rows_leaving_range(C, b, eps, L):
+    """How often a row's sum S_i of the fused log2-domain iteration (row shifts fixed at a cold
+    start) leaves [2^-64, 2^64] during an L-iteration solve, in FP64: the inputs below must reach
+    the exact re-shift branch of the sweeps."""
+    cp = C / (eps * np.log(2.0))
+    g = np.zeros(C.shape[1])
+    ct = cp + (g - cp).max(1)[:, None]
+    n = 0
+    for _ in range(L):
+        p = np.exp2(g - ct)
+        S = p.sum(1)
+        bad = (S < 2.0 ** -64) | (S > 2.0 ** 64)
+        if bad.any():
+            n += int(bad.sum())
+            ct[bad] += (g - ct).max(1)[bad, None]
+            p = np.exp2(g - ct)
+            S = p.sum(1)
+        g -= np.log2((p / S[:, None]).sum(0) / b)
+    return n
+
+
+@pytest.mark.parametrize("I,K,scale", [
+    (40, 10, 5.0),    # register sweep, 11 columns
+    (40, 5, 5.0),     # register sweep, 8-column bucket
+    (1030, 10, 1.5),  # tile sweep (more than 1024 items, 11 columns)
+])
+def test_rows_leaving_the_exponent_range_are_reshifted(I, K, scale):
+    """eps = 0.1 and N(0, scale^2) costs from a cold start: potentials drift far enough during the
+    solve that some rows' sums leave the exponent range fixed by their initial shift, so the sweep
+    must re-shift them exactly; the solve still matches the oracle. (Wider cost spreads at 1030
+    items leave some items with impacts below FP32's normal range, which the library reports as
+    FR_ENUMERIC; the spreads here keep every impact above 1e-26.)
+
+    Exponents reach E = max|c| / (eps ln 2) ~ 100-300 log2 units here. A term's exponent
+    g'_k - c~_ik is the difference of two FP32 numbers of magnitude up to E, each rounded (up to
+    E 2^-24 apiece), and g'_k also carries the rounding of the last column update, so the term is
+    off by up to ~3 E 2^-24 ln 2 relative; impacts (sums of such terms) and the policy are
+    compared at 4 E 2^-24 (~2.3e-5 at 1030 items, where 1.0e-5 was measured on the deepest
+    tails), F (a sum of logs over items, where these errors average) at the usual 1e-6."""
+    U, L, eps = 4, 50, 0.1
+    r = synth.relevance_lowrank(U, I, seed=4)
+    g, o = pair(U, I, K, r, epsilon=eps, sinkhorn_iters=L, warm_start=0)
+    C, m1, m2, gg = seeded_state(U, I, K, seed=21, scale=scale)
+    b, _ = oracle.marginals(I, K, synth.dcg_exposure(K))
+    assert sum(_rows_leaving_range(C[u].astype(np.float64), b, eps, L) for u in range(U)) > 0
+    g.set_state(C, m1, m2, gg, t=0)
+    o.set_state(C.astype(np.float64), m1.astype(np.float64), m2.astype(np.float64),
+                gg.astype(np.float64), 0)
+    tol = 4.0 * float(np.abs(C).max()) / (eps * np.log(2.0)) * 2.0 ** -24
+    imp, _, F = g.impacts()
+    oimp, _, oF = o.impacts()
+    assert rel(F, oF) < NSW_RTOL
+    np.testing.assert_allclose(imp, oimp, rtol=tol)
+    np.testing.assert_allclose(g.policy(), o.policy(), atol=max(X_ATOL, tol))
+
+
+@pytest.mark.parametrize("I", [1001, 1201])  # register sweep, tile sweep
+def test_several_consumers_per_cta_ragged_items(I):
+    """1300 consumers, K = 10, a ragged item count (padding rows up to the next multiple of 8 in
+    every tile): more consumers than resident CTAs, so each CTA stages and solves several in turn
+    and accumulates their impacts; whole-market F and impacts after the solve and after two ascent
+    steps, and the policies of consumers solved after the first by their CTA."""
+    U, K = 1300, 10
+    r = synth.relevance_lowrank(U, I, seed=8)
+    g, o = pair(U, I, K, r)
+    C, m1, m2, gg = seeded_state(U, I, K, seed=31, scale=0.5)
+    g.set_state(C, m1, m2, gg, t=0)
+    o.set_state(C.astype(np.float64), m1.astype(np.float64), m2.astype(np.float64),
+                gg.astype(np.float64), 0)
+    imp, _, F = g.impacts()
+    oimp, _, oF = o.impacts()
+    assert rel(F, oF) < NSW_RTOL
+    np.testing.assert_allclose(imp, oimp, rtol=1e-6)
+    dg, do = g.grad(), o.grad()
+    assert np.linalg.norm(dg - do) <= 1e-5 * np.linalg.norm(do)
+    Fg = g.step(2)
+    Fo, _ = o.step(2)
+    np.testing.assert_allclose(Fg, Fo, rtol=NSW_RTOL)
+    for u in (3, 700, 1299):
+        np.testing.assert_allclose(g.policy(u, 1)[0], o.policy(u, 1)[0], atol=X_ATOL)
