@@ -11,7 +11,7 @@ namespace fr {
 namespace {
 
 constexpr int RED_ITEMS = 32;  // items per CTA (one per lane)
-constexpr int RED_WARPS = 8;   // warps splitting the per-CTA partials
+constexpr int RED_WARPS = 32;  // warps splitting the per-CTA partials
 
 // Eq. (4) across consumers and Eq. (5): Imp_i = sum over the sweep CTAs' partials (fixed order,
 // FP64), omega_i = 1/Imp_i for the next gradient, F = sum_i log Imp_i in FP64. The last CTA to
@@ -25,10 +25,33 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a, int bid, int nb
     if (a.st->stop) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int item = bid * RED_ITEMS + lane;
-    double acc = 0.0;
-    if (item < a.I)
-        for (int g = warp; g < a.G; g += RED_WARPS) acc += (double)a.part[(size_t)g * a.ld + item];
-    s_sum[warp][lane] = acc;
+    // partials g = warp, warp + RED_WARPS, ... in two interleaved compensated FP32 sums (Knuth's
+    // TwoSum: the rounding error of every addition is carried exactly in c), so each warp's total
+    // s + c is accurate to double-level precision without FP64 arithmetic per partial (the FP64
+    // pipe is a small fraction of the FP32 one on this part); the fixed order keeps it
+    // deterministic
+    float sa[2] = {0.f, 0.f}, ca[2] = {0.f, 0.f};
+    if (item < a.I) {
+        const float* p = a.part + item;
+        const size_t step = (size_t)RED_WARPS * a.ld;
+        int g = warp;
+        auto two_sum = [](float& s, float& c, float x) {
+            const float t = __fadd_rn(s, x);
+            const float bp = __fsub_rn(t, s);
+            c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
+            s = t;
+        };
+        for (; g + 7 * RED_WARPS < a.G; g += 8 * RED_WARPS) {  // eight loads in flight
+            const float* q = p + (size_t)g * a.ld;
+            float x[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) x[j] = __ldcg(q + j * step);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) two_sum(sa[j & 1], ca[j & 1], x[j]);
+        }
+        for (; g < a.G; g += RED_WARPS) two_sum(sa[0], ca[0], __ldcg(p + (size_t)g * a.ld));
+    }
+    s_sum[warp][lane] = ((double)sa[0] + (double)ca[0]) + ((double)sa[1] + (double)ca[1]);
     __syncthreads();
     if (warp == 0) {
         double tot = 0.0;

@@ -174,7 +174,8 @@ bool p2_variant_generic(int ncb, int threads, P2Variant* out);
 // Launchers (return cudaError_t of the launch). `variant` is resolved by p1_select.
 struct P1Variant {
     int ncb, rows, exact;
-    bool tile_sweep;      // Sinkhorn phase reads its costs from the resident shared tile
+    int tile_stride;      // 0: register sweep; else the Sinkhorn phase reads its costs from the
+                          // resident shared tile, whose columns are tile_stride floats apart
     int threads;          // CTA size
     size_t smem;          // dynamic shared memory (bytes) of the largest mode
     const void* fn[3];    // kernels by Mode

@@ -62,7 +62,6 @@ struct Smem {
     float* lse;   // [ld] row log2-normalisers of the previous policy (update modes)
     float* h;     // [ld]
     float* alpha; // [ld]
-    float* vimp;  // [ld] sum_{k<K} e_k x_ik (gradient mode)
     float* X;     // [nc][ld] policy of the consumer (update modes, wide tiles only)
 };
 
@@ -74,11 +73,12 @@ __host__ __device__ inline int ncp_of(int nc) { return (nc + 3) / 4 * 4; }
 // the compiled column bucket read zeros, never a neighbouring array
 __host__ __device__ inline int ncx_of(int nc, int ncb) { return ncp_of(nc > ncb ? nc : ncb); }
 
-// ts (tile sweep): the Sinkhorn phase reads its costs from the staged tile, so the tile stays
-// resident through the solve and the next consumer is staged after it; omega and the relevance row
-// are then read from global memory (L2) and alpha overwrites h, which keeps a 1000-item CTA near
-// 55 KB (four CTAs per SM).
-__host__ __device__ inline size_t smem_layout(int ncb, int nc, int ld, int W, int mode, bool ts,
+// ts (tile sweep, ts = the shared tile's column stride in floats, a compile-time constant >= ld;
+// 0 for the register sweep, whose tile has stride ld): the Sinkhorn phase reads its costs from the
+// staged tile, so the tile stays resident through the solve and the next consumer is staged after
+// it; omega and the relevance row are then read from global memory (L2) and alpha overwrites h,
+// which keeps a 1000-item CTA near 56 KB (four CTAs per SM).
+__host__ __device__ inline size_t smem_layout(int ncb, int nc, int ld, int W, int mode, int ts,
                                               Smem* s, unsigned char* base) {
     const int P = pow2ceil(ncb);
     const int NG = n_gram(ncb);
@@ -100,9 +100,9 @@ __host__ __device__ inline size_t smem_layout(int ncb, int nc, int ld, int W, in
     const size_t o_coef = take(sizeof(float) * 2), o_bar = take(sizeof(unsigned long long));
     const size_t o_red = take(sizeof(float) * red_f);
     const size_t o_out = take(sizeof(float) * (3 * ncp + NG));
-    const size_t o_C = take(sizeof(float) * (size_t)nc * ld);
+    const size_t o_C = take(sizeof(float) * (size_t)nc * (ts ? ts : ld));
     const size_t o_r = ts ? 0 : take(sizeof(float) * ld);
-    size_t o_A = 0, o_rhs = 0, o_Lt = 0, o_om = 0, o_lse = 0, o_h = 0, o_al = 0, o_vi = 0, o_X = 0;
+    size_t o_A = 0, o_rhs = 0, o_Lt = 0, o_om = 0, o_lse = 0, o_h = 0, o_al = 0, o_X = 0;
     if (upd) {
         o_A = take(sizeof(double) * (size_t)(n > 0 ? n * n : 1));
         o_rhs = take(sizeof(double) * ncp);
@@ -111,7 +111,6 @@ __host__ __device__ inline size_t smem_layout(int ncb, int nc, int ld, int W, in
         o_lse = take(sizeof(float) * ld);
         o_h = take(sizeof(float) * ld);
         o_al = ts ? o_h : take(sizeof(float) * ld);
-        if (mode == MODE_GRAD) o_vi = take(sizeof(float) * ld);
         if (!reg_gram(ncb)) o_X = take(sizeof(float) * (size_t)nc * ld);
     }
     if (s) {
@@ -132,24 +131,28 @@ __host__ __device__ inline size_t smem_layout(int ncb, int nc, int ld, int W, in
         s->lse = (float*)(base + o_lse);
         s->h = (float*)(base + o_h);
         s->alpha = (float*)(base + o_al);
-        s->vimp = (float*)(base + o_vi);
         s->X = (float*)(base + o_X);
     }
     return off;
 }
 
 // Thread 0: bulk-copies consumer un's cost tile (and, unless ts, its relevance row) into the
-// staging buffers. Every thread of the CTA must be done reading them (the caller sits after a
-// __syncthreads).
+// staging buffers; with ts the tile's columns land ts floats apart (one copy per column). Every
+// thread of the CTA must be done reading them (the caller sits after a __syncthreads).
 __device__ __forceinline__ void stage_consumer(const P1Args& a, int un, int nc, int ld,
-                                               const Smem& s, bool prefetch_moments, bool ts) {
+                                               const Smem& s, bool prefetch_moments, int ts) {
     if (un >= a.U) return;
     const unsigned tile = (unsigned)(sizeof(float) * (size_t)nc * ld);
     const unsigned row = (unsigned)(sizeof(float) * ld);
     fence_proxy_async_smem();
     mbar_arrive_expect_tx(s.bar, ts ? tile : tile + row);
-    bulk_g2s(s.C, a.C + (size_t)un * nc * ld, tile, s.bar);
-    if (!ts) bulk_g2s(s.r, a.r + (size_t)un * ld, row, s.bar);
+    if (ts) {
+        for (int k = 0; k < nc; ++k)
+            bulk_g2s(s.C + (size_t)k * ts, a.C + ((size_t)un * nc + k) * ld, row, s.bar);
+    } else {
+        bulk_g2s(s.C, a.C + (size_t)un * nc * ld, tile, s.bar);
+        bulk_g2s(s.r, a.r + (size_t)un * ld, row, s.bar);
+    }
     if (prefetch_moments) {  // the Adam moments of that consumer: into L2 for the gradient step
         bulk_prefetch_l2(a.m1 + (size_t)un * nc * ld, tile);
         bulk_prefetch_l2(a.m2 + (size_t)un * nc * ld, tile);
@@ -173,9 +176,10 @@ __device__ __forceinline__ void prefetch_consumer(const P1Args& a, int un, int n
 // Tile sweep: the Sinkhorn phase of consumer u with its costs read from the resident shared tile
 // (the same iteration as the register sweep of p1_kernel). A thread owns R / BR blocks of BR
 // consecutive rows (BR = 2 or 4), block b at rows BR (b T + tid): the read of a block's column k
-// is one 8- or 16-byte load per lane and conflict-free (consecutive lanes, consecutive words), and
-// no costs stay in registers between iterations, which is what allows eight rows per thread at
-// four CTAs per SM. The impacts of a block's rows go straight into the CTA's partial row
+// is one 8- or 16-byte load per lane and conflict-free (consecutive lanes, consecutive words), at
+// a compile-time offset k LDS from the block's base (no address arithmetic per load), and no
+// costs stay in registers between iterations, which is what allows eight rows per thread at four
+// CTAs per SM. The impacts of a block's rows go straight into the CTA's partial row
 // part[blockIdx] (written by its first consumer, accumulated by the later ones).
 template <int BR>
 struct RowBlock {  // one load / store of a block's BR consecutive floats (8- or 16-byte aligned)
@@ -197,7 +201,7 @@ struct RowBlock {  // one load / store of a block's BR consecutive floats (8- or
     }
 };
 
-template <int NCB, int R, int BR, bool EXACT, int MODE>
+template <int NCB, int R, int BR, int LDS, bool EXACT, int MODE>
 __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u, int nc,
                                            float (&gm)[(NCB + 31) / 32], int& par) {
     static_assert((BR == 2 || BR == 4) && R % BR == 0, "blocks of two or four rows");
@@ -228,7 +232,7 @@ __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u
             for (int k = 0; k < NCB; ++k) {
                 if (EXACT || k < nc) {
                     f2 c[NP];
-                    RBk::load(cb + k * ld, c);
+                    RBk::load(cb + k * LDS, c);
 #pragma unroll
                     for (int q = 0; q < NP; ++q) {
                         float c0, c1;
@@ -242,13 +246,13 @@ __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u
             for (int k = 0; k < NCB; ++k) {
                 if (EXACT || k < nc) {
                     f2 c[NP];
-                    RBk::load(cb + k * ld, c);
+                    RBk::load(cb + k * LDS, c);
                     float v[BR];
 #pragma unroll
                     for (int q = 0; q < NP; ++q) upk(c[q], v[2 * q], v[2 * q + 1]);
 #pragma unroll
                     for (int j = 0; j < BR; ++j) v[j] = rb + j < I ? fmaf(v[j], sc, M[j]) : INFINITY;
-                    RBk::store(cb + k * ld, v);
+                    RBk::store(cb + k * LDS, v);
                 }
             }
         }
@@ -283,7 +287,7 @@ __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u
             for (int k = 0; k < NCB; ++k) {
                 if (EXACT || k < nc) {
                     f2 c[NP];
-                    RBk::load(cb + k * ld, c);
+                    RBk::load(cb + k * LDS, c);
 #pragma unroll
                     for (int q = 0; q < NP; ++q) {
                         float d0, d1;
@@ -316,7 +320,7 @@ __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u
                         float gkk, dup;
                         upk(g2[k], gkk, dup);
                         f2 c[NP];
-                        RBk::load(cb + k * ld, c);
+                        RBk::load(cb + k * LDS, c);
 #pragma unroll
                         for (int q = 0; q < NP; ++q) {
                             float c0, c1;
@@ -334,7 +338,7 @@ __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u
                 for (int k = 0; k < NCB; ++k) {
                     if (EXACT || k < nc) {
                         f2 c[NP];
-                        RBk::load(cb + k * ld, c);
+                        RBk::load(cb + k * LDS, c);
                         float v[BR];
 #pragma unroll
                         for (int q = 0; q < NP; ++q) {
@@ -345,7 +349,7 @@ __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u
                             upk(sub2(g2[k], pk(v[2 * q], v[2 * q + 1])), d0, d1);
                             p[q][k] = pk(ex2(d0), ex2(d1));
                         }
-                        RBk::store(cb + k * ld, v);
+                        RBk::store(cb + k * LDS, v);
                     }
 #pragma unroll
                     for (int q = 0; q < NP; ++q) S2[q] = add2(S2[q], p[q][k]);
@@ -409,7 +413,10 @@ __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u
         }
         column_update<NCB, GPL>(cs, gm, nc, s.red, s.ib, par, lane, warp, W);
         par ^= 1;
-        if (l == 0 && tid == 0)
+        // the next consumer's data into L2 eight iterations before the end of this solve: early
+        // enough to hide the HBM latency, late enough that four CTAs per SM prefetching at once
+        // do not evict it again before the copy after the solve
+        if (l == (a.L > 8 ? a.L - 8 : 0) && tid == 0)
             prefetch_consumer(a, u + gridDim.x, nc, ld, MODE == MODE_UPDATE_SWEEP && a.optimizer == 0);
     }
 }
@@ -433,6 +440,7 @@ __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
     const float sc = a.inv_eps_ln2;
     Smem s;
     smem_layout(NCB, nc, ld, W, MODE, TS, &s, smem_raw);
+    const int lds = TS ? TS : ld;  // column stride of the shared tile
 
     if (a.st->stop) return;  // fr_solve reached its threshold: the remaining steps are no-ops
 
@@ -504,7 +512,7 @@ __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
                     float M = -INFINITY;
 #pragma unroll
                     for (int k = 0; k < NCB; ++k) {
-                        x[k] = (EXACT || k < nc) ? s.gp[k] - s.C[k * ld + i] * sc : -INFINITY;
+                        x[k] = (EXACT || k < nc) ? s.gp[k] - s.C[k * lds + i] * sc : -INFINITY;
                         M = fmaxf(M, x[k]);
                     }
                     float S = 0.f;
@@ -533,7 +541,8 @@ __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
                     }
                     s.lse[i] = M + lg2_approx(S);
                     s.h[i] = hh;
-                    if (MODE == MODE_GRAD) s.vimp[i] = vi;
+                    // dF/dr(u,i) = (dF/dImp_i) sum_{k<K} e_k x_ik (C does not depend on r)
+                    if (MODE == MODE_GRAD && a.dr) a.dr[(size_t)u * I + i] = om_at(i) * vi;
                 }
                 cta_reduce<NCB, 3>(acc, nc, s.red, s.out, ncp);  // s.out: [q | cs | X^T h]
             }
@@ -548,7 +557,7 @@ __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
                     const float l = s.lse[i];
 #pragma unroll
                     for (int k = 0; k < NCB; ++k)
-                        x[k] = (EXACT || k < nc) ? ex2(s.gp[k] - s.C[k * ld + i] * sc - l) : 0.f;
+                        x[k] = (EXACT || k < nc) ? ex2(s.gp[k] - s.C[k * lds + i] * sc - l) : 0.f;
                     int q = 0;
 #pragma unroll
                     for (int k = 0; k < NCB - 1; ++k) {
@@ -608,7 +617,7 @@ __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
                 float sb = 0.f;
 #pragma unroll
                 for (int k = 0; k < NCB; ++k)
-                    if (EXACT || k < nc) sb += ex2(s.gp[k] - s.C[k * ld + i] * sc - l) * s.beta[k];
+                    if (EXACT || k < nc) sb += ex2(s.gp[k] - s.C[k * lds + i] * sc - l) * s.beta[k];
                 s.alpha[i] = s.h[i] - sb;
             }
             __syncthreads();
@@ -624,7 +633,8 @@ __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
                 const int k = q / g4;
                 const int i = (q - k * g4) * 4;
                 if (i >= I) continue;
-                const float4 c4 = reinterpret_cast<const float4*>(s.C)[q];
+                const int qs = k * (lds / 4) + i / 4;  // float4 index in the shared tile
+                const float4 c4 = reinterpret_cast<const float4*>(s.C)[qs];
                 const float4 l4 = reinterpret_cast<const float4*>(s.lse)[i / 4];
                 const float4 a4 = reinterpret_cast<const float4*>(s.alpha)[i / 4];
                 const float4 o4 = TS ? __ldg(reinterpret_cast<const float4*>(a.omega) + i / 4)
@@ -671,15 +681,11 @@ __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
                     }
                     const float4 cn = make_float4(cv[0], cv[1], cv[2], cv[3]);
                     *reinterpret_cast<float4*>(Cg + off) = cn;
-                    reinterpret_cast<float4*>(s.C)[q] = cn;
+                    reinterpret_cast<float4*>(s.C)[qs] = cn;
                 }
             }
             gn2 += (double)gsq;
             if constexpr (MODE == MODE_GRAD) {
-                if (a.dr) {
-                    // dF/dr(u,i) = (dF/dImp_i) sum_{k<K} e_k x_ik (C does not depend on r)
-                    for (int i = tid; i < I; i += T) a.dr[(size_t)u * I + i] = om_at(i) * s.vimp[i];
-                }
                 __syncthreads();
                 if (tid == 0) stage_consumer(a, u + gridDim.x, nc, ld, s, false, TS);
                 continue;  // no solve in gradient mode
@@ -689,7 +695,7 @@ __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
 
         // ---------------- Sinkhorn solve on the consumer's (new) costs ----------------------------
         if constexpr (TS != 0) {
-            tile_sweep<NCB, R, TS, EXACT, MODE>(a, s, u, nc, gm, par);
+            tile_sweep<NCB, R, 2, TS, EXACT, MODE>(a, s, u, nc, gm, par);
         } else {
         float rr[R];
         bool vr[R];
@@ -707,7 +713,7 @@ __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
                 float tmp[R];
 #pragma unroll
                 for (int r = 0; r < R; ++r) tmp[r] = 0.f;
-                if ((EXACT || k < nc) && any_row) ldv<R>(tmp, s.C + k * ld + i0);
+                if ((EXACT || k < nc) && any_row) ldv<R>(tmp, s.C + k * lds + i0);
 #pragma unroll
                 for (int r = 0; r < R; ++r) c[r][k] = tmp[r];
             }
@@ -881,8 +887,8 @@ __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
                 if (j * 32 + lane < nc) a.gL[(size_t)u * nc + j * 32 + lane] = gm[j];
         }
         // tile sweep: the last column update ended with a barrier after every read of the tile, so
-        // the next consumer's tile can be staged now (its L2 prefetch was issued at iteration 0)
-        if (TS && tid == 0) stage_consumer(a, u + gridDim.x, nc, ld, s, false, true);
+        // the next consumer's tile can be staged now (its L2 prefetch was issued during the solve)
+        if (TS && tid == 0) stage_consumer(a, u + gridDim.x, nc, ld, s, false, TS);
     }
 
     if constexpr (MODE != MODE_GRAD) {
@@ -906,7 +912,7 @@ __global__ void __launch_bounds__(512) p1_kernel(const P1Args a) {
     }
 }
 
-// TS: 0 register sweep, 2 or 4 tile sweep with blocks of TS rows
+// TS: 0 register sweep, else the tile sweep with that shared column stride (floats)
 template <int NCB, int R, bool EXACT, int TS = 0>
 P1Variant make_variant(int threads) {
     P1Variant v;
@@ -915,7 +921,7 @@ P1Variant make_variant(int threads) {
     v.exact = EXACT;
     v.threads = threads;
     v.smem = 0;
-    v.tile_sweep = TS != 0;
+    v.tile_stride = TS;
     v.fn[MODE_SWEEP] = (const void*)p1_kernel<NCB, R, EXACT, MODE_SWEEP, TS>;
     v.fn[MODE_UPDATE_SWEEP] = (const void*)p1_kernel<NCB, R, EXACT, MODE_UPDATE_SWEEP, TS>;
     v.fn[MODE_GRAD] = (const void*)p1_kernel<NCB, R, EXACT, MODE_GRAD, TS>;
@@ -925,7 +931,7 @@ P1Variant make_variant(int threads) {
 }  // namespace
 
 size_t p1_smem_bytes(const P1Variant& v, int mode, int nc, int ld) {
-    return smem_layout(v.ncb, nc, ld, v.threads / 32, mode, v.tile_sweep, nullptr, nullptr);
+    return smem_layout(v.ncb, nc, ld, v.threads / 32, mode, v.tile_stride, nullptr, nullptr);
 }
 
 // Compiled variants: exact column counts for the hot shapes, padded buckets for the rest.
@@ -936,15 +942,22 @@ bool p1_select(int nc, int I, P1Variant* out) {
         return (t + 31) / 32 * 32;
     };
     P1Variant v;
-    // 11 columns: costs in registers up to 1024 items (256-thread CTAs, two per SM); beyond that
-    // the tile sweep (eight rows per thread, costs read from the resident tile), which keeps
-    // two CTAs per SM up to 2048 items and reaches 4096. On 250 x 2000 the tile sweep's fused
-    // step is 12 % faster than the register sweep's (one 512-thread CTA per SM); at 1000 items
-    // and below the two are level or the register sweep is ahead.
-    if (nc == 11 && threads_for(4) <= 256) {
+    // 11 columns: costs in registers up to 768 items; beyond that the tile sweep (eight rows per
+    // thread, costs read from the resident tile at a compile-time column stride of 1024, 2048 or
+    // 4096 floats), up to 4096 items. Measured fused steps: 2000 x 1000 0.485 vs 0.506 ms,
+    // 2000 x 2000 0.977 vs 1.126 ms, 250 x 2000 0.148 vs 0.174 ms for the tile sweep; at 250 and
+    // 500 items a 1024-float stride leaves one-warp CTAs four to an SM and the tile sweep runs
+    // at half the register sweep's speed.
+    const int ld = (I + 7) / 8 * 8;
+    if (nc == 11 && ld <= 768 && threads_for(4) <= 512) {
         v = make_variant<11, 4, true>(threads_for(4));
     } else if (nc == 11 && threads_for(8) <= 512) {
-        v = make_variant<11, 8, true, 2>(threads_for(8));
+        if (ld <= 1024)
+            v = make_variant<11, 8, true, 1024>(threads_for(8));
+        else if (ld <= 2048)
+            v = make_variant<11, 8, true, 2048>(threads_for(8));
+        else
+            v = make_variant<11, 8, true, 4096>(threads_for(8));
     } else if (nc == 50 && threads_for(1) <= 512) {
         v = make_variant<50, 1, true>(threads_for(1));
     } else if (nc <= 8 && threads_for(4) <= 512) {
