@@ -59,7 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling driver: set up the workload, run this many ascent steps, exit")
-    ap.add_argument("--compare", choices=["batch", "unrolled", "bf16", "paper-shapes"], default=None,
+    ap.add_argument("--compare", choices=["batch", "unrolled", "bf16", "paper-shapes", "p1-scale"],
+                    default=None,
                     help="compare a layered form against the plain FP32 method (one JSON line)")
     ap.add_argument("--profile-item", choices=["implicit", "unrolled", "bf16", "batch"], default=None,
                     help="profiling driver for the per-item forms: set up the workload, run "
@@ -469,6 +470,60 @@ def compare_bf16(args):
     return out
 
 
+def compare_p1_scale(args):
+    """The free-cost parametrisation (the paper's Problem (8)) at the sizes of the differentiation
+    and batching workloads: (a) |U| = 20000, |I| = 2000, K = 20 (21 columns), L = 100, S ascent
+    steps (implicit gradient, Adam) from C = 0 with the per-step kernel times; (b) the 256 markets
+    of the batching workload's size distribution, each a free-cost context created, advanced S
+    steps from C = 0 and destroyed in turn (one market's state on the device at a time)."""
+    import torch
+    from paper_2406_10262_gb300 import fairrank as fr
+    from paper_2406_10262_gb300 import synth
+    out = {"compare": "p1-scale"}
+    U, I, K, L, S = 20000, 2000, 20, 100, max(args.steps, 1) * 2
+    r = synth.relevance_lowrank_fast(U, I, seed=7)
+    g = fr.FairRank(U, I, K, sinkhorn_iters=L, lr=0.1)
+    g.set_relevance(r)
+    g.set_exposure(synth.dcg_exposure(K))
+    g.step(1, trace=False)  # warm-up (graph capture)
+    g.reset()
+    F, t = _timed(lambda: g.step(S))
+    kms = g.time_kernels(3)
+    nc = fr.num_cols(I, K)
+    out["differentiation_size"] = {
+        "n_users": U, "n_items": I, "n_slots": K, "n_cols": nc, "sinkhorn_iters": L,
+        "ascent_steps": S, "s_per_run": t, "F": [float(x) for x in F],
+        "fused_ms": kms[0], "reduce_ms": kms[1], "sweep_only_ms": kms[2],
+        "sweep_cell_updates_per_s": U * I * nc * L / (kms[2] * 1e-3),
+        "state_bytes": 3 * U * nc * ((I + 7) // 8 * 8) * 4}
+    del g
+    S2, L2 = max(args.steps, 1) * 8, 50
+    ms = synth.markets(256, seed=0)
+    cells, t_dev, t_all, Fs = 0, 0.0, 0.0, []
+    for m in ms:
+        U, I, K = m.n_users, m.n_items, m.n_slots
+        r = synth.relevance_lowrank_fast(U, I, seed=m.seed)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = fr.FairRank(U, I, K, sinkhorn_iters=L2)
+        g.set_relevance(r)
+        g.set_exposure(synth.dcg_exposure(K))
+        F, t = _timed(lambda: g.step(S2))
+        del g
+        torch.cuda.synchronize()
+        t_all += time.perf_counter() - t0
+        t_dev += t
+        cells += U * I * fr.num_cols(I, K)
+        Fs.append(float(F[-1]))
+    cu = cells * L2 * (S2 + 1)
+    out["batching_markets"] = {
+        "markets": len(ms), "ascent_steps": S2, "sinkhorn_iters": L2, "cells": cells,
+        "cell_updates": cu, "step_s": t_dev, "with_setup_s": t_all,
+        "cell_updates_per_s": cu / t_dev, "F_min": min(Fs), "F_max": max(Fs),
+        "all_F_finite": bool(np.all(np.isfinite(Fs)))}
+    return out
+
+
 def compare_paper_shapes(args):
     """Computation time per ascent step of the free-cost method (the paper's Algorithm 1, K = 10,
     m = 11, L = 50) on the shapes of the paper's timing figure: |U| swept at |I| = 250 and |I|
@@ -553,7 +608,7 @@ def main():
         from paper_2406_10262_gb300 import build as frbuild
         frbuild.build()
         fn = {"batch": compare_batch, "unrolled": compare_unrolled, "bf16": compare_bf16,
-              "paper-shapes": compare_paper_shapes}[args.compare]
+              "paper-shapes": compare_paper_shapes, "p1-scale": compare_p1_scale}[args.compare]
         print(json.dumps(fn(args)), flush=True)
         return
     w = workload(args.workload)

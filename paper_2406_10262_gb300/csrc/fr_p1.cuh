@@ -1,0 +1,997 @@
+// fr_p1.cuh -- kernels of the free-cost parametrisation (Problem (8): one cost c_uik per cell),
+// instantiated by fr_p1.cu (the variant table) and fr_p1_k21.cu (21 columns).
+//
+// One persistent CTA processes consumers u = blockIdx.x, blockIdx.x + G, ... (Algorithm 1's
+// parallel loop over consumers). Each consumer's cost tile and relevance row are bulk-copied (TMA)
+// into shared memory one consumer ahead, while the previous consumer's Sinkhorn iterations run.
+//
+// Sinkhorn (Problem (7)) runs in the fused single-pass log-domain form, in log2 units
+// c' = c / (eps ln 2), g' = g / (eps ln 2):
+//   p_ik = 2^(g'_k - c~_ik),  S_i = sum_k p_ik,  x_ik = p_ik / S_i       (row update, Eq. 1)
+//   cs_k = sum_i x_ik,        g'_k += log2 b_k - log2 cs_k               (column update, Eq. 2)
+// which equals the textbook two-pass update (f_i = -eps LSE_k, g_k = eps log b_k - eps LSE_i)
+// algebraically and costs one exp2 per cell per iteration. In the register sweep a thread owns R
+// consecutive items (rows) and keeps their costs in registers for the whole solve; in the tile
+// sweep (tile_sweep below) it owns R / 2 pairs of rows and reads their costs from the resident
+// shared tile every iteration. c~_ik = c'_ik + shift_i carries
+// a per-row shift fixed at the start of the solve (the row max), so 2^(.) stays in range without
+// a max pass per iteration; a row whose S_i leaves [2^-64, 2^64] is re-shifted exactly.
+//
+// Inner loop: two rows at a time in packed f32x2 arithmetic (one instruction per pair of cells),
+// one exp2 per cell on the MUFU. Column sums: per-warp reduce-scatter by shuffles, one
+// __syncthreads per iteration on double-buffered partials, after which every warp sums the
+// per-warp partials of its lanes' columns in the same fixed order and updates its own copy of the
+// column potentials (so no second barrier is needed and every warp holds identical g').
+//
+// The last iteration emits x (the policy right after the last row update, rows sum to 1) and adds
+// r(u,i) * sum_{k<K} e_k x_ik into impact partials (Eq. 4) that accumulate over the CTA's
+// consumers in part[blockIdx][i] (per-thread registers written once per launch in the register
+// sweep, the partial row itself in the tile sweep); the reduction kernel combines them across CTAs
+// in a fixed order.
+//
+// MODE_UPDATE_SWEEP first takes the gradient step of Algorithm 1 for the consumer, working from
+// the shared-memory tile with compact loops (the code runs once per consumer, so it is kept small
+// for the instruction cache): it re-forms the previous policy from C and g^(L-1), computes dF/dC
+// by implicit differentiation of the optimality conditions of Problem (7),
+//   h_i = sum_k x_ik G_ik, q_k = sum_i x_ik G_ik, (diag(cs) - X^T X) beta = q - X^T h (beta_last = 0),
+//   alpha_i = h_i - sum_k x_ik beta_k,  dF/dc_ik = -(1/eps) x_ik (G_ik - alpha_i - beta_k),
+// with G_ik = r(u,i) e_k / Imp_i, applies Adam (ascent) to the tile and writes C and the moments
+// back, then solves Sinkhorn on the new costs without reloading them from HBM. The Gram block is
+// accumulated in registers for tiles of up to 21 columns (in passes of at most 64 entries) and from
+// a shared copy of the policy otherwise; the (m-1) x (m-1) system is solved by one warp,
+// lane-parallel in single precision for tiles of up to 21 columns (double-precision division and
+// square root are long software sequences on this part) and in double precision for wider ones.
+#pragma once
+#include "fr_device.cuh"
+#include "fr_internal.h"
+
+namespace fr {
+
+namespace {
+
+struct Smem {
+    float* gp;    // [ncx] g^(L-1)' of the previous solve (update modes)
+    float* ib;    // [ncx] 1 / b_k
+    float* e;     // [ncx] exposure
+    float* beta;  // [ncx]
+    float* coef;  // [2] Adam step size and sqrt of the second bias correction
+    unsigned long long* bar;  // mbarrier of the staged copies
+    float* red;   // reduction scratch (sweep double buffer / update reductions)
+    float* out;   // [3*ncp + NG] reduction results
+    double* A;    // [n*n] Gram system (update modes; floats for narrow tiles)
+    double* rhs;  // [ncp]
+    float* Lt;    // [n*n] transposed Cholesky factor (update modes, narrow tiles)
+    float* C;     // [nc][ld] staged cost tile of the consumer
+    float* r;     // [ld] staged relevance row
+    float* om;    // [ld] dF/dImp_i (update modes)
+    float* lse;   // [ld] row log2-normalisers of the previous policy (update modes)
+    float* h;     // [ld]
+    float* alpha; // [ld]
+    float* X;     // [nc][ld] policy of the consumer (update modes, wide tiles only)
+};
+
+// The Gram block of diag(cs) - X^T X is accumulated in registers for tiles of up to 21 columns, in
+// passes of at most 64 entries (re-forming the policy each pass); wider tiles keep a shared copy of
+// the policy instead.
+__host__ __device__ constexpr bool reg_gram(int ncb) { return ncb <= 21; }
+__host__ __device__ constexpr int n_gram(int ncb) { return reg_gram(ncb) ? ncb * (ncb - 1) / 2 : 1; }
+__host__ __device__ constexpr int gram_chunk(int ncb) {
+    return (n_gram(ncb) + (n_gram(ncb) + 63) / 64 - 1) / ((n_gram(ncb) + 63) / 64);
+}
+
+__host__ __device__ inline int ncp_of(int nc) { return (nc + 3) / 4 * 4; }
+// per-column shared arrays hold max(nc, NCB) entries (zero beyond nc) so that unrolled loops over
+// the compiled column bucket read zeros, never a neighbouring array
+__host__ __device__ inline int ncx_of(int nc, int ncb) { return ncp_of(nc > ncb ? nc : ncb); }
+
+// ts (tile sweep, ts = the shared tile's column stride in floats, a compile-time constant >= ld;
+// 0 for the register sweep, whose tile has stride ld): the Sinkhorn phase reads its costs from the
+// staged tile, so the tile stays resident through the solve and the next consumer is staged after
+// it; omega and the relevance row are then read from global memory (L2) and alpha overwrites h,
+// which keeps a 1000-item CTA near 56 KB (four CTAs per SM).
+__host__ __device__ inline size_t smem_layout(int ncb, int nc, int ld, int W, int mode, int ts,
+                                              Smem* s, unsigned char* base) {
+    const int P = pow2ceil(ncb);
+    const int NG = n_gram(ncb);
+    const int PG = pow2ceil(gram_chunk(ncb));
+    const int ncp = ncp_of(nc);
+    const int ncx = ncx_of(nc, ncb);
+    const int n = nc - 1;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += (bytes + 15) / 16 * 16;
+        return o;
+    };
+    const bool upd = mode != MODE_SWEEP;
+    size_t red_f = (size_t)W * 3 * P;
+    if ((size_t)W * PG > red_f) red_f = (size_t)W * PG;
+    const size_t o_gp = take(sizeof(float) * ncx), o_ib = take(sizeof(float) * ncx);
+    const size_t o_e = take(sizeof(float) * ncx), o_beta = take(sizeof(float) * ncx);
+    const size_t o_coef = take(sizeof(float) * 2), o_bar = take(sizeof(unsigned long long));
+    const size_t o_red = take(sizeof(float) * red_f);
+    const size_t o_out = take(sizeof(float) * (3 * ncp + NG));
+    const size_t o_C = take(sizeof(float) * (size_t)nc * (ts ? ts : ld));
+    const size_t o_r = ts ? 0 : take(sizeof(float) * ld);
+    size_t o_A = 0, o_rhs = 0, o_Lt = 0, o_om = 0, o_lse = 0, o_h = 0, o_al = 0, o_X = 0;
+    if (upd) {
+        o_A = take(sizeof(double) * (size_t)(n > 0 ? n * n : 1));
+        o_rhs = take(sizeof(double) * ncp);
+        o_Lt = take(sizeof(float) * (size_t)(n > 0 ? n * n : 1));
+        o_om = ts ? 0 : take(sizeof(float) * ld);
+        o_lse = take(sizeof(float) * ld);
+        o_h = take(sizeof(float) * ld);
+        o_al = ts ? o_h : take(sizeof(float) * ld);
+        if (!reg_gram(ncb)) o_X = take(sizeof(float) * (size_t)nc * ld);
+    }
+    if (s) {
+        s->gp = (float*)(base + o_gp);
+        s->ib = (float*)(base + o_ib);
+        s->e = (float*)(base + o_e);
+        s->beta = (float*)(base + o_beta);
+        s->coef = (float*)(base + o_coef);
+        s->bar = (unsigned long long*)(base + o_bar);
+        s->red = (float*)(base + o_red);
+        s->out = (float*)(base + o_out);
+        s->A = (double*)(base + o_A);
+        s->rhs = (double*)(base + o_rhs);
+        s->Lt = (float*)(base + o_Lt);
+        s->C = (float*)(base + o_C);
+        s->r = ts ? nullptr : (float*)(base + o_r);
+        s->om = ts ? nullptr : (float*)(base + o_om);
+        s->lse = (float*)(base + o_lse);
+        s->h = (float*)(base + o_h);
+        s->alpha = (float*)(base + o_al);
+        s->X = (float*)(base + o_X);
+    }
+    return off;
+}
+
+// Thread 0: bulk-copies consumer un's cost tile (and, unless ts, its relevance row) into the
+// staging buffers; with ts the tile's columns land ts floats apart (one copy per column). Every
+// thread of the CTA must be done reading them (the caller sits after a __syncthreads).
+__device__ __forceinline__ void stage_consumer(const P1Args& a, int un, int nc, int ld,
+                                               const Smem& s, bool prefetch_moments, int ts) {
+    if (un >= a.U) return;
+    const unsigned tile = (unsigned)(sizeof(float) * (size_t)nc * ld);
+    const unsigned row = (unsigned)(sizeof(float) * ld);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(s.bar, ts ? tile : tile + row);
+    if (ts) {
+        for (int k = 0; k < nc; ++k)
+            bulk_g2s(s.C + (size_t)k * ts, a.C + ((size_t)un * nc + k) * ld, row, s.bar);
+    } else {
+        bulk_g2s(s.C, a.C + (size_t)un * nc * ld, tile, s.bar);
+        bulk_g2s(s.r, a.r + (size_t)un * ld, row, s.bar);
+    }
+    if (prefetch_moments) {  // the Adam moments of that consumer: into L2 for the gradient step
+        bulk_prefetch_l2(a.m1 + (size_t)un * nc * ld, tile);
+        bulk_prefetch_l2(a.m2 + (size_t)un * nc * ld, tile);
+    }
+}
+
+// Thread 0, tile sweep: pulls consumer un's tile, relevance row and (update mode) Adam moments into
+// L2 while the current consumer's solve still holds the shared tile.
+__device__ __forceinline__ void prefetch_consumer(const P1Args& a, int un, int nc, int ld,
+                                                  bool moments) {
+    if (un >= a.U) return;
+    const unsigned tile = (unsigned)(sizeof(float) * (size_t)nc * ld);
+    bulk_prefetch_l2(a.C + (size_t)un * nc * ld, tile);
+    bulk_prefetch_l2(a.r + (size_t)un * ld, (unsigned)(sizeof(float) * ld));
+    if (moments) {
+        bulk_prefetch_l2(a.m1 + (size_t)un * nc * ld, tile);
+        bulk_prefetch_l2(a.m2 + (size_t)un * nc * ld, tile);
+    }
+}
+
+// Gram entries Q0 .. Q0 + NQ - 1 (the upper triangle of the leading (NCB-1) x (NCB-1) block, row by
+// row) of diag(cs) - X^T X over the consumer's rows, from the policy re-formed as
+// x_ik = 2^(g'_k - c'_ik - lse_i); rows of x sum to 1, so the diagonal is sum_i x_ik (1 - x_ik)
+// without cancellation. The CTA sums land in gout[Q0 ..]. Every thread of the CTA must call it.
+template <int NCB, bool EXACT, int Q0, int NQ>
+__device__ __forceinline__ void gram_pass(const Smem& s, int nc, int I, int lds, float sc,
+                                          float* gout) {
+    const int n = nc - 1;
+    float gram[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) gram[q] = 0.f;
+    for (int i = threadIdx.x; i < I; i += blockDim.x) {
+        float x[NCB];
+        const float l = s.lse[i];
+#pragma unroll
+        for (int k = 0; k < NCB; ++k)
+            x[k] = (EXACT || k < nc) ? ex2(s.gp[k] - s.C[k * lds + i] * sc - l) : 0.f;
+        int q = 0;
+#pragma unroll
+        for (int k = 0; k < NCB - 1; ++k) {
+#pragma unroll
+            for (int m = k; m < NCB - 1; ++m, ++q) {
+                if (q >= Q0 && q < Q0 + NQ && (EXACT || m < n))
+                    gram[q - Q0] += k == m ? x[k] * (1.f - x[k]) : -x[k] * x[m];
+            }
+        }
+    }
+    cta_reduce_vec<NQ>(gram, NQ, s.red, gout + Q0);
+}
+
+template <int NCB, bool EXACT, int Q0 = 0>
+__device__ __forceinline__ void gram_block(const Smem& s, int nc, int I, int lds, float sc,
+                                           float* gout) {
+    constexpr int NGALL = n_gram(NCB), CH = gram_chunk(NCB);
+    constexpr int NQ = NGALL - Q0 < CH ? NGALL - Q0 : CH;
+    gram_pass<NCB, EXACT, Q0, NQ>(s, nc, I, lds, sc, gout);
+    if constexpr (Q0 + NQ < NGALL) gram_block<NCB, EXACT, Q0 + NQ>(s, nc, I, lds, sc, gout);
+}
+
+// Tile sweep: the Sinkhorn phase of consumer u with its costs read from the resident shared tile
+// (the same iteration as the register sweep of p1_kernel). A thread owns R / BR blocks of BR
+// consecutive rows (BR = 2 or 4), block b at rows BR (b T + tid): the read of a block's column k
+// is one 8- or 16-byte load per lane and conflict-free (consecutive lanes, consecutive words), at
+// a compile-time offset k LDS from the block's base (no address arithmetic per load), and no
+// costs stay in registers between iterations, which is what allows eight rows per thread at four
+// CTAs per SM. The impacts of a block's rows go straight into the CTA's partial row
+// part[blockIdx] (written by its first consumer, accumulated by the later ones).
+template <int BR>
+struct RowBlock {  // one load / store of a block's BR consecutive floats (8- or 16-byte aligned)
+    static __device__ __forceinline__ void load(const float* p, f2 (&c)[BR / 2]) {
+        if constexpr (BR == 2) {
+            const float2 v = *reinterpret_cast<const float2*>(p);
+            c[0] = pk(v.x, v.y);
+        } else {
+            const float4 v = *reinterpret_cast<const float4*>(p);
+            c[0] = pk(v.x, v.y);
+            c[1] = pk(v.z, v.w);
+        }
+    }
+    static __device__ __forceinline__ void store(float* p, const float (&v)[BR]) {
+        if constexpr (BR == 2)
+            *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+        else
+            *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+
+template <int NCB, int R, int BR, int LDS, bool EXACT, int MODE>
+__device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u, int nc,
+                                           float (&gm)[(NCB + 31) / 32], int& par) {
+    static_assert((BR == 2 || BR == 4) && R % BR == 0, "blocks of two or four rows");
+    constexpr int GPL = (NCB + 31) / 32;
+    constexpr int NB = R / BR, NP = BR / 2;
+    using RBk = RowBlock<BR>;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
+    const int T = blockDim.x, I = a.I, ld = a.ld;
+    const float sc = a.inv_eps_ln2;
+    // Block b starts at row rb = BR (b T + tid); ld is a multiple of 8, so a block lies inside the
+    // tile (rb < ld) or past it. Row j of the block is a consumer row if rb + j < I.
+    //
+    // c~_ik = c_ik / (eps ln 2) + shift_i in place, shift_i = max_k (g'_k - c_ik / (eps ln 2)), so
+    // that the row's largest term is 2^0; +inf on the padding rows I <= i < ld (their terms are 0).
+    // Each thread rewrites only its own rows, which only it reads during the solve.
+    {
+        float gk[NCB];
+        bcast_g<NCB, GPL>(gm, gk);
+#pragma unroll 1
+        for (int b = 0; b < NB; ++b) {
+            const int rb = BR * (b * T + tid);
+            if (rb >= ld) break;
+            float* cb = s.C + rb;
+            float M[BR];
+#pragma unroll
+            for (int j = 0; j < BR; ++j) M[j] = -INFINITY;
+#pragma unroll
+            for (int k = 0; k < NCB; ++k) {
+                if (EXACT || k < nc) {
+                    f2 c[NP];
+                    RBk::load(cb + k * LDS, c);
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) {
+                        float c0, c1;
+                        upk(c[q], c0, c1);
+                        M[2 * q] = fmaxf(M[2 * q], gk[k] - c0 * sc);
+                        M[2 * q + 1] = fmaxf(M[2 * q + 1], gk[k] - c1 * sc);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NCB; ++k) {
+                if (EXACT || k < nc) {
+                    f2 c[NP];
+                    RBk::load(cb + k * LDS, c);
+                    float v[BR];
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) upk(c[q], v[2 * q], v[2 * q + 1]);
+#pragma unroll
+                    for (int j = 0; j < BR; ++j) v[j] = rb + j < I ? fmaf(v[j], sc, M[j]) : INFINITY;
+                    RBk::store(cb + k * LDS, v);
+                }
+            }
+        }
+    }
+    for (int l = 0; l < a.L; ++l) {
+        const bool last = l == a.L - 1;
+        if (last && warp == 0) {
+#pragma unroll
+            for (int j = 0; j < GPL; ++j)
+                if (j * 32 + lane < nc) a.gP[(size_t)u * nc + j * 32 + lane] = gm[j];
+        }
+        // Tiles of up to 16 columns hold g' as packed pairs (g'_k, g'_k) and the column sums as
+        // packed row-pair partials; wider tiles hold both as scalars (pairs formed at use, column
+        // sums accumulated with two FMAs), which keeps 21 columns within the register budget.
+        constexpr bool WIDE = NCB > 16;
+        float gk[NCB];
+        bcast_g<NCB, GPL>(gm, gk);
+        f2 g2[WIDE ? 1 : NCB];
+        if constexpr (!WIDE) {
+#pragma unroll
+            for (int k = 0; k < NCB; ++k) g2[k] = pk(gk[k], gk[k]);
+        }
+        auto gpair = [&](int k) -> f2 {
+            if constexpr (WIDE) return pk(gk[k], gk[k]);
+            else return g2[k];
+        };
+        auto gscal = [&](int k) -> float {
+            if constexpr (WIDE) {
+                return gk[k];
+            } else {
+                float lo, hi;
+                upk(g2[k], lo, hi);
+                return lo;
+            }
+        };
+        f2 cs2[WIDE ? 1 : NCB];
+        float csw[WIDE ? NCB : 1];
+#pragma unroll
+        for (int k = 0; k < (WIDE ? 1 : NCB); ++k) cs2[k] = 0ull;
+#pragma unroll
+        for (int k = 0; k < (WIDE ? NCB : 1); ++k) csw[k] = 0.f;
+#pragma unroll 1
+        for (int b = 0; b < NB; ++b) {
+            const int rb = BR * (b * T + tid);
+            if (rb >= ld) break;
+            float* cb = s.C + rb;
+            f2 p[NP][NCB];  // row pairs (0, 1) and (2, 3) of the block
+            f2 S2[NP];
+#pragma unroll
+            for (int q = 0; q < NP; ++q) S2[q] = 0ull;
+#pragma unroll
+            for (int k = 0; k < NCB; ++k) {
+                if (EXACT || k < nc) {
+                    f2 c[NP];
+                    RBk::load(cb + k * LDS, c);
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) {
+                        float d0, d1;
+                        upk(sub2(gpair(k), c[q]), d0, d1);
+                        p[q][k] = pk(ex2(d0), ex2(d1));
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) p[q][k] = 0ull;
+                }
+#pragma unroll
+                for (int q = 0; q < NP; ++q) S2[q] = add2(S2[q], p[q][k]);
+            }
+            float S[BR];
+#pragma unroll
+            for (int q = 0; q < NP; ++q) upk(S2[q], S[2 * q], S[2 * q + 1]);
+            bool bad[BR], any_bad = false;
+#pragma unroll
+            for (int j = 0; j < BR; ++j) {
+                bad[j] = rb + j < I && !(S[j] >= 0x1p-64f && S[j] <= 0x1p64f);
+                any_bad |= bad[j];
+            }
+            if (__builtin_expect(any_bad, 0)) {  // re-shift the block's out-of-range rows exactly
+                float M[BR];
+#pragma unroll
+                for (int j = 0; j < BR; ++j) M[j] = -INFINITY;
+#pragma unroll
+                for (int k = 0; k < NCB; ++k) {
+                    if (EXACT || k < nc) {
+                        const float gkk = gscal(k);
+                        f2 c[NP];
+                        RBk::load(cb + k * LDS, c);
+#pragma unroll
+                        for (int q = 0; q < NP; ++q) {
+                            float c0, c1;
+                            upk(c[q], c0, c1);
+                            M[2 * q] = fmaxf(M[2 * q], gkk - c0);
+                            M[2 * q + 1] = fmaxf(M[2 * q + 1], gkk - c1);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < BR; ++j) M[j] = bad[j] ? M[j] : 0.f;
+#pragma unroll
+                for (int q = 0; q < NP; ++q) S2[q] = 0ull;
+#pragma unroll
+                for (int k = 0; k < NCB; ++k) {
+                    if (EXACT || k < nc) {
+                        f2 c[NP];
+                        RBk::load(cb + k * LDS, c);
+                        float v[BR];
+#pragma unroll
+                        for (int q = 0; q < NP; ++q) {
+                            upk(c[q], v[2 * q], v[2 * q + 1]);
+                            v[2 * q] += M[2 * q];
+                            v[2 * q + 1] += M[2 * q + 1];
+                            float d0, d1;
+                            upk(sub2(gpair(k), pk(v[2 * q], v[2 * q + 1])), d0, d1);
+                            p[q][k] = pk(ex2(d0), ex2(d1));
+                        }
+                        RBk::store(cb + k * LDS, v);
+                    }
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) S2[q] = add2(S2[q], p[q][k]);
+                }
+#pragma unroll
+                for (int q = 0; q < NP; ++q) upk(S2[q], S[2 * q], S[2 * q + 1]);
+            }
+            float inv[BR];
+#pragma unroll
+            for (int j = 0; j < BR; ++j) inv[j] = rb + j < I ? rcp_approx(S[j]) : 0.f;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const f2 i2 = pk(inv[2 * q], inv[2 * q + 1]);
+#pragma unroll
+                for (int k = 0; k < NCB; ++k) {
+                    if constexpr (WIDE) {
+                        float p0, p1;
+                        upk(p[q][k], p0, p1);
+                        csw[k] = fmaf(p1, inv[2 * q + 1], fmaf(p0, inv[2 * q], csw[k]));
+                    } else {
+                        cs2[k] = fma2(p[q][k], i2, cs2[k]);
+                    }
+                }
+            }
+            if (last) {  // impacts: r(u,i) sum_{k<K} e_k x_ik for the block's rows
+                float w[BR];
+#pragma unroll
+                for (int j = 0; j < BR; ++j) w[j] = 0.f;
+#pragma unroll
+                for (int k = 0; k < NCB; ++k) {
+                    if (k < a.K) {
+                        const float ek = s.e[k];
+#pragma unroll
+                        for (int q = 0; q < NP; ++q) {
+                            float p0, p1;
+                            upk(p[q][k], p0, p1);
+                            w[2 * q] += ek * p0;
+                            w[2 * q + 1] += ek * p1;
+                        }
+                    }
+                }
+                float* pp = a.part + (size_t)blockIdx.x * ld + rb;
+                f2 rr[NP], acc[NP];
+                RBk::load(a.r + (size_t)u * ld + rb, rr);
+                if (u == (int)blockIdx.x) {
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) acc[q] = 0ull;
+                } else {
+                    RBk::load(pp, acc);
+                }
+                float v[BR];
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    float r0, r1, a0, a1;
+                    upk(rr[q], r0, r1);
+                    upk(acc[q], a0, a1);
+                    v[2 * q] = a0 + r0 * (w[2 * q] * inv[2 * q]);
+                    v[2 * q + 1] = a1 + r1 * (w[2 * q + 1] * inv[2 * q + 1]);
+                }
+                RBk::store(pp, v);
+            }
+        }
+        float cs[NCB];
+#pragma unroll
+        for (int k = 0; k < NCB; ++k) {
+            if constexpr (WIDE) {
+                cs[k] = csw[k];
+            } else {
+                float lo, hi;
+                upk(cs2[k], lo, hi);
+                cs[k] = lo + hi;
+            }
+        }
+        column_update<NCB, GPL>(cs, gm, nc, s.red, s.ib, par, lane, warp, W);
+        par ^= 1;
+        // the next consumer's data into L2 eight iterations before the end of this solve: early
+        // enough to hide the HBM latency, late enough that four CTAs per SM prefetching at once
+        // do not evict it again before the copy after the solve
+        if (l == (a.L > 8 ? a.L - 8 : 0) && tid == 0)
+            prefetch_consumer(a, u + gridDim.x, nc, ld, MODE == MODE_UPDATE_SWEEP && a.optimizer == 0);
+    }
+}
+
+// Launch bound: 512 threads, except the tile sweep of more than 16 columns, which serves at most
+// 2048 items (256 threads) and may then use up to 255 registers per thread.
+template <int NCB, int R, bool EXACT, int MODE, int TS>
+__global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(const P1Args a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int GPL = (NCB + 31) / 32;
+    constexpr bool REG_GRAM = reg_gram(NCB);
+    constexpr bool PAIR = R % 2 == 0;
+    const int nc = EXACT ? NCB : a.nc;
+    const int ncp = ncp_of(nc);
+    const int ncx = ncx_of(nc, NCB);
+    const int n = nc - 1;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
+    const int T = blockDim.x;
+    const int I = a.I, ld = a.ld;
+    const int i0 = tid * R;
+    const bool any_row = i0 < I;
+    const float sc = a.inv_eps_ln2;
+    Smem s;
+    smem_layout(NCB, nc, ld, W, MODE, TS, &s, smem_raw);
+    const int lds = TS ? TS : ld;  // column stride of the shared tile
+
+    if (a.st->stop) return;  // fr_solve reached its threshold: the remaining steps are no-ops
+
+    if (tid == 0) {
+        mbar_init(s.bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();  // the mbarrier is initialised before any thread waits on it
+    if (tid == 0) {
+        stage_consumer(a, blockIdx.x, nc, ld, s, MODE == MODE_UPDATE_SWEEP && a.optimizer == 0, TS);
+        // Adam bias corrections for this step (t counts applied steps before this one)
+        float step_size = a.lr, bc2s = 1.f;
+        if (MODE == MODE_UPDATE_SWEEP && a.optimizer == 0) {
+            const double t1 = (double)(a.st->t + 1);
+            const double bc1 = 1.0 - pow((double)a.beta1, t1);
+            const double bc2 = 1.0 - pow((double)a.beta2, t1);
+            step_size = (float)((double)a.lr / bc1);
+            bc2s = (float)sqrt(bc2);
+        }
+        s.coef[0] = step_size;
+        s.coef[1] = bc2s;
+    }
+    for (int k = tid; k < ncx; k += T) {
+        s.ib[k] = k < nc ? a.invb[k] : 0.f;
+        s.e[k] = k < nc ? a.e[k] : 0.f;
+    }
+    if (MODE != MODE_SWEEP && !TS)
+        for (int i = tid; i < ld; i += T) s.om[i] = i < I ? a.omega[i] : 0.f;
+    // omega_i and r(u,i): the staged copies, or (tile sweep) global memory; omega has ld entries,
+    // zero beyond I
+    auto om_at = [&](int i) { return TS ? __ldg(a.omega + i) : s.om[i]; };
+
+    float acc_imp[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc_imp[r] = 0.f;
+    double gn2 = 0.0;
+    int par = 0;
+    unsigned phase = 0;
+
+    for (int u = blockIdx.x; u < a.U; u += gridDim.x) {
+        const size_t tile = (size_t)u * nc * ld;
+        const float* __restrict__ r_u = a.r + (size_t)u * ld;
+        auto r_at = [&](int i) { return TS ? __ldg(r_u + i) : s.r[i]; };
+        float gm[GPL];  // column potentials of the columns this lane holds (same in every warp)
+#pragma unroll
+        for (int j = 0; j < GPL; ++j) {
+            const int col = j * 32 + lane;
+            gm[j] = (a.warm && col < nc) ? a.gL[(size_t)u * nc + col] : 0.f;
+        }
+        if (MODE != MODE_SWEEP && tid < ncx) s.gp[tid] = tid < nc ? a.gP[(size_t)u * nc + tid] : 0.f;
+        // the consumer's tile was staged one consumer ago; a bounded wait records a timeout
+        // instead of hanging (the CTA then continues on whatever data is there)
+        if (!mbar_wait(s.bar, phase, 1u << 26)) {
+            if (tid == 0) atomicOr(&a.st->err, 4);
+        }
+        phase ^= 1u;
+        __syncthreads();  // s.gp / s.e / s.ib / s.om / s.coef visible
+
+        if constexpr (MODE != MODE_SWEEP) {
+            // ---------------- gradient of F at the previous policy ------------------------------
+            // x_ik = 2^(g'_k - c'_ik - lse_i) is re-formed from the staged tile and the row
+            // log-normaliser lse_i of the first pass.
+            {
+                float acc[3][NCB];  // q, cs, X^T h partials
+#pragma unroll
+                for (int k = 0; k < NCB; ++k) acc[0][k] = acc[1][k] = acc[2][k] = 0.f;
+                for (int i = tid; i < I; i += T) {
+                    float x[NCB];
+                    float M = -INFINITY;
+#pragma unroll
+                    for (int k = 0; k < NCB; ++k) {
+                        x[k] = (EXACT || k < nc) ? s.gp[k] - s.C[k * lds + i] * sc : -INFINITY;
+                        M = fmaxf(M, x[k]);
+                    }
+                    float S = 0.f;
+#pragma unroll
+                    for (int k = 0; k < NCB; ++k) {
+                        x[k] = ex2(x[k] - M);
+                        S += x[k];
+                    }
+                    const float inv = rcp_approx(S);  // S in [1, m]: the row max contributes 1
+                    const float wr = om_at(i) * r_at(i);  // dF/dx_ik = wr_i e_k
+                    float hh = 0.f, vi = 0.f;
+#pragma unroll
+                    for (int k = 0; k < NCB; ++k) {
+                        x[k] *= inv;
+                        hh += x[k] * (wr * s.e[k]);
+                        if (MODE == MODE_GRAD && k < a.K) vi += s.e[k] * x[k];
+                    }
+#pragma unroll
+                    for (int k = 0; k < NCB; ++k) {
+                        acc[0][k] += x[k] * (wr * s.e[k]);
+                        acc[1][k] += x[k];
+                        acc[2][k] += x[k] * hh;
+                        if constexpr (!REG_GRAM) {
+                            if (EXACT || k < nc) s.X[k * ld + i] = x[k];
+                        }
+                    }
+                    s.lse[i] = M + lg2_approx(S);
+                    s.h[i] = hh;
+                    // dF/dr(u,i) = (dF/dImp_i) sum_{k<K} e_k x_ik (C does not depend on r)
+                    if (MODE == MODE_GRAD && a.dr) a.dr[(size_t)u * I + i] = om_at(i) * vi;
+                }
+                cta_reduce<NCB, 3>(acc, nc, s.red, s.out, ncp);  // s.out: [q | cs | X^T h]
+            }
+            // Gram block M[0:n,0:n] of diag(cs) - X^T X; rows of x sum to 1, so the diagonal is
+            // sum_i x_ik (1 - x_ik) without cancellation.
+            if constexpr (REG_GRAM) {
+                float* gout = s.out + 3 * ncp;
+                gram_block<NCB, EXACT>(s, nc, I, lds, sc, gout);
+                float* Af = reinterpret_cast<float*>(s.A);
+                float* rf = reinterpret_cast<float*>(s.rhs);
+                for (int idx = tid; idx < n * n; idx += T) {
+                    int k = idx / n, m = idx % n;
+                    if (k > m) { const int t = k; k = m; m = t; }
+                    Af[idx] = gout[k * (NCB - 1) - k * (k - 1) / 2 + (m - k)];
+                }
+                for (int k = tid; k < ncx; k += T) {
+                    if (k < n) rf[k] = s.out[k] - s.out[2 * ncp + k];
+                    s.beta[k] = 0.f;
+                }
+                __syncthreads();
+                if (warp == 0) warp_cholesky_solve_f32<NCB - 1>(Af, rf, n, s.Lt, s.beta, lane);
+                __syncthreads();
+            } else {
+                for (int pidx = warp; pidx < n * (n + 1) / 2; pidx += W) {
+                    int k = 0, rem = pidx;
+                    while (rem >= n - k) { rem -= n - k; ++k; }
+                    const int m = k + rem;
+                    const float* xk = s.X + k * ld;
+                    const float* xm = s.X + m * ld;
+                    float sum = 0.f;
+                    if (k == m) {
+                        for (int i = lane; i < I; i += 32) sum += xk[i] * (1.f - xk[i]);
+                    } else {
+                        for (int i = lane; i < I; i += 32) sum -= xk[i] * xm[i];
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
+                    if (lane == 0) {
+                        s.A[k * n + m] = (double)sum;
+                        s.A[m * n + k] = (double)sum;
+                    }
+                }
+                for (int k = tid; k < n; k += T)
+                    s.rhs[k] = (double)s.out[k] - (double)s.out[2 * ncp + k];
+                __syncthreads();
+                if (warp == 0) warp_cholesky_solve(s.A, s.rhs, n, lane);
+                __syncthreads();
+                for (int k = tid; k < ncx; k += T) s.beta[k] = k < n ? (float)s.rhs[k] : 0.f;
+                __syncthreads();
+            }
+            // alpha_i = h_i - sum_k x_ik beta_k
+            for (int i = tid; i < I; i += T) {
+                const float l = s.lse[i];
+                float sb = 0.f;
+#pragma unroll
+                for (int k = 0; k < NCB; ++k)
+                    if (EXACT || k < nc) sb += ex2(s.gp[k] - s.C[k * lds + i] * sc - l) * s.beta[k];
+                s.alpha[i] = s.h[i] - sb;
+            }
+            __syncthreads();
+            // gradient and Adam over the tile, four consecutive items per step (float4)
+            const float step_size = s.coef[0], inv_bc2s = 1.f / s.coef[1];
+            const int g4 = ld / 4;
+            float* __restrict__ Cg = a.C;
+            float* __restrict__ m1g = a.m1;
+            float* __restrict__ m2g = a.m2;
+            float gsq = 0.f;
+#pragma unroll 4
+            for (int q = tid; q < nc * g4; q += T) {
+                const int k = q / g4;
+                const int i = (q - k * g4) * 4;
+                if (i >= I) continue;
+                const int qs = k * (lds / 4) + i / 4;  // float4 index in the shared tile
+                const float4 c4 = reinterpret_cast<const float4*>(s.C)[qs];
+                const float4 l4 = reinterpret_cast<const float4*>(s.lse)[i / 4];
+                const float4 a4 = reinterpret_cast<const float4*>(s.alpha)[i / 4];
+                const float4 o4 = TS ? __ldg(reinterpret_cast<const float4*>(a.omega) + i / 4)
+                                     : reinterpret_cast<const float4*>(s.om)[i / 4];
+                const float4 r4 = TS ? __ldg(reinterpret_cast<const float4*>(r_u) + i / 4)
+                                     : reinterpret_cast<const float4*>(s.r)[i / 4];
+                const float gpk = s.gp[k], ek = s.e[k], bk = s.beta[k];
+                float cv[4] = {c4.x, c4.y, c4.z, c4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
+                float av[4] = {a4.x, a4.y, a4.z, a4.w};
+                float wv[4] = {o4.x * r4.x, o4.y * r4.y, o4.z * r4.z, o4.w * r4.w};
+                float gr[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const bool valid = i + j < I;
+                    const float x = valid ? ex2(gpk - cv[j] * sc - lv[j]) : 0.f;
+                    gr[j] = valid ? -a.inv_eps * x * (wv[j] * ek - av[j] - bk) : 0.f;
+                    gsq += gr[j] * gr[j];
+                }
+                if constexpr (MODE == MODE_GRAD) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (i + j < I) a.dC[((size_t)u * I + i + j) * nc + k] = gr[j];
+                } else {
+                    const size_t off = tile + (size_t)q * 4;
+                    if (a.optimizer == 1) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) cv[j] += a.lr * gr[j];
+                    } else {
+                        const float4 mm4 = *reinterpret_cast<const float4*>(m1g + off);
+                        const float4 vv4 = *reinterpret_cast<const float4*>(m2g + off);
+                        float mm[4] = {mm4.x, mm4.y, mm4.z, mm4.w};
+                        float vv[4] = {vv4.x, vv4.y, vv4.z, vv4.w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            mm[j] = a.beta1 * mm[j] + (1.f - a.beta1) * gr[j];
+                            vv[j] = a.beta2 * vv[j] + (1.f - a.beta2) * gr[j] * gr[j];
+                            // sqrt(v) / bc2s + eps with MUFU rsqrt / rcp (IEEE sqrt and division
+                            // are long instruction sequences on the per-cell path)
+                            const float sq = vv[j] > 0.f ? vv[j] * rsqrtf(vv[j]) : 0.f;
+                            cv[j] += __fdividef(step_size * mm[j], fmaf(sq, inv_bc2s, a.adam_eps));
+                        }
+                        *reinterpret_cast<float4*>(m1g + off) = make_float4(mm[0], mm[1], mm[2], mm[3]);
+                        *reinterpret_cast<float4*>(m2g + off) = make_float4(vv[0], vv[1], vv[2], vv[3]);
+                    }
+                    const float4 cn = make_float4(cv[0], cv[1], cv[2], cv[3]);
+                    *reinterpret_cast<float4*>(Cg + off) = cn;
+                    reinterpret_cast<float4*>(s.C)[qs] = cn;
+                }
+            }
+            gn2 += (double)gsq;
+            if constexpr (MODE == MODE_GRAD) {
+                __syncthreads();
+                if (tid == 0) stage_consumer(a, u + gridDim.x, nc, ld, s, false, TS);
+                continue;  // no solve in gradient mode
+            }
+            __syncthreads();  // updated tile visible
+        }
+
+        // ---------------- Sinkhorn solve on the consumer's (new) costs ----------------------------
+        if constexpr (TS != 0) {
+            tile_sweep<NCB, R, 2, TS, EXACT, MODE>(a, s, u, nc, gm, par);
+        } else {
+        float rr[R];
+        bool vr[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) rr[r] = 0.f;
+        if (any_row) ldv<R>(rr, s.r + i0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) vr[r] = i0 + r < I;
+        float c[R][NCB];
+        {
+            float gk[NCB];
+            bcast_g<NCB, GPL>(gm, gk);
+#pragma unroll
+            for (int k = 0; k < NCB; ++k) {
+                float tmp[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) tmp[r] = 0.f;
+                if ((EXACT || k < nc) && any_row) ldv<R>(tmp, s.C + k * lds + i0);
+#pragma unroll
+                for (int r = 0; r < R; ++r) c[r][k] = tmp[r];
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float M = 0.f;
+                if (vr[r]) {
+                    M = -INFINITY;
+#pragma unroll
+                    for (int k = 0; k < NCB; ++k)
+                        if (EXACT || k < nc) M = fmaxf(M, gk[k] - c[r][k] * sc);
+                }
+#pragma unroll
+                for (int k = 0; k < NCB; ++k)
+                    c[r][k] = (vr[r] && (EXACT || k < nc)) ? c[r][k] * sc + M : INFINITY;
+            }
+        }
+        if constexpr (PAIR) {
+            constexpr int RP = R / 2;
+            f2 c2[RP][NCB];
+#pragma unroll
+            for (int rp = 0; rp < RP; ++rp)
+#pragma unroll
+                for (int k = 0; k < NCB; ++k) c2[rp][k] = pk(c[2 * rp][k], c[2 * rp + 1][k]);
+            for (int l = 0; l < a.L; ++l) {
+                const bool last = l == a.L - 1;
+                if (last && warp == 0) {
+#pragma unroll
+                    for (int j = 0; j < GPL; ++j)
+                        if (j * 32 + lane < nc) a.gP[(size_t)u * nc + j * 32 + lane] = gm[j];
+                }
+                f2 g2[NCB];
+                {
+                    float gk[NCB];
+                    bcast_g<NCB, GPL>(gm, gk);
+#pragma unroll
+                    for (int k = 0; k < NCB; ++k) g2[k] = pk(gk[k], gk[k]);
+                }
+                f2 cs2[NCB];
+#pragma unroll
+                for (int k = 0; k < NCB; ++k) cs2[k] = 0ull;
+#pragma unroll
+                for (int rp = 0; rp < RP; ++rp) {
+                    const bool v0 = vr[2 * rp], v1 = vr[2 * rp + 1];
+                    f2 p2[NCB];
+                    f2 S2 = 0ull;
+#pragma unroll
+                    for (int k = 0; k < NCB; ++k) {
+                        float d0, d1;
+                        upk(sub2(g2[k], c2[rp][k]), d0, d1);
+                        p2[k] = pk(ex2(d0), ex2(d1));
+                        S2 = add2(S2, p2[k]);
+                    }
+                    float S0, S1;
+                    upk(S2, S0, S1);
+                    const bool bad0 = v0 && !(S0 >= 0x1p-64f && S0 <= 0x1p64f);
+                    const bool bad1 = v1 && !(S1 >= 0x1p-64f && S1 <= 0x1p64f);
+                    if (bad0 || bad1) {  // re-shift the pair's rows exactly
+                        float M0 = -INFINITY, M1 = -INFINITY;
+#pragma unroll
+                        for (int k = 0; k < NCB; ++k) {
+                            if (EXACT || k < nc) {
+                                float gkk, gdup, c0, c1;
+                                upk(g2[k], gkk, gdup);
+                                upk(c2[rp][k], c0, c1);
+                                M0 = fmaxf(M0, gkk - c0);
+                                M1 = fmaxf(M1, gkk - c1);
+                            }
+                        }
+                        const f2 M2 = pk(bad0 ? M0 : 0.f, bad1 ? M1 : 0.f);
+                        S2 = 0ull;
+#pragma unroll
+                        for (int k = 0; k < NCB; ++k) {
+                            if (EXACT || k < nc) c2[rp][k] = add2(c2[rp][k], M2);
+                            float d0, d1;
+                            upk(sub2(g2[k], c2[rp][k]), d0, d1);
+                            p2[k] = pk(ex2(d0), ex2(d1));
+                            S2 = add2(S2, p2[k]);
+                        }
+                        upk(S2, S0, S1);
+                    }
+                    const float inv0 = v0 ? rcp_approx(S0) : 0.f;
+                    const float inv1 = v1 ? rcp_approx(S1) : 0.f;
+                    const f2 inv2 = pk(inv0, inv1);
+#pragma unroll
+                    for (int k = 0; k < NCB; ++k) cs2[k] = fma2(p2[k], inv2, cs2[k]);
+                    if (last) {
+                        float w0 = 0.f, w1 = 0.f;
+#pragma unroll
+                        for (int k = 0; k < NCB; ++k) {
+                            if (k < a.K) {
+                                float p0, p1;
+                                upk(p2[k], p0, p1);
+                                w0 += s.e[k] * p0;
+                                w1 += s.e[k] * p1;
+                            }
+                        }
+                        acc_imp[2 * rp] += rr[2 * rp] * (w0 * inv0);
+                        acc_imp[2 * rp + 1] += rr[2 * rp + 1] * (w1 * inv1);
+                    }
+                }
+                float cs[NCB];
+#pragma unroll
+                for (int k = 0; k < NCB; ++k) {
+                    float lo, hi;
+                    upk(cs2[k], lo, hi);
+                    cs[k] = lo + hi;
+                }
+                column_update<NCB, GPL>(cs, gm, nc, s.red, s.ib, par, lane, warp, W);
+                par ^= 1;
+                if (l == 0 && tid == 0)
+                    stage_consumer(a, u + gridDim.x, nc, ld, s, MODE == MODE_UPDATE_SWEEP && a.optimizer == 0, false);
+            }
+        } else {
+            for (int l = 0; l < a.L; ++l) {
+                const bool last = l == a.L - 1;
+                if (last && warp == 0) {
+#pragma unroll
+                    for (int j = 0; j < GPL; ++j)
+                        if (j * 32 + lane < nc) a.gP[(size_t)u * nc + j * 32 + lane] = gm[j];
+                }
+                float gk[NCB];
+                bcast_g<NCB, GPL>(gm, gk);
+                float cs[NCB];
+#pragma unroll
+                for (int k = 0; k < NCB; ++k) cs[k] = 0.f;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (!vr[r]) continue;
+                    float p[NCB];
+                    float S = 0.f;
+#pragma unroll
+                    for (int k = 0; k < NCB; ++k) {
+                        p[k] = ex2(gk[k] - c[r][k]);
+                        S += p[k];
+                    }
+                    if (!(S >= 0x1p-64f && S <= 0x1p64f)) {
+                        float M = -INFINITY;
+#pragma unroll
+                        for (int k = 0; k < NCB; ++k)
+                            if (EXACT || k < nc) M = fmaxf(M, gk[k] - c[r][k]);
+                        S = 0.f;
+#pragma unroll
+                        for (int k = 0; k < NCB; ++k) {
+                            if (EXACT || k < nc) c[r][k] += M;
+                            p[k] = ex2(gk[k] - c[r][k]);
+                            S += p[k];
+                        }
+                    }
+                    const float inv = rcp_approx(S);
+#pragma unroll
+                    for (int k = 0; k < NCB; ++k) cs[k] += p[k] * inv;
+                    if (last) {
+                        float v = 0.f;
+#pragma unroll
+                        for (int k = 0; k < NCB; ++k)
+                            if (k < a.K) v += s.e[k] * p[k];
+                        acc_imp[r] += rr[r] * (v * inv);
+                    }
+                }
+                column_update<NCB, GPL>(cs, gm, nc, s.red, s.ib, par, lane, warp, W);
+                par ^= 1;
+                if (l == 0 && tid == 0)
+                    stage_consumer(a, u + gridDim.x, nc, ld, s, MODE == MODE_UPDATE_SWEEP && a.optimizer == 0, false);
+            }
+        }
+        }  // register sweep
+        if (warp == 0) {
+#pragma unroll
+            for (int j = 0; j < GPL; ++j)
+                if (j * 32 + lane < nc) a.gL[(size_t)u * nc + j * 32 + lane] = gm[j];
+        }
+        // tile sweep: the last column update ended with a barrier after every read of the tile, so
+        // the next consumer's tile can be staged now (its L2 prefetch was issued during the solve)
+        if (TS && tid == 0) stage_consumer(a, u + gridDim.x, nc, ld, s, false, TS);
+    }
+
+    if constexpr (MODE != MODE_GRAD) {
+        if constexpr (TS == 0) {  // (the tile sweep accumulates into part as it goes)
+            if (i0 < ld) stv<R>(a.part + (size_t)blockIdx.x * ld + i0, acc_imp);
+        }
+    }
+    if constexpr (MODE == MODE_UPDATE_SWEEP) {
+        // CTA sum of the squared gradient in double, fixed order
+        __syncthreads();
+        double* s_d = reinterpret_cast<double*>(s.red);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gn2 += __shfl_xor_sync(FULL, gn2, o);
+        if (lane == 0) s_d[warp] = gn2;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int w = 0; w < W; ++w) t += s_d[w];
+            a.gn2_part[blockIdx.x] = t;
+        }
+    }
+}
+
+// TS: 0 register sweep, else the tile sweep with that shared column stride (floats)
+template <int NCB, int R, bool EXACT, int TS = 0>
+P1Variant make_variant(int threads) {
+    P1Variant v;
+    v.ncb = NCB;
+    v.rows = R;
+    v.exact = EXACT;
+    v.threads = threads;
+    v.smem = 0;
+    v.tile_stride = TS;
+    v.fn[MODE_SWEEP] = (const void*)p1_kernel<NCB, R, EXACT, MODE_SWEEP, TS>;
+    v.fn[MODE_UPDATE_SWEEP] = (const void*)p1_kernel<NCB, R, EXACT, MODE_UPDATE_SWEEP, TS>;
+    v.fn[MODE_GRAD] = (const void*)p1_kernel<NCB, R, EXACT, MODE_GRAD, TS>;
+    return v;
+}
+
+}  // namespace
+
+}  // namespace fr

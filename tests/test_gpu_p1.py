@@ -42,7 +42,11 @@ def test_initial_sweep_is_the_uniform_policy():
     (3, 129, 10, 0.7, 20, 1),     # several warps per consumer, eps != 1
     (5, 11, 10, 1.0, 30, 0),      # dummy mass 1, cold start
     (2, 300, 3, 1.3, 1, 1),       # generic column bucket, L = 1
-    (4, 64, 20, 1.0, 40, 1),      # generic 32-column bucket
+    (3, 64, 25, 1.0, 30, 1),      # generic 32-column bucket
+    (4, 64, 20, 1.0, 40, 1),      # 21 columns (tile sweep, 512-float stride), one warp
+    (4, 300, 20, 1.0, 30, 1),     # 21 columns, 512-float stride, several warps
+    (3, 900, 20, 0.8, 20, 1),     # 21 columns, 1024-float stride, eps != 1
+    (2, 1999, 20, 1.0, 10, 1),    # 21 columns, 2048-float stride, ragged item count
 ])
 def test_one_step_from_seeded_state(U, I, K, eps, L, warm):
     r = synth.relevance_lowrank(U, I, seed=U + I)
@@ -216,6 +220,7 @@ def _rows_leaving_range(C, b, eps, L):
     (40, 10, 5.0),    # register sweep, 11 columns
     (40, 5, 5.0),     # register sweep, 8-column bucket
     (1030, 10, 1.5),  # tile sweep (more than 1024 items, 11 columns)
+    (300, 20, 2.0),   # tile sweep, 21 columns
 ])
 def test_rows_leaving_the_exponent_range_are_reshifted(I, K, scale):
     """eps = 0.1 and N(0, scale^2) costs from a cold start: potentials drift far enough during the
@@ -247,13 +252,16 @@ def test_rows_leaving_the_exponent_range_are_reshifted(I, K, scale):
     np.testing.assert_allclose(g.policy(), o.policy(), atol=max(X_ATOL, tol))
 
 
-@pytest.mark.parametrize("I", [1001, 1201])  # register sweep, tile sweep
-def test_several_consumers_per_cta_ragged_items(I):
-    """1300 consumers, K = 10, a ragged item count (padding rows up to the next multiple of 8 in
-    every tile): more consumers than resident CTAs, so each CTA stages and solves several in turn
-    and accumulates their impacts; whole-market F and impacts after the solve and after two ascent
-    steps, and the policies of consumers solved after the first by their CTA."""
-    U, K = 1300, 10
+@pytest.mark.parametrize("U,I,K", [
+    (1300, 1001, 10),  # register sweep
+    (1300, 1201, 10),  # tile sweep
+    (400, 1999, 20),   # tile sweep, 21 columns (one CTA per SM)
+])
+def test_several_consumers_per_cta_ragged_items(U, I, K):
+    """A ragged item count (padding rows up to the next multiple of 8 in every tile) and more
+    consumers than resident CTAs, so each CTA stages and solves several in turn and accumulates
+    their impacts: whole-market F, impacts and gradient after the solve, F over two ascent steps,
+    and the policies of consumers solved after the first by their CTA."""
     r = synth.relevance_lowrank(U, I, seed=8)
     g, o = pair(U, I, K, r)
     C, m1, m2, gg = seeded_state(U, I, K, seed=31, scale=0.5)
@@ -269,5 +277,32 @@ def test_several_consumers_per_cta_ragged_items(I):
     Fg = g.step(2)
     Fo, _ = o.step(2)
     np.testing.assert_allclose(Fg, Fo, rtol=NSW_RTOL)
-    for u in (3, 700, 1299):
+    for u in (3, U // 2 + 1, U - 1):
         np.testing.assert_allclose(g.policy(u, 1)[0], o.policy(u, 1)[0], atol=X_ATOL)
+
+
+def test_differentiation_size_free_costs_sampled_parity():
+    """|U| = 20000, |I| = 2000, K = 20 (21 columns), L = 100 under free costs (the tile sweep at a
+    2048-float stride, one CTA per SM, about 130 consumers per CTA; C and the Adam moments 3.4 GB
+    each): at a seeded state (C ~ N(0, 0.25), zero moments and potentials) the policies of sampled
+    consumers against the oracle's Sinkhorn on their cost tiles, rows summing to one, and one
+    ascent step raising F. (The full market is too large for the FP64 oracle in a test.)"""
+    U, I, K, L = 20000, 2000, 20, 100
+    e = synth.dcg_exposure(K)
+    g = fr.FairRank(U, I, K, sinkhorn_iters=L)
+    g.set_relevance(synth.relevance_lowrank_fast(U, I, seed=7))
+    g.set_exposure(e)
+    m = oracle.num_cols(I, K)
+    C = (np.random.default_rng(41).standard_normal((U, I, m), dtype=np.float32) * 0.5)
+    zeros = np.zeros((U, I, m), np.float32)
+    g.set_state(C, zeros, zeros, np.zeros((U, m), np.float32), t=0)
+    imp, _, F0 = g.impacts()
+    assert np.isfinite(F0) and np.all(imp > 0)
+    b, _ = oracle.marginals(I, K, e)
+    for u in (0, 1, 9876, 19999):
+        X = g.policy(u, 1)[0]
+        xo, _, _ = oracle.sinkhorn(C[u].astype(np.float64), b, 1.0, L, np.zeros(m))
+        np.testing.assert_allclose(X, xo, atol=X_ATOL)
+        np.testing.assert_allclose(X.sum(1), 1.0, atol=1e-5)
+    F = g.step(1)
+    assert F[0] > F0
