@@ -685,67 +685,69 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
                 s.alpha[i] = s.h[i] - sb;
             }
             __syncthreads();
-            // gradient and Adam over the tile, four consecutive items per step (float4)
+            // gradient and Adam over the tile: each thread takes four consecutive items (float4)
+            // and runs through the columns, so the per-item values (lse, alpha, omega r) are read
+            // once per four items and eleven columns, and no index needs a division
             const float step_size = s.coef[0], inv_bc2s = 1.f / s.coef[1];
-            const int g4 = ld / 4;
             float* __restrict__ Cg = a.C;
             float* __restrict__ m1g = a.m1;
             float* __restrict__ m2g = a.m2;
             float gsq = 0.f;
+            for (int i4 = tid; i4 * 4 < I; i4 += T) {
+                const int i = i4 * 4;
+                const float4 l4 = reinterpret_cast<const float4*>(s.lse)[i4];
+                const float4 a4 = reinterpret_cast<const float4*>(s.alpha)[i4];
+                const float4 o4 = TS ? __ldg(reinterpret_cast<const float4*>(a.omega) + i4)
+                                     : reinterpret_cast<const float4*>(s.om)[i4];
+                const float4 r4 = TS ? __ldg(reinterpret_cast<const float4*>(r_u) + i4)
+                                     : reinterpret_cast<const float4*>(s.r)[i4];
+                const float lv[4] = {l4.x, l4.y, l4.z, l4.w}, av[4] = {a4.x, a4.y, a4.z, a4.w};
+                const float wv[4] = {o4.x * r4.x, o4.y * r4.y, o4.z * r4.z, o4.w * r4.w};
 #pragma unroll 4
-            for (int q = tid; q < nc * g4; q += T) {
-                const int k = q / g4;
-                const int i = (q - k * g4) * 4;
-                if (i >= I) continue;
-                const int qs = k * (lds / 4) + i / 4;  // float4 index in the shared tile
-                const float4 c4 = reinterpret_cast<const float4*>(s.C)[qs];
-                const float4 l4 = reinterpret_cast<const float4*>(s.lse)[i / 4];
-                const float4 a4 = reinterpret_cast<const float4*>(s.alpha)[i / 4];
-                const float4 o4 = TS ? __ldg(reinterpret_cast<const float4*>(a.omega) + i / 4)
-                                     : reinterpret_cast<const float4*>(s.om)[i / 4];
-                const float4 r4 = TS ? __ldg(reinterpret_cast<const float4*>(r_u) + i / 4)
-                                     : reinterpret_cast<const float4*>(s.r)[i / 4];
-                const float gpk = s.gp[k], ek = s.e[k], bk = s.beta[k];
-                float cv[4] = {c4.x, c4.y, c4.z, c4.w}, lv[4] = {l4.x, l4.y, l4.z, l4.w};
-                float av[4] = {a4.x, a4.y, a4.z, a4.w};
-                float wv[4] = {o4.x * r4.x, o4.y * r4.y, o4.z * r4.z, o4.w * r4.w};
-                float gr[4];
+                for (int k = 0; k < NCB; ++k) {
+                    if (!EXACT && k >= nc) break;
+                    const int qs = k * (lds / 4) + i4;  // float4 index in the shared tile
+                    const float4 c4 = reinterpret_cast<const float4*>(s.C)[qs];
+                    const float gpk = s.gp[k], ek = s.e[k], bk = s.beta[k];
+                    float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+                    float gr[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const bool valid = i + j < I;
-                    const float x = valid ? ex2(gpk - cv[j] * sc - lv[j]) : 0.f;
-                    gr[j] = valid ? -a.inv_eps * x * (wv[j] * ek - av[j] - bk) : 0.f;
-                    gsq += gr[j] * gr[j];
-                }
-                if constexpr (MODE == MODE_GRAD) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (i + j < I) a.dC[((size_t)u * I + i + j) * nc + k] = gr[j];
-                } else {
-                    const size_t off = tile + (size_t)q * 4;
-                    if (a.optimizer == 1) {
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) cv[j] += a.lr * gr[j];
-                    } else {
-                        const float4 mm4 = *reinterpret_cast<const float4*>(m1g + off);
-                        const float4 vv4 = *reinterpret_cast<const float4*>(m2g + off);
-                        float mm[4] = {mm4.x, mm4.y, mm4.z, mm4.w};
-                        float vv[4] = {vv4.x, vv4.y, vv4.z, vv4.w};
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            mm[j] = a.beta1 * mm[j] + (1.f - a.beta1) * gr[j];
-                            vv[j] = a.beta2 * vv[j] + (1.f - a.beta2) * gr[j] * gr[j];
-                            // sqrt(v) / bc2s + eps with MUFU rsqrt / rcp (IEEE sqrt and division
-                            // are long instruction sequences on the per-cell path)
-                            const float sq = vv[j] > 0.f ? vv[j] * rsqrtf(vv[j]) : 0.f;
-                            cv[j] += __fdividef(step_size * mm[j], fmaf(sq, inv_bc2s, a.adam_eps));
-                        }
-                        *reinterpret_cast<float4*>(m1g + off) = make_float4(mm[0], mm[1], mm[2], mm[3]);
-                        *reinterpret_cast<float4*>(m2g + off) = make_float4(vv[0], vv[1], vv[2], vv[3]);
+                    for (int j = 0; j < 4; ++j) {
+                        const bool valid = i + j < I;
+                        const float x = valid ? ex2(gpk - cv[j] * sc - lv[j]) : 0.f;
+                        gr[j] = valid ? -a.inv_eps * x * (wv[j] * ek - av[j] - bk) : 0.f;
+                        gsq += gr[j] * gr[j];
                     }
-                    const float4 cn = make_float4(cv[0], cv[1], cv[2], cv[3]);
-                    *reinterpret_cast<float4*>(Cg + off) = cn;
-                    reinterpret_cast<float4*>(s.C)[qs] = cn;
+                    if constexpr (MODE == MODE_GRAD) {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (i + j < I) a.dC[((size_t)u * I + i + j) * nc + k] = gr[j];
+                    } else {
+                        const size_t off = tile + (size_t)k * ld + i;
+                        if (a.optimizer == 1) {
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) cv[j] += a.lr * gr[j];
+                        } else {
+                            const float4 mm4 = *reinterpret_cast<const float4*>(m1g + off);
+                            const float4 vv4 = *reinterpret_cast<const float4*>(m2g + off);
+                            float mm[4] = {mm4.x, mm4.y, mm4.z, mm4.w};
+                            float vv[4] = {vv4.x, vv4.y, vv4.z, vv4.w};
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                mm[j] = a.beta1 * mm[j] + (1.f - a.beta1) * gr[j];
+                                vv[j] = a.beta2 * vv[j] + (1.f - a.beta2) * gr[j] * gr[j];
+                                // sqrt(v) / bc2s + eps with MUFU rsqrt / rcp (IEEE sqrt and
+                                // division are long instruction sequences on the per-cell path)
+                                const float sq = vv[j] > 0.f ? vv[j] * rsqrtf(vv[j]) : 0.f;
+                                cv[j] += __fdividef(step_size * mm[j], fmaf(sq, inv_bc2s, a.adam_eps));
+                            }
+                            *reinterpret_cast<float4*>(m1g + off) = make_float4(mm[0], mm[1], mm[2], mm[3]);
+                            *reinterpret_cast<float4*>(m2g + off) = make_float4(vv[0], vv[1], vv[2], vv[3]);
+                        }
+                        const float4 cn = make_float4(cv[0], cv[1], cv[2], cv[3]);
+                        *reinterpret_cast<float4*>(Cg + off) = cn;
+                        reinterpret_cast<float4*>(s.C)[qs] = cn;
+                    }
                 }
             }
             gn2 += (double)gsq;
