@@ -30,6 +30,14 @@ __device__ __forceinline__ float lg2_approx(float x) {
 
 constexpr int pow2ceil(int n) { return n <= 1 ? 1 : 2 * pow2ceil((n + 1) / 2); }
 
+// Adam's bias correction 1 - beta^t (beta in [0.5, 1), t >= 1) in FP32 without cancellation, as
+// -expm1(t log1p(beta - 1)): beta - 1 is exact, and the result keeps a few-ulp relative accuracy
+// where 1 - powf(beta, t) would lose log2(1 / (1 - beta)) bits. (The double-precision pow it
+// replaces is a long sequence on the FP64 pipe, and one thread's evaluation held its CTA.)
+__device__ __forceinline__ float one_minus_pow(float beta, float t) {
+    return -expm1f(t * log1pf(beta - 1.f));
+}
+
 // ---- bulk (TMA) copies and mbarriers --------------------------------------------------------
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return (unsigned)__cvta_generic_to_shared(p);

@@ -536,11 +536,9 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
         // Adam bias corrections for this step (t counts applied steps before this one)
         float step_size = a.lr, bc2s = 1.f;
         if (MODE == MODE_UPDATE_SWEEP && a.optimizer == 0) {
-            const double t1 = (double)(a.st->t + 1);
-            const double bc1 = 1.0 - pow((double)a.beta1, t1);
-            const double bc2 = 1.0 - pow((double)a.beta2, t1);
-            step_size = (float)((double)a.lr / bc1);
-            bc2s = (float)sqrt(bc2);
+            const float t1 = (float)(a.st->t + 1);
+            step_size = a.lr / one_minus_pow(a.beta1, t1);
+            bc2s = sqrtf(one_minus_pow(a.beta2, t1));
         }
         s.coef[0] = step_size;
         s.coef[1] = bc2s;
@@ -573,12 +571,19 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
             gm[j] = (a.warm && col < nc) ? a.gL[(size_t)u * nc + col] : 0.f;
         }
         if (MODE != MODE_SWEEP && tid < ncx) s.gp[tid] = tid < nc ? a.gP[(size_t)u * nc + tid] : 0.f;
-        // the consumer's tile was staged one consumer ago; a bounded wait records a timeout
-        // instead of hanging (the CTA then continues on whatever data is there)
-        if (!mbar_wait(s.bar, phase, 1u << 26)) {
-            if (tid == 0) atomicOr(&a.st->err, 4);
-        }
-        phase ^= 1u;
+        // the consumer's tile was staged one consumer ago (the register sweep) or right after the
+        // previous solve (the tile sweep); a bounded wait records a timeout instead of hanging (the
+        // CTA then continues on whatever data is there). In the tile sweep's update modes the
+        // first gradient pass reads the costs from global memory (L2, where the previous solve
+        // prefetched them) while the copy lands, and the wait follows that pass.
+        constexpr bool LATE_WAIT = TS != 0 && MODE != MODE_SWEEP;
+        auto wait_tile = [&]() {
+            if (!mbar_wait(s.bar, phase, 1u << 26)) {
+                if (tid == 0) atomicOr(&a.st->err, 4);
+            }
+            phase ^= 1u;
+        };
+        if constexpr (!LATE_WAIT) wait_tile();
         __syncthreads();  // s.gp / s.e / s.ib / s.om / s.coef visible
 
         if constexpr (MODE != MODE_SWEEP) {
@@ -594,7 +599,10 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
                     float M = -INFINITY;
 #pragma unroll
                     for (int k = 0; k < NCB; ++k) {
-                        x[k] = (EXACT || k < nc) ? s.gp[k] - s.C[k * lds + i] * sc : -INFINITY;
+                        float c = 0.f;
+                        if (EXACT || k < nc)
+                            c = LATE_WAIT ? __ldcg(a.C + tile + (size_t)k * ld + i) : s.C[k * lds + i];
+                        x[k] = (EXACT || k < nc) ? s.gp[k] - c * sc : -INFINITY;
                         M = fmaxf(M, x[k]);
                     }
                     float S = 0.f;
@@ -628,6 +636,7 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
                 }
                 cta_reduce<NCB, 3>(acc, nc, s.red, s.out, ncp);  // s.out: [q | cs | X^T h]
             }
+            if constexpr (LATE_WAIT) wait_tile();  // the shared tile from here on
             // Gram block M[0:n,0:n] of diag(cs) - X^T X; rows of x sum to 1, so the diagonal is
             // sum_i x_ik (1 - x_ik) without cancellation.
             if constexpr (REG_GRAM) {

@@ -39,9 +39,9 @@ __device__ __forceinline__ void adam_body(const P2AdamArgs& a, int bid, int nb) 
                 if (a.optimizer == 1) {
                     th += a.lr * gr;
                 } else {
-                    const double t1 = (double)(a.st->t + 1);
-                    const float step = (float)((double)a.lr / (1.0 - pow((double)a.beta1, t1)));
-                    const float bc2s = (float)sqrt(1.0 - pow((double)a.beta2, t1));
+                    const float t1 = (float)(a.st->t + 1);
+                    const float step = a.lr / one_minus_pow(a.beta1, t1);
+                    const float bc2s = sqrtf(one_minus_pow(a.beta2, t1));
                     float m = a.m1[item], v = a.m2[item];
                     m = a.beta1 * m + (1.f - a.beta1) * gr;
                     v = a.beta2 * v + (1.f - a.beta2) * gr * gr;
