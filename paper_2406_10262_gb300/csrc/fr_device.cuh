@@ -355,6 +355,24 @@ __device__ __forceinline__ void bcast_g(const float (&gm)[GPL], float (&gk)[NCB]
     for (int k = 0; k < NCB; ++k) gk[k] = __shfl_sync(FULL, gm[k / 32], k % 32);
 }
 
+// log2(y) for y > 0, with a short path near 1, where the column updates of a converging Sinkhorn
+// solve spend almost all their calls: for |y - 1| < 2^-5, t = y - 1 is exact and log2(1 + t) is
+// the Taylor series of ln(1 + t) / ln 2 through t^6 in Horner form (truncation below 2^-30
+// relative), a few dependent FMAs on the iteration's critical path; elsewhere log2f.
+__device__ __forceinline__ float log2_near1(float y) {
+    const float t = y - 1.f;
+    if (fabsf(t) < 0x1p-5f) {
+        constexpr float c1 = 1.4426950408889634f;    //  1 / ln 2
+        constexpr float c2 = -0.7213475204444817f;   // -1 / (2 ln 2)
+        constexpr float c3 = 0.48089834696298783f;   //  1 / (3 ln 2)
+        constexpr float c4 = -0.36067376022224085f;  // -1 / (4 ln 2)
+        constexpr float c5 = 0.28853900817779266f;   //  1 / (5 ln 2)
+        constexpr float c6 = -0.24044917348149392f;  // -1 / (6 ln 2)
+        return t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, fmaf(t, c6, c5), c4), c3), c2), c1);
+    }
+    return log2f(y);
+}
+
 // Column update after the row sums: warp reduce-scatter of cs, one barrier, then every warp sums
 // the per-warp partials of its lanes' columns and updates its copy of g'.
 template <int NCB, int GPL>
@@ -384,7 +402,7 @@ __device__ __forceinline__ void column_update(float (&cs)[NCB], float (&gm)[GPL]
             // log2 b - log2 cs = -log2(cs / b): the argument is near 1, so the log2 and the one
             // rounding of cs / b are accurate to ~1e-7 absolute (two logs of ~log2 |I| each would
             // carry ~5e-7 of rounding into every iteration's potentials)
-            gm[j] -= log2f(fmaxf(sum * s_ib[col], 1e-37f));
+            gm[j] -= log2_near1(fmaxf(sum * s_ib[col], 1e-37f));
         }
     }
 }

@@ -494,11 +494,12 @@ __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u
         }
         column_update<NCB, GPL>(cs, gm, nc, s.red, s.ib, par, lane, warp, W);
         par ^= 1;
-        // the next consumer's data into L2 eight iterations before the end of this solve: early
-        // enough to hide the HBM latency, late enough that four CTAs per SM prefetching at once
-        // do not evict it again before the copy after the solve
+        // the next consumer's tile and relevance row into L2 eight iterations before the end of
+        // this solve: early enough to hide the HBM latency, late enough that four CTAs per SM
+        // prefetching at once do not evict them again before the copy after the solve (its Adam
+        // moments follow at the start of its gradient step, closer to their use)
         if (l == (a.L > 8 ? a.L - 8 : 0) && tid == 0)
-            prefetch_consumer(a, u + gridDim.x, nc, ld, MODE == MODE_UPDATE_SWEEP && a.optimizer == 0);
+            prefetch_consumer(a, u + gridDim.x, nc, ld, false);
     }
 }
 
@@ -587,6 +588,12 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
         __syncthreads();  // s.gp / s.e / s.ib / s.om / s.coef visible
 
         if constexpr (MODE != MODE_SWEEP) {
+            if (TS && MODE == MODE_UPDATE_SWEEP && a.optimizer == 0 && tid == 0) {
+                // the consumer's Adam moments into L2 while the gradient passes run
+                const unsigned tb = (unsigned)(sizeof(float) * (size_t)nc * ld);
+                bulk_prefetch_l2(a.m1 + tile, tb);
+                bulk_prefetch_l2(a.m2 + tile, tb);
+            }
             // ---------------- gradient of F at the previous policy ------------------------------
             // x_ik = 2^(g'_k - c'_ik - lse_i) is re-formed from the staged tile and the row
             // log-normaliser lse_i of the first pass.
