@@ -44,9 +44,14 @@ SMS_NOMINAL, SM_MAX_MHZ = 152, 2070.0
 # ex2 results per clock per SM assumed for the nominal MUFU peak (a doubled special-function rate
 # on Blackwell Ultra); the microbenchmark below measures the real rate on the box.
 EX2_PER_CLK_SM = 32
-# the fused free-cost kernel the library selects for 1000 items x 11 columns: eight rows per
-# thread, costs read from the resident shared tile at a 1024-float column stride
-P1_KERNEL = "p1_kernel<11,8,exact,update+sweep,tile1024>"
+
+
+def p1_kernel_name(g):
+    """Name of the fused free-cost kernel serving FairRank context g (its compiled variant)."""
+    v = g.kernel_variant()
+    tile = f",tile{v['tile_stride']}" if v["tile_stride"] else ""
+    return (f"p1_kernel<{v['n_cols_kernel']},{v['rows_per_thread']},"
+            f"{'exact' if v['exact'] else 'padded'},update+sweep{tile}>")
 
 
 def parse():
@@ -321,8 +326,8 @@ def run_ours(args, w):
     bytes_alg = cells * 4 * 6 + U * I * 4  # read C, m, v + write C, m, v; read r
     roof = {"bound": "alu", "unit": "Gex2/s", "achieved": achieved / 1e9, "peak": peak_nominal / 1e9,
             "frac": achieved / peak_nominal,
-            "traffic": recorded_traffic(P1_KERNEL),
-            "kernel": P1_KERNEL, "kernel_ms": kms[0], "reduce_ms": kms[1],
+            "traffic": recorded_traffic(p1_kernel_name(g)),
+            "kernel": p1_kernel_name(g), "kernel_ms": kms[0], "reduce_ms": kms[1],
             "sweep_only_ms": kms[2], "sweep_only_frac": ex2_alg / (kms[2] * 1e-3) / peak_nominal,
             "ex2_per_launch": ex2_alg, "peak_source": f"nominal {SMS_NOMINAL} SMs x {EX2_PER_CLK_SM} "
             f"ex2/clk x {SM_MAX_MHZ:.0f} MHz", "ex2_microbench": ex2_measured / 1e9,

@@ -233,6 +233,13 @@ FR_API int64_t fr_launch_count(const fr_ctx* ctx);
    the optimiser state like fr_step. */
 FR_API fr_status fr_time_kernels(fr_ctx* ctx, int32_t n_steps, double* ms);
 
+/* The compiled kernel variant that serves ctx's Sinkhorn sweep (diagnostics, e.g. to name the
+   kernel a profile refers to): out[0] column bucket, out[1] rows per thread, out[2] 1 if compiled
+   for exactly n_cols columns, out[3] CTA size, out[4] shared-tile column stride in floats of the
+   free-cost tile sweep (0: costs held in registers; always 0 for FR_PARAM_ITEM), out[5] persistent
+   grid size. FR_EINVAL if ctx or out is NULL. */
+FR_API fr_status fr_kernel_variant(const fr_ctx* ctx, int32_t* out);
+
 /* Measures the sustained rate of ex2.approx.f32 on the current device with a dependent-chain-free
    microbenchmark (grid = SMs x 4 CTAs): writes exp2 evaluations per second. Used as the measured
    denominator of the Sinkhorn roofline. */

@@ -1016,6 +1016,20 @@ const char* fr_last_error(const fr_ctx* ctx) {
 
 int64_t fr_launch_count(const fr_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+fr_status fr_kernel_variant(const fr_ctx* ctx, int32_t* out) {
+    if (!ctx || !out) return fail(nullptr, FR_EINVAL, "ctx or out is NULL");
+    if (ctx->p2) {
+        const P2Variant& v = ctx->var2;
+        const int32_t o[6] = {v.ncb, v.rows, v.exact, v.threads, 0, ctx->G};
+        for (int j = 0; j < 6; ++j) out[j] = o[j];
+    } else {
+        const P1Variant& v = ctx->var;
+        const int32_t o[6] = {v.ncb, v.rows, v.exact, v.threads, v.tile_stride, ctx->G};
+        for (int j = 0; j < 6; ++j) out[j] = o[j];
+    }
+    return FR_OK;
+}
+
 fr_status fr_measure_ex2_rate(double* ex2_per_second) {
     fr_ctx* ctx = nullptr;
     if (!ex2_per_second) return fail(nullptr, FR_EINVAL, "output is NULL");

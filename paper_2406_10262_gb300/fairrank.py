@@ -74,6 +74,7 @@ def lib():
             "fr_launch_count": (i64, [_vp]),
             "fr_measure_ex2_rate": (i32, [_dp]),
             "fr_time_kernels": (i32, [_vp, i32, _dp]),
+            "fr_kernel_variant": (i32, [_vp, ct.POINTER(i32)]),
             "fr_batch_create": (i32, [ct.POINTER(Config), i32, _vp, ct.POINTER(_vp)]),
             "fr_batch_destroy": (i32, [_vp]),
             "fr_batch_reset": (i32, [_vp]),
@@ -276,6 +277,13 @@ class FairRank:
 
     def launch_count(self) -> int:
         return lib().fr_launch_count(self.h)
+
+    def kernel_variant(self) -> dict:
+        """The compiled Sinkhorn-sweep variant serving this context (see fr_kernel_variant)."""
+        o = (ct.c_int32 * 6)()
+        self._check(lib().fr_kernel_variant(self.h, o))
+        return {"n_cols_kernel": o[0], "rows_per_thread": o[1], "exact": bool(o[2]),
+                "threads": o[3], "tile_stride": o[4], "grid": o[5]}
 
 
 class FairRankBatch:

@@ -306,3 +306,19 @@ def test_differentiation_size_free_costs_sampled_parity():
         np.testing.assert_allclose(X.sum(1), 1.0, atol=1e-5)
     F = g.step(1)
     assert F[0] > F0
+
+
+@pytest.mark.parametrize("I,K,expect", [
+    (1000, 10, (11, 8, True, 128, 1024)),   # tile sweep (the benchmarked shape)
+    (500, 10, (11, 4, True, 128, 0)),       # register sweep
+    (2000, 20, (21, 8, True, 256, 2048)),   # 21-column tile sweep
+    (300, 3, (8, 4, False, 96, 0)),         # padded 8-column bucket
+])
+def test_kernel_variant_reports_the_selected_sweep(I, K, expect):
+    g = fr.FairRank(3, I, K)
+    v = g.kernel_variant()
+    got = (v["n_cols_kernel"], v["rows_per_thread"], v["exact"], v["threads"], v["tile_stride"])
+    assert got == expect
+    assert 1 <= v["grid"] <= 3
+    p = fr.FairRank(3, I, K, param=fr.PARAM_ITEM).kernel_variant()
+    assert p["tile_stride"] == 0 and p["threads"] % 32 == 0
