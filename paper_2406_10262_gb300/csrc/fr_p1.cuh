@@ -2,8 +2,10 @@
 // instantiated by fr_p1.cu (the variant table) and fr_p1_k21.cu (21 columns).
 //
 // One persistent CTA processes consumers u = blockIdx.x, blockIdx.x + G, ... (Algorithm 1's
-// parallel loop over consumers). Each consumer's cost tile and relevance row are bulk-copied (TMA)
-// into shared memory one consumer ahead, while the previous consumer's Sinkhorn iterations run.
+// parallel loop over consumers). Each consumer's cost tile is bulk-copied (TMA) into shared
+// memory: in the register sweep one consumer ahead (with the relevance row), while the previous
+// consumer's Sinkhorn iterations run; in the tile sweep, whose solve keeps reading the tile, right
+// after the previous solve, from L2 where that solve prefetched it.
 //
 // Sinkhorn (Problem (7)) runs in the fused single-pass log-domain form, in log2 units
 // c' = c / (eps ln 2), g' = g / (eps ln 2):
