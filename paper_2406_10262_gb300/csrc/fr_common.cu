@@ -41,15 +41,22 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a, int bid, int nb
             c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
             s = t;
         };
-        for (; g + 7 * RED_WARPS < a.G; g += 8 * RED_WARPS) {  // eight loads in flight
+        for (; g + 15 * RED_WARPS < a.G; g += 16 * RED_WARPS) {  // sixteen loads in flight
             const float* q = p + (size_t)g * a.ld;
-            float x[8];
+            float x[16];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) x[j] = __ldcg(q + j * step);
+            for (int j = 0; j < 16; ++j) x[j] = __ldcg(q + j * step);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) two_sum(sa[j & 1], ca[j & 1], x[j]);
+            for (int j = 0; j < 16; ++j) two_sum(sa[j & 1], ca[j & 1], x[j]);
         }
-        for (; g < a.G; g += RED_WARPS) two_sum(sa[0], ca[0], __ldcg(p + (size_t)g * a.ld));
+        {  // the remaining fewer than sixteen, all loads first (zeros add exactly)
+            float x[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                x[j] = g + j * RED_WARPS < a.G ? __ldcg(p + (size_t)(g + j * RED_WARPS) * a.ld) : 0.f;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) two_sum(sa[j & 1], ca[j & 1], x[j]);
+        }
     }
     s_sum[warp][lane] = ((double)sa[0] + (double)ca[0]) + ((double)sa[1] + (double)ca[1]);
     __syncthreads();
