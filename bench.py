@@ -175,6 +175,19 @@ def oracle_sample(w, seed, budget_s, min_steps=1):
     return rate, info, dt
 
 
+def workload_config(args, w, world):
+    """The JSON line's config: the workload and its sizes (shared by both arms)."""
+    U, I, K, L, S = w["n_users"], w["n_items"], w["n_slots"], w["iters"], w["steps"]
+    state_mb = 3 * U * w["n_cols"] * ((I + 7) // 8 * 8) * 4 / 1e6
+    l2 = (f"state larger than L2 (C, m1, m2: {state_mb:.0f} MB read and written per ascent step)"
+          if state_mb > 129 else f"state {state_mb:.1f} MB, L2-resident (not flushed)")
+    return {"workload": args.workload, "n_users": U, "n_items": I, "n_slots": K,
+            "n_cols": w["n_cols"], "sinkhorn_iters": L, "ascent_steps": S, "param": "full_cost",
+            "optimizer": "adam lr 0.1", "step": f"reset + initial solve + {S} ascent steps",
+            "l2": l2,
+            "parallelism": f"independent markets x{world}" if world > 1 else "single market"}
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -192,7 +205,7 @@ def run_reference(args, w):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "sample": info["sample"]},
+            "config": dict(workload_config(args, w, 1), sample=info["sample"]),
             "impl": "reference", "cpu_baseline": info,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -337,11 +350,7 @@ def run_ours(args, w):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "n_users": U, "n_items": I, "n_slots": K,
-                       "n_cols": nc, "sinkhorn_iters": L, "ascent_steps": S, "param": "full_cost",
-                       "optimizer": "adam lr 0.1", "step": "reset + initial solve + 500 ascent steps",
-                       "l2": "state larger than L2 (C, m1, m2: 264 MB per solve step)",
-                       "parallelism": f"independent markets x{world}" if world > 1 else "single market"},
+            "config": workload_config(args, w, world),
             "time_to_nsw_s": ttn, "time_to_nsw_step": first, "nsw_final": float(trace[-1]),
             "nsw_ref_fp64": F_ref,
             "nsw_rel_err_final": None if F_ref is None else abs(float(trace[-1]) - F_ref) / abs(F_ref),
