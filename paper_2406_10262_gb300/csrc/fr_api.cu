@@ -893,11 +893,13 @@ fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* be
     fr_status st = ensure_fresh(ctx);
     if (st != FR_OK) return st;
     // scratch in tmp: V [U][ld] floats | rmax [tiles][ld] floats | diag [ld] floats | ru [ld]
-    // doubles | out [3] doubles (16-byte aligned pieces)
+    // doubles | out [3] doubles | column-sum partials [colsum_chunks()][ld] doubles (16-byte
+    // aligned pieces)
     const size_t ld = ctx->ld, nt = envy_tc_tiles(ctx->I);
     auto al = [](size_t b) { return (b + 15) / 16 * 16; };
     const size_t oV = 0, oM = oV + al(4 * (size_t)ctx->U * ld), oD = oM + al(4 * nt * ld),
-                 oR = oD + al(4 * ld), oO = oR + al(8 * ld), need = oO + al(8 * 3);
+                 oR = oD + al(4 * ld), oO = oR + al(8 * ld), oP = oO + al(8 * 3),
+                 need = oP + al(8 * (size_t)colsum_chunks() * ld);
     if ((st = ensure_tmp(ctx, need)) != FR_OK) return st;
     unsigned char* base = reinterpret_cast<unsigned char*>(ctx->tmp);
     float* V = reinterpret_cast<float*>(base + oV);
@@ -909,8 +911,9 @@ fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* be
     CU(cudaMemsetAsync(ctx->flags, 0, sizeof(int) * 4, ctx->s));
     CU(launch_envy(ctx->r, ctx->r_bf16, V, ctx->U, ctx->I, ctx->ld, ctx->imp, ctx->esum,
                    reinterpret_cast<float*>(base + oM), reinterpret_cast<float*>(base + oD),
-                   reinterpret_cast<double*>(base + oR), out, ctx->flags, ctx->s));
-    ctx->launches += 4;
+                   reinterpret_cast<double*>(base + oR), reinterpret_cast<double*>(base + oP), out,
+                   ctx->flags, ctx->s));
+    ctx->launches += 5;
     double h[3];
     int hf[4];
     CU(cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, ctx->s));

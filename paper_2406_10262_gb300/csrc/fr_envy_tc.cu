@@ -10,8 +10,8 @@
 // kind::tf32) and tracked by an mbarrier through tcgen05.commit. Operands live in shared memory in
 // the K-major, no-swizzle canonical layout: 8-row x 16-byte core matrices, core matrices adjacent
 // in K 128 bytes apart (leading byte offset), 8-row groups 1024 bytes apart (stride byte offset).
-// The CTA's 512 threads stage the next 32 consumers (two buffers) while the tensor cores work on the
-// current ones. The epilogue reads the accumulator rows back from tensor memory (tcgen05.ld,
+// The CTA's 512 threads stage the next 32 consumers (two shared buffers, operands loaded into
+// registers two stages ahead) while the tensor cores work on the current ones. The epilogue reads the accumulator rows back from tensor memory (tcgen05.ld,
 // 32 lanes per warp) and keeps only the row maxima over the tile's valid columns and, on diagonal
 // tiles, E_ii: the |I|^2 matrix is never written.
 //
@@ -35,7 +35,8 @@ constexpr int STAGE_BYTES = 4 * OPER_BYTES;   // A_hi, A_lo, B_hi, B_lo
 constexpr int LBO = 128;                      // bytes between K-adjacent core matrices
 constexpr int SBO = (TK / 4) * 128;           // bytes between 8-row groups
 constexpr unsigned kPolls = 1u << 20;
-constexpr unsigned kTmemCols = 128;           // FP32 accumulator: one column per tile column
+constexpr unsigned kTmemCols = 2 * TN;        // two FP32 accumulator regions of TN columns
+constexpr int CHUNK = 8;                      // stages (8 x 32 consumers) per accumulator chunk
 constexpr int NTHREADS = 512;                 // staging threads (warps 0-3 also run the epilogue)
 constexpr int KGROUPS = NTHREADS / TM;        // groups of 4 consumers per stage per thread row
 
@@ -88,7 +89,7 @@ __device__ __forceinline__ void mma_commit(unsigned long long* bar) {
 
 // One stage = 32 consumers of the tile: A[m][k] = r(u0 + k, i0 + m), B[n][k] = v(u0 + k, j0 + n).
 // Thread t owns row t % 128 of both operands and the groups of 4 consumers g0 + KGROUPS q,
-// g0 = t / 128. load_stage reads them into registers (issued one stage ahead, so the global-memory
+// g0 = t / 128. load_stage reads them into registers (issued two stages ahead, so the global-memory
 // latency overlaps the tensor cores' work); store_stage splits each value into TF32 hi and lo parts
 // and writes one 16-byte vector per group and part.
 constexpr int QG = TK / 4 / KGROUPS;  // groups per thread per stage
@@ -163,9 +164,37 @@ __global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const void* __rest
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *tmem_slot;
 
+    // Running sums of the tile in registers: warp w holds the tile rows of its tensor-memory lane
+    // quarter, 32 (w % 4) + lane, and the 32 columns 32 (w / 4) .. + 31.
+    const int q4 = warp & 3, cslice = warp >> 2;
+    float sum[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) sum[q] = 0.f;
+    auto read_chunk = [&](int c) {  // adds chunk c's accumulator (region c & 1) to the sums
+        unsigned v[32];
+        const unsigned taddr = tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)((c & 1) * TN + cslice * 32);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+            "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, "
+            "%26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+              "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+              "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
+              "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+              "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int q = 0; q < 32; ++q) sum[q] += __uint_as_float(v[q]);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    };
+
     const int nk = (U + TK - 1) / TK;
+    const int nch = (nk + CHUNK - 1) / CHUNK;
     bool ok = true;
     int issued = -1;  // last stage whose MMAs were committed
+    int nread = 0;    // chunks added to the running sums (in order)
     StageRegs regs;
     load_stage(regs, r, r_bf16, V, U, ld, i0, j0, 0);
     for (int kc = 0; kc < nk; ++kc) {
@@ -178,6 +207,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const void* __rest
             ok = false;
             break;
         }
+        // the chunk that ended with stage kc - 2 is complete (waited for just above): add it
+        // before chunk kc / CHUNK + 1 reuses its region
+        if (kc % CHUNK == 1 && kc > CHUNK) read_chunk(nread++);
         store_stage(sbuf, regs);
         if (kc + 1 < nk) load_stage(regs, r, r_bf16, V, U, ld, i0, j0, (kc + 1) * TK);
         fence_proxy_async_smem();  // generic-proxy stores -> the tensor cores' (async proxy) reads
@@ -185,6 +217,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const void* __rest
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const unsigned base = smem_u32(sbuf);
+            const unsigned dst = tmem + (unsigned)(((kc / CHUNK) & 1) * TN);
+            const bool first = kc % CHUNK == 0;
 #pragma unroll
             for (int ks = 0; ks < TK / KSTEP; ++ks) {
                 const unsigned koff = (unsigned)(ks * 2 * LBO);  // two core matrices per K step
@@ -192,9 +226,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const void* __rest
                 const unsigned long long al = smem_desc(base + 1 * OPER_BYTES + koff);
                 const unsigned long long bh = smem_desc(base + 2 * OPER_BYTES + koff);
                 const unsigned long long bl = smem_desc(base + 3 * OPER_BYTES + koff);
-                mma_tf32(tmem, ah, bh, (kc > 0 || ks > 0) ? 1u : 0u);
-                mma_tf32(tmem, ah, bl, 1u);
-                mma_tf32(tmem, al, bh, 1u);
+                mma_tf32(dst, ah, bh, (first && ks == 0) ? 0u : 1u);
+                mma_tf32(dst, ah, bl, 1u);
+                mma_tf32(dst, al, bh, 1u);
             }
             mma_commit(bar + st);
         }
@@ -205,36 +239,27 @@ __global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const void* __rest
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!__syncthreads_and(ok)) {
         if (tid == 0) atomicOr(err, 4);
-    } else if (warp < TM / 32) {
-        // epilogue: warp w reads accumulator lanes 32w .. 32w + 31 (tile rows), 32 columns at a time
-        const int il = warp * 32 + lane;
-        const int i = i0 + il;
-        float m = -INFINITY;
-#pragma unroll 1
-        for (int c0 = 0; c0 < TN; c0 += 32) {
-            unsigned v[32];
-            const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
-                "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, "
-                "%26, %27, %28, %29, %30, %31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                  "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-                  "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
-                  "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-                  "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-                  "=r"(v[30]), "=r"(v[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    } else {
+        while (nread < nch) read_chunk(nread++);  // the last one or two chunks
+        // row maxima over the tile's valid columns: each warp over its 32 columns, then the four
+        // column slices of a row combined through shared memory (the stage buffers are idle now)
+        const int row = q4 * 32 + lane, i = i0 + row;
+        float m = -INFINITY, d = 0.f;
 #pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                const int j = j0 + c0 + q;
-                const float e = __uint_as_float(v[q]);
-                if (j < I) m = fmaxf(m, e);
-                if (i0 == j0 && j == i && i < I) diag[i] = e;
-            }
+        for (int q = 0; q < 32; ++q) {
+            if (j0 + cslice * 32 + q < I) m = fmaxf(m, sum[q]);
+            if (q == lane) d = sum[q];
         }
-        if (i < I) rmax[(size_t)blockIdx.x * ld + i] = m;
+        if (i0 == j0 && cslice == q4 && i < I) diag[i] = d;  // column j = i sits in this slice
+        float* red = reinterpret_cast<float*>(stages);
+        red[cslice * TM + row] = m;
+        __syncthreads();
+        if (warp < TM / 32 && i < I) {
+            float mm = red[row];
+#pragma unroll
+            for (int sl = 1; sl < TN / 32; ++sl) mm = fmaxf(mm, red[sl * TM + row]);
+            rmax[(size_t)blockIdx.x * ld + i] = mm;
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();

@@ -209,7 +209,7 @@ cudaError_t launch_solve_cond(const DevState* st, int* ctl, cudaGraphConditional
 // evaluation metrics (fr_metrics.cu): v_ui = sum_{k<K} e_k x_uik into V [U][ld]; then the envy
 // contraction E = R^T V with its row-max epilogue, column sums of r and the ratio tests. out[3]:
 // mean max envy, % better off, % worse off. Scratch: rmax [envy_tc_tiles(I)][ld] floats, diag [ld]
-// floats, ru [ld] doubles.
+// floats, ru [ld] doubles, ru_part [colsum_chunks()][ld] doubles.
 // The contraction runs on the tensor cores (fr_envy_tc.cu: 128-item tiles, three TF32 products;
 // an expired bounded wait sets bit 4 of *err); rmax holds envy_tc_tiles(I) rows.
 int envy_tc_tiles(int I);
@@ -220,7 +220,8 @@ cudaError_t launch_envy_tc(const void* r, int r_bf16, const float* V, int U, int
                            float* rmax, float* diag, int* err, cudaStream_t s);
 cudaError_t launch_envy(const void* r, int r_bf16, const float* V, int U, int I, int ld,
                         const double* imp, double esum, float* rmax, float* diag, double* ru,
-                        double* out, int* err, cudaStream_t s);
+                        double* ru_part, double* out, int* err, cudaStream_t s);
+int colsum_chunks();  // FP64 partials [colsum_chunks()][ld] of the column sums of r (ru_part)
 // Frank-Wolfe certificate (fr_metrics.cu): one of a1 / a2 non-null (the policy's form); G CTAs
 // (cert_grid), per-CTA partials gap_part [G] doubles and res_part [G] floats; out[0] = gap,
 // out[1] = column residual.

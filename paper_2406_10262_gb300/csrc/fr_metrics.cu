@@ -22,59 +22,98 @@ __device__ __forceinline__ float rval(const void* r, int bf16, size_t o) {
                 : static_cast<const float*>(r)[o];
 }
 
-// v of consumers u0 + blockIdx.x under the free-cost policy (same arithmetic as policy_kernel).
+// v of consumer blockIdx.x under the free-cost policy (same arithmetic as policy_kernel). The
+// column constants are staged in shared memory once per consumer; the row maximum takes one pass
+// without exponentials and the normalisation a reciprocal.
 __global__ void v_p1_kernel(const P1Args a, float* __restrict__ V) {
+    __shared__ float s_gp[64], s_e[64];
     const int u = blockIdx.x;
     const int nc = a.nc;
     const float* C = a.C + (size_t)u * nc * a.ld;
-    const float* gp = a.gP + (size_t)u * nc;
+    for (int k = threadIdx.x; k < nc; k += blockDim.x) {
+        s_gp[k] = a.gP[(size_t)u * nc + k];
+        s_e[k] = k < a.K ? a.e[k] : 0.f;
+    }
+    __syncthreads();
+    const float sc = a.inv_eps_ln2;
     for (int i = threadIdx.x; i < a.ld; i += blockDim.x) {
         float v = 0.f;
         if (i < a.I) {
             float M = -INFINITY;
-            for (int k = 0; k < nc; ++k) M = fmaxf(M, gp[k] - C[(size_t)k * a.ld + i] * a.inv_eps_ln2);
+            for (int k = 0; k < nc; ++k) M = fmaxf(M, fmaf(-C[(size_t)k * a.ld + i], sc, s_gp[k]));
             float S = 0.f, num = 0.f;
             for (int k = 0; k < nc; ++k) {
-                const float p = ex2(gp[k] - C[(size_t)k * a.ld + i] * a.inv_eps_ln2 - M);
+                const float p = ex2(fmaf(-C[(size_t)k * a.ld + i], sc, s_gp[k]) - M);
                 S += p;
-                if (k < a.K) num += a.e[k] * p;
+                num = fmaf(s_e[k], p, num);
             }
-            v = num / S;
+            v = num * rcp_approx(S);
         }
         V[(size_t)u * a.ld + i] = v;
     }
 }
 
-// v under the per-item policy x_ik = softmax_k(g'_k + s_i (e_k - e_max)).
+// v under the per-item policy x_ik = softmax_k(g'_k + s_i (e_k - e_max)): the consumer's column
+// constants are held in registers for a compiled column bucket NCB >= nc (the padding columns get
+// g' = -inf, so their terms vanish), the row maximum takes one pass without exponentials and the
+// normalisation a reciprocal.
+template <int NCB>
 __global__ void v_p2_kernel(const P2Args a, float* __restrict__ V) {
     const int u = blockIdx.x;
     const int nc = a.nc;
-    const float* gp = a.gP + (size_t)u * nc;
+    float gk[NCB], ehk[NCB], ek[NCB];
+#pragma unroll
+    for (int k = 0; k < NCB; ++k) {
+        gk[k] = k < nc ? __ldg(a.gP + (size_t)u * nc + k) : -INFINITY;
+        ehk[k] = k < nc ? __ldg(a.e + k) - a.emax : 0.f;
+        ek[k] = k < a.K ? __ldg(a.e + k) : 0.f;
+    }
     for (int i = threadIdx.x; i < a.ld; i += blockDim.x) {
         float v = 0.f;
         if (i < a.I) {
-            const float si = rval(a.r, a.r_bf16, (size_t)u * a.ld + i) * a.w[i] * a.inv_eps_ln2;
+            const float si = rval(a.r, a.r_bf16, (size_t)u * a.ld + i) * __ldg(a.w + i) * a.inv_eps_ln2;
             float M = -INFINITY;
-            for (int k = 0; k < nc; ++k) M = fmaxf(M, fmaf(si, a.e[k] - a.emax, gp[k]));
+#pragma unroll
+            for (int k = 0; k < NCB; ++k) M = fmaxf(M, fmaf(si, ehk[k], gk[k]));
             float S = 0.f, num = 0.f;
-            for (int k = 0; k < nc; ++k) {
-                const float p = ex2(fmaf(si, a.e[k] - a.emax, gp[k]) - M);
+#pragma unroll
+            for (int k = 0; k < NCB; ++k) {
+                const float p = ex2(fmaf(si, ehk[k], gk[k]) - M);
                 S += p;
-                if (k < a.K) num += a.e[k] * p;
+                num = fmaf(ek[k], p, num);
             }
-            v = num / S;
+            v = num * rcp_approx(S);
         }
         V[(size_t)u * a.ld + i] = v;
     }
 }
 
-// sum_u r(u,i) in FP64, one thread per item (coalesced across items).
+// sum_u r(u,i): chunk blockIdx.y of COLSUM_CHUNKS interleaved consumer chunks, one thread per item
+// (coalesced across items), compensated FP32 sums (Knuth's TwoSum) written as FP64 partials
+// part[chunk][i]; colsum_final_kernel adds the chunks in a fixed order.
+constexpr int COLSUM_CHUNKS = 32;
+
 __global__ void colsum_kernel(const void* __restrict__ r, int r_bf16, int U, int I, int ld,
-                              double* __restrict__ ru) {
+                              double* __restrict__ part) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= I) return;
+    float s = 0.f, c = 0.f;
+    for (int u = blockIdx.y; u < U; u += COLSUM_CHUNKS) {
+        const float x = rval(r, r_bf16, (size_t)u * ld + i);
+        const float t = __fadd_rn(s, x);
+        const float bp = __fsub_rn(t, s);
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
+        s = t;
+    }
+    part[(size_t)blockIdx.y * ld + i] = (double)s + (double)c;
+}
+
+__global__ void colsum_final_kernel(const double* __restrict__ part, int I, int ld,
+                                    double* __restrict__ ru) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= I) return;
     double s = 0.0;
-    for (int u = 0; u < U; ++u) s += (double)rval(r, r_bf16, (size_t)u * ld + i);
+    for (int q = 0; q < COLSUM_CHUNKS; ++q) s += part[(size_t)q * ld + i];
     ru[i] = s;
 }
 
@@ -132,17 +171,32 @@ cudaError_t launch_v_p1(const P1Args& a, float* V, cudaStream_t s) {
 }
 
 cudaError_t launch_v_p2(const P2Args& a, float* V, cudaStream_t s) {
-    v_p2_kernel<<<a.U, 256, 0, s>>>(a, V);
+    switch (a.nc) {  // exact column counts of the common shapes (K = 5, 10, 20), buckets otherwise
+        case 6: v_p2_kernel<6><<<a.U, 256, 0, s>>>(a, V); break;
+        case 11: v_p2_kernel<11><<<a.U, 256, 0, s>>>(a, V); break;
+        case 21: v_p2_kernel<21><<<a.U, 256, 0, s>>>(a, V); break;
+        default:
+            if (a.nc <= 8)
+                v_p2_kernel<8><<<a.U, 256, 0, s>>>(a, V);
+            else if (a.nc <= 16)
+                v_p2_kernel<16><<<a.U, 256, 0, s>>>(a, V);
+            else
+                v_p2_kernel<32><<<a.U, 256, 0, s>>>(a, V);
+    }
     return cudaGetLastError();
 }
 
+int colsum_chunks() { return COLSUM_CHUNKS; }
+
 cudaError_t launch_envy(const void* r, int r_bf16, const float* V, int U, int I, int ld,
                         const double* imp, double esum, float* rmax, float* diag, double* ru,
-                        double* out, int* err, cudaStream_t s) {
+                        double* ru_part, double* out, int* err, cudaStream_t s) {
     const int nt = envy_tc_tiles(I);
     cudaError_t e = launch_envy_tc(r, r_bf16, V, U, I, ld, rmax, diag, err, s);
     if (e != cudaSuccess) return e;
-    colsum_kernel<<<(I + 255) / 256, 256, 0, s>>>(r, r_bf16, U, I, ld, ru);
+    colsum_kernel<<<dim3((I + 255) / 256, COLSUM_CHUNKS), 256, 0, s>>>(r, r_bf16, U, I, ld, ru_part);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    colsum_final_kernel<<<(I + 255) / 256, 256, 0, s>>>(ru_part, I, ld, ru);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     envy_final_kernel<<<1, 1024, 0, s>>>(rmax, nt, diag, ru, I, ld, imp, esum, out);
     return cudaGetLastError();
