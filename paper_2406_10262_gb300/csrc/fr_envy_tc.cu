@@ -48,10 +48,11 @@ __device__ __forceinline__ float rval_tc(const void* r, int bf16, size_t o) {
                 : static_cast<const float*>(r)[o];
 }
 
+// x rounded to TF32 (10 explicit mantissa bits), to nearest with ties away from zero, in two integer
+// operations: add half a TF32 unit in the last place to the magnitude bits, then clear the 13
+// dropped bits (a carry into the exponent is the correct rounding up to the next binade).
 __device__ __forceinline__ unsigned to_tf32(float x) {
-    unsigned y;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
-    return y;
+    return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
 }
 
 // Byte offset of element (row m, k) of a 128 x 32 K-major operand part.
