@@ -67,11 +67,14 @@ def parse():
     ap.add_argument("--compare", choices=["batch", "unrolled", "bf16", "paper-shapes", "p1-scale"],
                     default=None,
                     help="compare a layered form against the plain FP32 method (one JSON line)")
-    ap.add_argument("--profile-item", choices=["implicit", "unrolled", "bf16", "batch"], default=None,
+    ap.add_argument("--profile-item", choices=["implicit", "unrolled", "bf16", "batch", "metrics"],
+                    default=None,
                     help="profiling driver for the per-item forms: set up the workload, run "
-                         "--profile-steps ascent steps, exit")
+                         "--profile-steps ascent steps (metrics: then one fr_metrics call), exit")
     ap.add_argument("--profile-users", type=int, default=0,
                     help="with --profile-item: override the number of consumers (small captures)")
+    ap.add_argument("--profile-items", type=int, default=0,
+                    help="with --profile-item metrics: override the number of items")
     return ap.parse_args()
 
 
@@ -577,7 +580,8 @@ def compare_paper_shapes(args):
 def profile_item(args):
     """Sets up one per-item workload and runs --profile-steps ascent steps (for ncu captures):
     implicit / unrolled: 20000 x 2000, K = 20, L = 100 (checkpoints every 10); bf16: 200000 x 10^4,
-    K = 20, L = 50, BF16 relevance; batch: the 256-market workload, L = 50."""
+    K = 20, L = 50, BF16 relevance; batch: the 256-market workload, L = 50; metrics: 20000 x 10^4,
+    K = 20, L = 20, then one fr_metrics call (the envy contraction)."""
     import torch
     from paper_2406_10262_gb300 import fairrank as fr
     from paper_2406_10262_gb300 import synth
@@ -591,6 +595,14 @@ def profile_item(args):
             b.set_exposure(j, synth.dcg_exposure(m.n_slots))
         b.step(n, trace=False)
         launches = b.launch_count()
+    elif args.profile_item == "metrics":
+        U, I, K = args.profile_users or 20000, args.profile_items or 10000, 20
+        g = fr.FairRank(U, I, K, param=fr.PARAM_ITEM, sinkhorn_iters=20)
+        g.set_relevance(synth.relevance_lowrank_fast(U, I, seed=5))
+        g.set_exposure(synth.dcg_exposure(K))
+        g.step(n, trace=False)
+        g.metrics()
+        launches = g.launch_count()
     else:
         bf16 = args.profile_item == "bf16"
         U, I, K, L = (200000, 10000, 20, 50) if bf16 else (20000, 2000, 20, 100)
