@@ -580,7 +580,8 @@ def compare_paper_shapes(args):
 def profile_item(args):
     """Sets up one per-item workload and runs --profile-steps ascent steps (for ncu captures):
     implicit / unrolled: 20000 x 2000, K = 20, L = 100 (checkpoints every 10); bf16: 200000 x 10^4,
-    K = 20, L = 50, BF16 relevance; batch: the 256-market workload, L = 50; metrics: 20000 x 10^4,
+    K = 20, L = 50, BF16 relevance; batch: the 256-market workload, L = 50, autotuned and warmed up
+    first, the n steps between profiler start and stop (ncu --profile-from-start off); metrics: 20000 x 10^4,
     K = 20, L = 20, then one fr_metrics call (the envy contraction)."""
     import torch
     from paper_2406_10262_gb300 import fairrank as fr
@@ -593,7 +594,13 @@ def profile_item(args):
         for j, m in enumerate(ms):
             b.set_relevance(j, synth.relevance_lowrank_fast(m.n_users, m.n_items, seed=m.seed))
             b.set_exposure(j, synth.dcg_exposure(m.n_slots))
+        b.autotune()
+        b.step(1, trace=False)  # warm-up; captures may start at the profiler start below
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
         b.step(n, trace=False)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
         launches = b.launch_count()
     elif args.profile_item == "metrics":
         U, I, K = args.profile_users or 20000, args.profile_items or 10000, 20
