@@ -233,6 +233,14 @@ __device__ __forceinline__ void gram_block(const Smem& s, int nc, int I, int lds
 // costs stay in registers between iterations, which is what allows eight rows per thread at four
 // CTAs per SM. The impacts of a block's rows go straight into the CTA's partial row
 // part[blockIdx] (written by its first consumer, accumulated by the later ones).
+template <bool B>
+struct BoolTag {
+    static constexpr bool value = B;
+};
+template <bool B>
+__device__ __forceinline__ constexpr bool last_of(BoolTag<B>) { return B; }
+__device__ __forceinline__ bool last_of(bool b) { return b; }
+
 template <int BR>
 struct RowBlock {  // one load / store of a block's BR consecutive floats (8- or 16-byte aligned)
     static __device__ __forceinline__ void load(const float* p, f2 (&c)[BR / 2]) {
@@ -309,8 +317,10 @@ __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u
             }
         }
     }
-    for (int l = 0; l < a.L; ++l) {
-        const bool last = l == a.L - 1;
+    // One iteration; the last one (which also writes g^(L-1) and adds the impacts) is a separate
+    // instantiation, so the loop over the first L - 1 carries no test for it.
+    auto iteration = [&](int l, auto tag) {
+        constexpr bool last = decltype(tag)::value;
         if (last && warp == 0) {
 #pragma unroll
             for (int j = 0; j < GPL; ++j)
@@ -326,6 +336,8 @@ __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u
         if constexpr (!WIDE) {
 #pragma unroll
             for (int k = 0; k < NCB; ++k) g2[k] = pk(gk[k], gk[k]);
+        } else {
+            (void)g2;
         }
         auto gpair = [&](int k) -> f2 {
             if constexpr (WIDE) return pk(gk[k], gk[k]);
@@ -502,7 +514,9 @@ __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u
         // moments follow at the start of its gradient step, closer to their use)
         if (l == (a.L > 8 ? a.L - 8 : 0) && tid == 0)
             prefetch_consumer(a, u + gridDim.x, nc, ld, false);
-    }
+    };
+    for (int l = 0; l < a.L - 1; ++l) iteration(l, BoolTag<false>{});
+    iteration(a.L - 1, BoolTag<true>{});
 }
 
 // Launch bound: 512 threads, except the tile sweep of more than 16 columns, which serves at most
@@ -815,6 +829,9 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
                     c[r][k] = (vr[r] && (EXACT || k < nc)) ? c[r][k] * sc + M : INFINITY;
             }
         }
+        // the last iteration (which also writes g^(L-1) and adds the impacts) as a separate
+        // instantiation, where a second copy of the body fits the registers
+        constexpr bool PEEL = NCB <= 11;
         if constexpr (PAIR) {
             constexpr int RP = R / 2;
             f2 c2[RP][NCB];
@@ -822,8 +839,8 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
             for (int rp = 0; rp < RP; ++rp)
 #pragma unroll
                 for (int k = 0; k < NCB; ++k) c2[rp][k] = pk(c[2 * rp][k], c[2 * rp + 1][k]);
-            for (int l = 0; l < a.L; ++l) {
-                const bool last = l == a.L - 1;
+            auto iteration = [&](int l, auto tag) {
+                const bool last = last_of(tag);
                 if (last && warp == 0) {
 #pragma unroll
                     for (int j = 0; j < GPL; ++j)
@@ -910,10 +927,16 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
                 par ^= 1;
                 if (l == 0 && tid == 0)
                     stage_consumer(a, u + gridDim.x, nc, ld, s, MODE == MODE_UPDATE_SWEEP && a.optimizer == 0, false);
+            };
+            if constexpr (PEEL) {
+                for (int l = 0; l < a.L - 1; ++l) iteration(l, BoolTag<false>{});
+                iteration(a.L - 1, BoolTag<true>{});
+            } else {
+                for (int l = 0; l < a.L; ++l) iteration(l, l == a.L - 1);
             }
         } else {
-            for (int l = 0; l < a.L; ++l) {
-                const bool last = l == a.L - 1;
+            auto iteration = [&](int l, auto tag) {
+                const bool last = last_of(tag);
                 if (last && warp == 0) {
 #pragma unroll
                     for (int j = 0; j < GPL; ++j)
@@ -962,6 +985,12 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
                 par ^= 1;
                 if (l == 0 && tid == 0)
                     stage_consumer(a, u + gridDim.x, nc, ld, s, MODE == MODE_UPDATE_SWEEP && a.optimizer == 0, false);
+            };
+            if constexpr (PEEL) {
+                for (int l = 0; l < a.L - 1; ++l) iteration(l, BoolTag<false>{});
+                iteration(a.L - 1, BoolTag<true>{});
+            } else {
+                for (int l = 0; l < a.L; ++l) iteration(l, l == a.L - 1);
             }
         }
         }  // register sweep
