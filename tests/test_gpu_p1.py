@@ -47,6 +47,12 @@ def test_initial_sweep_is_the_uniform_policy():
     (4, 300, 20, 1.0, 30, 1),     # 21 columns, 512-float stride, several warps
     (3, 900, 20, 0.8, 20, 1),     # 21 columns, 1024-float stride, eps != 1
     (2, 1999, 20, 1.0, 10, 1),    # 21 columns, 2048-float stride, ragged item count
+    # L = 1 runs only the last iteration's instantiation, L = 2 one of each
+    (3, 200, 10, 1.0, 1, 1),      # 11 columns, register sweep
+    (3, 701, 10, 0.9, 2, 0),      # 11 columns, register sweep, cold start
+    (3, 1000, 10, 1.0, 1, 1),     # 11 columns, tile sweep
+    (2, 1030, 10, 0.9, 2, 1),     # 11 columns, tile sweep, 2048-float stride
+    (2, 700, 20, 1.0, 1, 1),      # 21 columns, tile sweep
 ])
 def test_one_step_from_seeded_state(U, I, K, eps, L, warm):
     r = synth.relevance_lowrank(U, I, seed=U + I)
