@@ -1033,6 +1033,15 @@ fr_status fr_kernel_variant(const fr_ctx* ctx, int32_t* out) {
     return FR_OK;
 }
 
+fr_status fr_sweep_stats(fr_ctx* ctx, int64_t* log_form_solves) {
+    if (!ctx || !log_form_solves) return fail(nullptr, FR_EINVAL, "ctx or out is NULL");
+    Join j(ctx);
+    CU(cudaMemcpyAsync(ctx->st_host, ctx->st, sizeof(DevState), cudaMemcpyDeviceToHost, ctx->s));
+    CU(cudaStreamSynchronize(ctx->s));
+    *log_form_solves = (int64_t)ctx->st_host->log_solves;
+    return FR_OK;
+}
+
 fr_status fr_measure_ex2_rate(double* ex2_per_second) {
     fr_ctx* ctx = nullptr;
     if (!ex2_per_second) return fail(nullptr, FR_EINVAL, "output is NULL");

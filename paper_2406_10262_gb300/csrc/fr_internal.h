@@ -31,6 +31,7 @@ struct DevState {
     int steps_done;       // steps applied since the host last cleared it
     unsigned int counter; // last-block-done counter of the reduction (returns to 0)
     int max_steps;        // > 0: the reduction raises stop once steps_done reaches it
+    unsigned long long log_solves;  // tile-sweep solves that finished in the log form
     double F, utility, gnorm;
     double thresh;        // < 0: never stop
 };

@@ -225,14 +225,9 @@ __device__ __forceinline__ void gram_block(const Smem& s, int nc, int I, int lds
     if constexpr (Q0 + NQ < NGALL) gram_block<NCB, EXACT, Q0 + NQ>(s, nc, I, lds, sc, gout);
 }
 
-// Tile sweep: the Sinkhorn phase of consumer u with its costs read from the resident shared tile
-// (the same iteration as the register sweep of p1_kernel). A thread owns R / BR blocks of BR
-// consecutive rows (BR = 2 or 4), block b at rows BR (b T + tid): the read of a block's column k
-// is one 8- or 16-byte load per lane and conflict-free (consecutive lanes, consecutive words), at
-// a compile-time offset k LDS from the block's base (no address arithmetic per load), and no
-// costs stay in registers between iterations, which is what allows eight rows per thread at four
-// CTAs per SM. The impacts of a block's rows go straight into the CTA's partial row
-// part[blockIdx] (written by its first consumer, accumulated by the later ones).
+// Whether a Sinkhorn iteration is the last one: BoolTag<B> decides at compile time (the peeled
+// last iteration is its own instantiation), a plain bool at run time. BoolTag also selects the
+// tile sweep's form.
 template <bool B>
 struct BoolTag {
     static constexpr bool value = B;
@@ -261,6 +256,33 @@ struct RowBlock {  // one load / store of a block's BR consecutive floats (8- or
     }
 };
 
+// Largest drift |g'_k - g0_k| (log2 units) of a column potential from its value at the start of
+// the solve for which the tile sweep keeps its exponential form (below).
+constexpr float TS_DRIFT = 30.f;
+
+// Tile sweep: the Sinkhorn phase of consumer u with its costs read from the resident shared tile
+// (the same iteration as the register sweep of p1_kernel). A thread owns R / BR blocks of BR
+// consecutive rows (BR = 2 or 4), block b at rows BR (b T + tid): the read of a block's column k
+// is one 8- or 16-byte load per lane and conflict-free (consecutive lanes, consecutive words), at
+// a compile-time offset k LDS from the block's base (no address arithmetic per load), and no
+// costs stay in registers between iterations, which is what allows eight rows per thread at four
+// CTAs per SM. The impacts of a block's rows go straight into the CTA's partial row
+// part[blockIdx] (written by its first consumer, accumulated by the later ones).
+//
+// The tile holds one of two forms of the row-shifted kernel; both give the same policy in exact
+// arithmetic (a factor per column or per row cancels in x_ik = p_ik / sum_k p_ik).
+// - Exponential form (from the start of every solve): E_ik = 2^(g0_k - c~_ik) with g0 = g' at the
+//   start, c~_ik = c_ik / (eps ln 2) + shift_i and shift_i = max_k (g0_k - c_ik / (eps ln 2)), so
+//   the row's largest E is exactly 1 (padding rows I <= i < ld hold 0). An iteration forms
+//   G_k = 2^(g'_k - g0_k), one ex2 per column, and p_ik = E_ik G_k, one multiply per cell. While
+//   every |g'_k - g0_k| <= TS_DRIFT, a real row's sum lies in [2^-30, m 2^30], and a term flushed
+//   to zero when E was formed (below 2^-126 of its row's largest) stays below 2^-66 of the row's
+//   largest term: the result is the log form's up to FP32 rounding.
+// - Log form: c~_ik in the tile (+inf on padding rows), p_ik = 2^(g'_k - c~_ik), one ex2 per cell,
+//   rows re-shifted exactly when their sum leaves [2^-64, 2^64]. When a potential drifts past
+//   TS_DRIFT the CTA rebuilds its rows in this form from the costs in global memory (at the
+//   current g') and finishes the solve in it; every warp holds the same g', so all decide alike.
+// Each thread rewrites only its own rows, which only it reads during the solve.
 template <int NCB, int R, int BR, int LDS, bool EXACT, int MODE>
 __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u, int nc,
                                            float (&gm)[(NCB + 31) / 32], int& par) {
@@ -274,9 +296,50 @@ __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u
     // Block b starts at row rb = BR (b T + tid); ld is a multiple of 8, so a block lies inside the
     // tile (rb < ld) or past it. Row j of the block is a consumer row if rb + j < I.
     //
-    // c~_ik = c_ik / (eps ln 2) + shift_i in place, shift_i = max_k (g'_k - c_ik / (eps ln 2)), so
-    // that the row's largest term is 2^0; +inf on the padding rows I <= i < ld (their terms are 0).
-    // Each thread rewrites only its own rows, which only it reads during the solve.
+    // The row shifts of costs cb[k LDS] (BR rows, column k) at potentials gk; EXPF: then E in place
+    // of the costs at cd, else c~.
+    auto shift_rows = [&](const float* cb, int cstride, float* cd, int rb, const float (&gk)[NCB],
+                          auto form) {
+        constexpr bool EXPF = decltype(form)::value;
+        float M[BR];
+#pragma unroll
+        for (int j = 0; j < BR; ++j) M[j] = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < NCB; ++k) {
+            if (EXACT || k < nc) {
+                f2 c[NP];
+                RBk::load(cb + k * cstride, c);
+#pragma unroll
+                for (int q = 0; q < NP; ++q) {
+                    float c0, c1;
+                    upk(c[q], c0, c1);
+                    M[2 * q] = fmaxf(M[2 * q], gk[k] - c0 * sc);
+                    M[2 * q + 1] = fmaxf(M[2 * q + 1], gk[k] - c1 * sc);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NCB; ++k) {
+            if (EXACT || k < nc) {
+                f2 c[NP];
+                RBk::load(cb + k * cstride, c);
+                float v[BR];
+#pragma unroll
+                for (int q = 0; q < NP; ++q) upk(c[q], v[2 * q], v[2 * q + 1]);
+#pragma unroll
+                for (int j = 0; j < BR; ++j) {
+                    if constexpr (EXPF)
+                        v[j] = rb + j < I ? ex2(gk[k] - fmaf(v[j], sc, M[j])) : 0.f;
+                    else
+                        v[j] = rb + j < I ? fmaf(v[j], sc, M[j]) : INFINITY;
+                }
+                RBk::store(cd + k * LDS, v);
+            }
+        }
+    };
+    float g0m[GPL];  // g' at the start of the solve (this lane's columns)
+#pragma unroll
+    for (int j = 0; j < GPL; ++j) g0m[j] = gm[j];
     {
         float gk[NCB];
         bcast_g<NCB, GPL>(gm, gk);
@@ -284,39 +347,11 @@ __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u
         for (int b = 0; b < NB; ++b) {
             const int rb = BR * (b * T + tid);
             if (rb >= ld) break;
-            float* cb = s.C + rb;
-            float M[BR];
-#pragma unroll
-            for (int j = 0; j < BR; ++j) M[j] = -INFINITY;
-#pragma unroll
-            for (int k = 0; k < NCB; ++k) {
-                if (EXACT || k < nc) {
-                    f2 c[NP];
-                    RBk::load(cb + k * LDS, c);
-#pragma unroll
-                    for (int q = 0; q < NP; ++q) {
-                        float c0, c1;
-                        upk(c[q], c0, c1);
-                        M[2 * q] = fmaxf(M[2 * q], gk[k] - c0 * sc);
-                        M[2 * q + 1] = fmaxf(M[2 * q + 1], gk[k] - c1 * sc);
-                    }
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < NCB; ++k) {
-                if (EXACT || k < nc) {
-                    f2 c[NP];
-                    RBk::load(cb + k * LDS, c);
-                    float v[BR];
-#pragma unroll
-                    for (int q = 0; q < NP; ++q) upk(c[q], v[2 * q], v[2 * q + 1]);
-#pragma unroll
-                    for (int j = 0; j < BR; ++j) v[j] = rb + j < I ? fmaf(v[j], sc, M[j]) : INFINITY;
-                    RBk::store(cb + k * LDS, v);
-                }
-            }
+            shift_rows(s.C + rb, LDS, s.C + rb, rb, gk, BoolTag<true>{});
         }
     }
+    bool lg = false;  // the tile holds the log form (the same in every thread of the CTA)
+    const float* __restrict__ Cu = a.C + (size_t)u * nc * ld;
     // One iteration; the last one (which also writes g^(L-1) and adds the impacts) is a separate
     // instantiation, so the loop over the first L - 1 carries no test for it.
     auto iteration = [&](int l, auto tag) {
@@ -326,95 +361,72 @@ __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u
             for (int j = 0; j < GPL; ++j)
                 if (j * 32 + lane < nc) a.gP[(size_t)u * nc + j * 32 + lane] = gm[j];
         }
-        // Tiles of up to 16 columns hold g' as packed pairs (g'_k, g'_k) and the column sums as
-        // packed row-pair partials; wider tiles hold both as scalars (pairs formed at use, column
-        // sums accumulated with two FMAs), which keeps 21 columns within the register budget.
-        constexpr bool WIDE = NCB > 16;
-        float gk[NCB];
-        bcast_g<NCB, GPL>(gm, gk);
-        f2 g2[WIDE ? 1 : NCB];
-        if constexpr (!WIDE) {
+        if (!lg) {
+            bool far = false;
 #pragma unroll
-            for (int k = 0; k < NCB; ++k) g2[k] = pk(gk[k], gk[k]);
-        } else {
-            (void)g2;
-        }
-        auto gpair = [&](int k) -> f2 {
-            if constexpr (WIDE) return pk(gk[k], gk[k]);
-            else return g2[k];
-        };
-        auto gscal = [&](int k) -> float {
-            if constexpr (WIDE) {
-                return gk[k];
-            } else {
-                float lo, hi;
-                upk(g2[k], lo, hi);
-                return lo;
+            for (int j = 0; j < GPL; ++j)
+                if (j * 32 + lane < nc) far |= !(fabsf(gm[j] - g0m[j]) <= TS_DRIFT);
+            if (__builtin_expect(__any_sync(FULL, far), 0)) {  // rebuild the rows in the log form
+                lg = true;
+                if (tid == 0) atomicAdd(&a.st->log_solves, 1ull);
+                float gk[NCB];
+                bcast_g<NCB, GPL>(gm, gk);
+#pragma unroll 1
+                for (int b = 0; b < NB; ++b) {
+                    const int rb = BR * (b * T + tid);
+                    if (rb >= ld) break;
+                    shift_rows(Cu + rb, ld, s.C + rb, rb, gk, BoolTag<false>{});
+                }
             }
-        };
+        }
+        // Tiles of up to 16 columns hold g' (or G) as packed pairs and the column sums as packed
+        // row-pair partials; wider tiles hold both as scalars (pairs formed at use, column sums
+        // accumulated with two FMAs), which keeps 21 columns within the register budget.
+        constexpr bool WIDE = NCB > 16;
         f2 cs2[WIDE ? 1 : NCB];
         float csw[WIDE ? NCB : 1];
 #pragma unroll
         for (int k = 0; k < (WIDE ? 1 : NCB); ++k) cs2[k] = 0ull;
 #pragma unroll
         for (int k = 0; k < (WIDE ? NCB : 1); ++k) csw[k] = 0.f;
-#pragma unroll 1
-        for (int b = 0; b < NB; ++b) {
-            const int rb = BR * (b * T + tid);
-            if (rb >= ld) break;
-            float* cb = s.C + rb;
-            f2 p[NP][NCB];  // row pairs (0, 1) and (2, 3) of the block
-            f2 S2[NP];
+        auto sweep = [&](auto form) {
+            constexpr bool EXPF = decltype(form)::value;
+            float gk[NCB];  // G_k (exponential form) or g'_k (log form)
+            if constexpr (EXPF) {
+                float Gm[GPL];
 #pragma unroll
-            for (int q = 0; q < NP; ++q) S2[q] = 0ull;
+                for (int j = 0; j < GPL; ++j) Gm[j] = ex2(gm[j] - g0m[j]);
+                bcast_g<NCB, GPL>(Gm, gk);
+            } else {
+                bcast_g<NCB, GPL>(gm, gk);
+            }
+            f2 g2[WIDE ? 1 : NCB];
+            if constexpr (!WIDE) {
 #pragma unroll
-            for (int k = 0; k < NCB; ++k) {
-                if (EXACT || k < nc) {
-                    f2 c[NP];
-                    RBk::load(cb + k * LDS, c);
-#pragma unroll
-                    for (int q = 0; q < NP; ++q) {
-                        float d0, d1;
-                        upk(sub2(gpair(k), c[q]), d0, d1);
-                        p[q][k] = pk(ex2(d0), ex2(d1));
-                    }
+                for (int k = 0; k < NCB; ++k) g2[k] = pk(gk[k], gk[k]);
+            } else {
+                (void)g2;
+            }
+            auto gpair = [&](int k) -> f2 {
+                if constexpr (WIDE) return pk(gk[k], gk[k]);
+                else return g2[k];
+            };
+            auto gscal = [&](int k) -> float {
+                if constexpr (WIDE) {
+                    return gk[k];
                 } else {
-#pragma unroll
-                    for (int q = 0; q < NP; ++q) p[q][k] = 0ull;
+                    float lo, hi;
+                    upk(g2[k], lo, hi);
+                    return lo;
                 }
-#pragma unroll
-                for (int q = 0; q < NP; ++q) S2[q] = add2(S2[q], p[q][k]);
-            }
-            float S[BR];
-#pragma unroll
-            for (int q = 0; q < NP; ++q) upk(S2[q], S[2 * q], S[2 * q + 1]);
-            bool bad[BR], any_bad = false;
-#pragma unroll
-            for (int j = 0; j < BR; ++j) {
-                bad[j] = rb + j < I && !(S[j] >= 0x1p-64f && S[j] <= 0x1p64f);
-                any_bad |= bad[j];
-            }
-            if (__builtin_expect(any_bad, 0)) {  // re-shift the block's out-of-range rows exactly
-                float M[BR];
-#pragma unroll
-                for (int j = 0; j < BR; ++j) M[j] = -INFINITY;
-#pragma unroll
-                for (int k = 0; k < NCB; ++k) {
-                    if (EXACT || k < nc) {
-                        const float gkk = gscal(k);
-                        f2 c[NP];
-                        RBk::load(cb + k * LDS, c);
-#pragma unroll
-                        for (int q = 0; q < NP; ++q) {
-                            float c0, c1;
-                            upk(c[q], c0, c1);
-                            M[2 * q] = fmaxf(M[2 * q], gkk - c0);
-                            M[2 * q + 1] = fmaxf(M[2 * q + 1], gkk - c1);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < BR; ++j) M[j] = bad[j] ? M[j] : 0.f;
+            };
+#pragma unroll 1
+            for (int b = 0; b < NB; ++b) {
+                const int rb = BR * (b * T + tid);
+                if (rb >= ld) break;
+                float* cb = s.C + rb;
+                f2 p[NP][NCB];  // row pairs (0, 1) and (2, 3) of the block
+                f2 S2[NP];
 #pragma unroll
                 for (int q = 0; q < NP; ++q) S2[q] = 0ull;
 #pragma unroll
@@ -422,79 +434,140 @@ __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u
                     if (EXACT || k < nc) {
                         f2 c[NP];
                         RBk::load(cb + k * LDS, c);
-                        float v[BR];
 #pragma unroll
                         for (int q = 0; q < NP; ++q) {
-                            upk(c[q], v[2 * q], v[2 * q + 1]);
-                            v[2 * q] += M[2 * q];
-                            v[2 * q + 1] += M[2 * q + 1];
-                            float d0, d1;
-                            upk(sub2(gpair(k), pk(v[2 * q], v[2 * q + 1])), d0, d1);
-                            p[q][k] = pk(ex2(d0), ex2(d1));
+                            if constexpr (EXPF) {
+                                p[q][k] = mul2(c[q], gpair(k));
+                            } else {
+                                float d0, d1;
+                                upk(sub2(gpair(k), c[q]), d0, d1);
+                                p[q][k] = pk(ex2(d0), ex2(d1));
+                            }
                         }
-                        RBk::store(cb + k * LDS, v);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < NP; ++q) p[q][k] = 0ull;
                     }
 #pragma unroll
                     for (int q = 0; q < NP; ++q) S2[q] = add2(S2[q], p[q][k]);
                 }
+                float S[BR];
 #pragma unroll
                 for (int q = 0; q < NP; ++q) upk(S2[q], S[2 * q], S[2 * q + 1]);
-            }
-            float inv[BR];
+                if constexpr (!EXPF) {
+                    bool bad[BR], any_bad = false;
 #pragma unroll
-            for (int j = 0; j < BR; ++j) inv[j] = rb + j < I ? rcp_approx(S[j]) : 0.f;
+                    for (int j = 0; j < BR; ++j) {
+                        bad[j] = rb + j < I && !(S[j] >= 0x1p-64f && S[j] <= 0x1p64f);
+                        any_bad |= bad[j];
+                    }
+                    if (__builtin_expect(any_bad, 0)) {  // re-shift the block's out-of-range rows
+                        float M[BR];
 #pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                const f2 i2 = pk(inv[2 * q], inv[2 * q + 1]);
+                        for (int j = 0; j < BR; ++j) M[j] = -INFINITY;
 #pragma unroll
-                for (int k = 0; k < NCB; ++k) {
-                    if constexpr (WIDE) {
-                        float p0, p1;
-                        upk(p[q][k], p0, p1);
-                        csw[k] = fmaf(p1, inv[2 * q + 1], fmaf(p0, inv[2 * q], csw[k]));
-                    } else {
-                        cs2[k] = fma2(p[q][k], i2, cs2[k]);
+                        for (int k = 0; k < NCB; ++k) {
+                            if (EXACT || k < nc) {
+                                const float gkk = gscal(k);
+                                f2 c[NP];
+                                RBk::load(cb + k * LDS, c);
+#pragma unroll
+                                for (int q = 0; q < NP; ++q) {
+                                    float c0, c1;
+                                    upk(c[q], c0, c1);
+                                    M[2 * q] = fmaxf(M[2 * q], gkk - c0);
+                                    M[2 * q + 1] = fmaxf(M[2 * q + 1], gkk - c1);
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int j = 0; j < BR; ++j) M[j] = bad[j] ? M[j] : 0.f;
+#pragma unroll
+                        for (int q = 0; q < NP; ++q) S2[q] = 0ull;
+#pragma unroll
+                        for (int k = 0; k < NCB; ++k) {
+                            if (EXACT || k < nc) {
+                                f2 c[NP];
+                                RBk::load(cb + k * LDS, c);
+                                float v[BR];
+#pragma unroll
+                                for (int q = 0; q < NP; ++q) {
+                                    upk(c[q], v[2 * q], v[2 * q + 1]);
+                                    v[2 * q] += M[2 * q];
+                                    v[2 * q + 1] += M[2 * q + 1];
+                                    float d0, d1;
+                                    upk(sub2(gpair(k), pk(v[2 * q], v[2 * q + 1])), d0, d1);
+                                    p[q][k] = pk(ex2(d0), ex2(d1));
+                                }
+                                RBk::store(cb + k * LDS, v);
+                            }
+#pragma unroll
+                            for (int q = 0; q < NP; ++q) S2[q] = add2(S2[q], p[q][k]);
+                        }
+#pragma unroll
+                        for (int q = 0; q < NP; ++q) upk(S2[q], S[2 * q], S[2 * q + 1]);
                     }
                 }
-            }
-            if (last) {  // impacts: r(u,i) sum_{k<K} e_k x_ik for the block's rows
-                float w[BR];
+                float inv[BR];
 #pragma unroll
-                for (int j = 0; j < BR; ++j) w[j] = 0.f;
+                for (int j = 0; j < BR; ++j) inv[j] = rb + j < I ? rcp_approx(S[j]) : 0.f;
 #pragma unroll
-                for (int k = 0; k < NCB; ++k) {
-                    if (k < a.K) {
-                        const float ek = s.e[k];
+                for (int q = 0; q < NP; ++q) {
+                    const f2 i2 = pk(inv[2 * q], inv[2 * q + 1]);
 #pragma unroll
-                        for (int q = 0; q < NP; ++q) {
+                    for (int k = 0; k < NCB; ++k) {
+                        if constexpr (WIDE) {
                             float p0, p1;
                             upk(p[q][k], p0, p1);
-                            w[2 * q] += ek * p0;
-                            w[2 * q + 1] += ek * p1;
+                            csw[k] = fmaf(p1, inv[2 * q + 1], fmaf(p0, inv[2 * q], csw[k]));
+                        } else {
+                            cs2[k] = fma2(p[q][k], i2, cs2[k]);
                         }
                     }
                 }
-                float* pp = a.part + (size_t)blockIdx.x * ld + rb;
-                f2 rr[NP], acc[NP];
-                RBk::load(a.r + (size_t)u * ld + rb, rr);
-                if (u == (int)blockIdx.x) {
+                if (last) {  // impacts: r(u,i) sum_{k<K} e_k x_ik for the block's rows
+                    float w[BR];
 #pragma unroll
-                    for (int q = 0; q < NP; ++q) acc[q] = 0ull;
-                } else {
-                    RBk::load(pp, acc);
-                }
-                float v[BR];
+                    for (int j = 0; j < BR; ++j) w[j] = 0.f;
 #pragma unroll
-                for (int q = 0; q < NP; ++q) {
-                    float r0, r1, a0, a1;
-                    upk(rr[q], r0, r1);
-                    upk(acc[q], a0, a1);
-                    v[2 * q] = a0 + r0 * (w[2 * q] * inv[2 * q]);
-                    v[2 * q + 1] = a1 + r1 * (w[2 * q + 1] * inv[2 * q + 1]);
+                    for (int k = 0; k < NCB; ++k) {
+                        if (k < a.K) {
+                            const float ek = s.e[k];
+#pragma unroll
+                            for (int q = 0; q < NP; ++q) {
+                                float p0, p1;
+                                upk(p[q][k], p0, p1);
+                                w[2 * q] += ek * p0;
+                                w[2 * q + 1] += ek * p1;
+                            }
+                        }
+                    }
+                    float* pp = a.part + (size_t)blockIdx.x * ld + rb;
+                    f2 rr[NP], acc[NP];
+                    RBk::load(a.r + (size_t)u * ld + rb, rr);
+                    if (u == (int)blockIdx.x) {
+#pragma unroll
+                        for (int q = 0; q < NP; ++q) acc[q] = 0ull;
+                    } else {
+                        RBk::load(pp, acc);
+                    }
+                    float v[BR];
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) {
+                        float r0, r1, a0, a1;
+                        upk(rr[q], r0, r1);
+                        upk(acc[q], a0, a1);
+                        v[2 * q] = a0 + r0 * (w[2 * q] * inv[2 * q]);
+                        v[2 * q + 1] = a1 + r1 * (w[2 * q + 1] * inv[2 * q + 1]);
+                    }
+                    RBk::store(pp, v);
                 }
-                RBk::store(pp, v);
             }
-        }
+        };
+        if (__builtin_expect(lg, 0))
+            sweep(BoolTag<false>{});
+        else
+            sweep(BoolTag<true>{});
         float cs[NCB];
 #pragma unroll
         for (int k = 0; k < NCB; ++k) {

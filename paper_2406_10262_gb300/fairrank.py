@@ -75,6 +75,7 @@ def lib():
             "fr_measure_ex2_rate": (i32, [_dp]),
             "fr_time_kernels": (i32, [_vp, i32, _dp]),
             "fr_kernel_variant": (i32, [_vp, ct.POINTER(i32)]),
+            "fr_sweep_stats": (i32, [_vp, ct.POINTER(i64)]),
             "fr_batch_create": (i32, [ct.POINTER(Config), i32, _vp, ct.POINTER(_vp)]),
             "fr_batch_destroy": (i32, [_vp]),
             "fr_batch_reset": (i32, [_vp]),
@@ -284,6 +285,12 @@ class FairRank:
         self._check(lib().fr_kernel_variant(self.h, o))
         return {"n_cols_kernel": o[0], "rows_per_thread": o[1], "exact": bool(o[2]),
                 "threads": o[3], "tile_stride": o[4], "grid": o[5]}
+
+    def log_form_solves(self) -> int:
+        """Tile-sweep solves since the last reset that finished in the log form (fr_sweep_stats)."""
+        o = ct.c_int64()
+        self._check(lib().fr_sweep_stats(self.h, ct.byref(o)))
+        return o.value
 
 
 class FairRankBatch:

@@ -199,17 +199,21 @@ def test_full_size_plain_workload_sampled_parity():
     assert rel(Fg[0], Fo[0]) < NSW_RTOL
     x0 = g.policy(1234, 1)[0]
     np.testing.assert_allclose(x0, o.policy(1234, 1)[0], atol=X_ATOL)
+    # warm-started solves keep the tile sweep's exponential form throughout
+    assert g.kernel_variant()["tile_stride"] > 0 and g.log_form_solves() == 0
 
 
 def _rows_leaving_range(C, b, eps, L):
     """How often a row's sum S_i of the fused log2-domain iteration (row shifts fixed at a cold
-    start) leaves [2^-64, 2^64] during an L-iteration solve, in FP64: the inputs below must reach
-    the exact re-shift branch of the sweeps."""
+    start) leaves [2^-64, 2^64] during an L-iteration solve, and the largest drift |g'_k - g'_k(0)|
+    of a column potential, in FP64: the inputs below must reach the exact re-shift branch of the
+    sweeps, and (drift beyond 30 log2 units) the tile sweep's switch to its log form."""
     cp = C / (eps * np.log(2.0))
     g = np.zeros(C.shape[1])
     ct = cp + (g - cp).max(1)[:, None]
-    n = 0
+    n, drift = 0, 0.0
     for _ in range(L):
+        drift = max(drift, float(np.abs(g).max()))
         p = np.exp2(g - ct)
         S = p.sum(1)
         bad = (S < 2.0 ** -64) | (S > 2.0 ** 64)
@@ -219,7 +223,7 @@ def _rows_leaving_range(C, b, eps, L):
             p = np.exp2(g - ct)
             S = p.sum(1)
         g -= np.log2((p / S[:, None]).sum(0) / b)
-    return n
+    return n, drift
 
 
 @pytest.mark.parametrize("I,K,scale", [
@@ -246,12 +250,18 @@ def test_rows_leaving_the_exponent_range_are_reshifted(I, K, scale):
     g, o = pair(U, I, K, r, epsilon=eps, sinkhorn_iters=L, warm_start=0)
     C, m1, m2, gg = seeded_state(U, I, K, seed=21, scale=scale)
     b, _ = oracle.marginals(I, K, synth.dcg_exposure(K))
-    assert sum(_rows_leaving_range(C[u].astype(np.float64), b, eps, L) for u in range(U)) > 0
+    ranges = [_rows_leaving_range(C[u].astype(np.float64), b, eps, L) for u in range(U)]
+    assert sum(n for n, _ in ranges) > 0
+    assert min(d for _, d in ranges) > 60.0  # every consumer drifts well past 30 log2 units
     g.set_state(C, m1, m2, gg, t=0)
     o.set_state(C.astype(np.float64), m1.astype(np.float64), m2.astype(np.float64),
                 gg.astype(np.float64), 0)
     tol = 4.0 * float(np.abs(C).max()) / (eps * np.log(2.0)) * 2.0 ** -24
     imp, _, F = g.impacts()
+    # the tile sweep leaves its exponential form in every consumer's solve; the register sweep
+    # has only the log form
+    tiled = g.kernel_variant()["tile_stride"] > 0
+    assert g.log_form_solves() == (U if tiled else 0)
     oimp, _, oF = o.impacts()
     assert rel(F, oF) < NSW_RTOL
     np.testing.assert_allclose(imp, oimp, rtol=tol)
