@@ -240,13 +240,15 @@ FR_API fr_status fr_time_kernels(fr_ctx* ctx, int32_t n_steps, double* ms);
    grid size. FR_EINVAL if ctx or out is NULL. */
 FR_API fr_status fr_kernel_variant(const fr_ctx* ctx, int32_t* out);
 
-/* Diagnostics of the free-cost tile sweep (out[4] of fr_kernel_variant > 0): writes the number of
-   consumer solves since the last fr_reset that left the sweep's exponential form (the row-shifted
-   kernel 2^(g'_k - c~_ik) held in shared memory, one multiply per cell) for its log form (one
-   exp2 per cell), because a column potential drifted more than 30 log2 units from its value at
-   the start of the solve. Warm-started ascent steps stay in the exponential form; cold starts
-   from widely spread costs leave it. Always 0 for the register sweep and FR_PARAM_ITEM.
-   Synchronises with ctx's work. FR_EINVAL if ctx or out is NULL. */
+/* Diagnostics of the free-cost Sinkhorn sweeps: writes the number of consumer solves since the
+   last fr_reset that left the sweep's exponential form (the row-shifted kernel 2^(g'_k - c~_ik)
+   held in shared memory or registers, one multiply per cell) for its log form (one exp2 per
+   cell), because a column potential drifted more than 30 log2 units from its value at the start
+   of the solve. Warm-started ascent steps stay in the exponential form; cold starts from widely
+   spread costs leave it. Kernels with the exponential form: the tile sweep (out[4] of
+   fr_kernel_variant > 0) and the register sweep of at most 11 columns; the wider register sweeps
+   and FR_PARAM_ITEM always report 0. Synchronises with ctx's work. FR_EINVAL if ctx or out is
+   NULL. */
 FR_API fr_status fr_sweep_stats(fr_ctx* ctx, int64_t* log_form_solves);
 
 /* Measures the sustained rate of ex2.approx.f32 on the current device with a dependent-chain-free

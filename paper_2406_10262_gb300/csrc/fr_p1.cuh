@@ -907,11 +907,29 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
         constexpr bool PEEL = NCB <= 11;
         if constexpr (PAIR) {
             constexpr int RP = R / 2;
+            // Up to 11 columns the pairs start in the exponential form of the tile sweep (E pairs in
+            // c2, G_k = 2^(g'_k - g0_k) per iteration, one packed multiply per two cells) and switch
+            // to the log form (c~ pairs rebuilt from the costs in global memory at the current g')
+            // when a potential drifts past TS_DRIFT; wider buckets keep the log form throughout.
+            constexpr bool EXPF_OK = NCB <= 11;
+            float g0m[GPL];  // g' at the start of the solve (this lane's columns)
+#pragma unroll
+            for (int j = 0; j < GPL; ++j) g0m[j] = gm[j];
             f2 c2[RP][NCB];
+            {
+                float gk[NCB];
+                bcast_g<NCB, GPL>(gm, gk);
 #pragma unroll
-            for (int rp = 0; rp < RP; ++rp)
+                for (int rp = 0; rp < RP; ++rp)
 #pragma unroll
-                for (int k = 0; k < NCB; ++k) c2[rp][k] = pk(c[2 * rp][k], c[2 * rp + 1][k]);
+                    for (int k = 0; k < NCB; ++k) {
+                        if constexpr (EXPF_OK)  // rows and columns outside the tile: c~ = inf, E = 0
+                            c2[rp][k] = pk(ex2(gk[k] - c[2 * rp][k]), ex2(gk[k] - c[2 * rp + 1][k]));
+                        else
+                            c2[rp][k] = pk(c[2 * rp][k], c[2 * rp + 1][k]);
+                    }
+            }
+            bool lg = !EXPF_OK;  // c2 holds the log form (the same in every thread of the CTA)
             auto iteration = [&](int l, auto tag) {
                 const bool last = last_of(tag);
                 if (last && warp == 0) {
@@ -919,75 +937,140 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
                     for (int j = 0; j < GPL; ++j)
                         if (j * 32 + lane < nc) a.gP[(size_t)u * nc + j * 32 + lane] = gm[j];
                 }
-                f2 g2[NCB];
-                {
-                    float gk[NCB];
-                    bcast_g<NCB, GPL>(gm, gk);
+                if constexpr (EXPF_OK) {
+                    if (!lg) {
+                        bool far = false;
 #pragma unroll
-                    for (int k = 0; k < NCB; ++k) g2[k] = pk(gk[k], gk[k]);
+                        for (int j = 0; j < GPL; ++j)
+                            if (j * 32 + lane < nc) far |= !(fabsf(gm[j] - g0m[j]) <= TS_DRIFT);
+                        if (__builtin_expect(__any_sync(FULL, far), 0)) {  // rebuild in the log form
+                            lg = true;
+                            if (tid == 0) atomicAdd(&a.st->log_solves, 1ull);
+                            float gk[NCB];
+                            bcast_g<NCB, GPL>(gm, gk);
+                            float cc[R][NCB];
+#pragma unroll
+                            for (int k = 0; k < NCB; ++k) {
+                                float tmp[R];
+#pragma unroll
+                                for (int r = 0; r < R; ++r) tmp[r] = 0.f;
+                                if ((EXACT || k < nc) && any_row) ldv<R>(tmp, a.C + tile + (size_t)k * ld + i0);
+#pragma unroll
+                                for (int r = 0; r < R; ++r) cc[r][k] = tmp[r];
+                            }
+#pragma unroll
+                            for (int r = 0; r < R; ++r) {
+                                float M = 0.f;
+                                if (vr[r]) {
+                                    M = -INFINITY;
+#pragma unroll
+                                    for (int k = 0; k < NCB; ++k)
+                                        if (EXACT || k < nc) M = fmaxf(M, gk[k] - cc[r][k] * sc);
+                                }
+#pragma unroll
+                                for (int k = 0; k < NCB; ++k)
+                                    cc[r][k] = (vr[r] && (EXACT || k < nc)) ? cc[r][k] * sc + M : INFINITY;
+                            }
+#pragma unroll
+                            for (int rp = 0; rp < RP; ++rp)
+#pragma unroll
+                                for (int k = 0; k < NCB; ++k) c2[rp][k] = pk(cc[2 * rp][k], cc[2 * rp + 1][k]);
+                        }
+                    }
                 }
                 f2 cs2[NCB];
 #pragma unroll
                 for (int k = 0; k < NCB; ++k) cs2[k] = 0ull;
+                auto sweep = [&](auto form) {
+                    constexpr bool EXPF = decltype(form)::value;
+                    f2 g2[NCB];  // (G_k, G_k) in the exponential form, (g'_k, g'_k) in the log form
+                    {
+                        float gk[NCB];
+                        if constexpr (EXPF) {
+                            float Gm[GPL];
 #pragma unroll
-                for (int rp = 0; rp < RP; ++rp) {
-                    const bool v0 = vr[2 * rp], v1 = vr[2 * rp + 1];
-                    f2 p2[NCB];
-                    f2 S2 = 0ull;
-#pragma unroll
-                    for (int k = 0; k < NCB; ++k) {
-                        float d0, d1;
-                        upk(sub2(g2[k], c2[rp][k]), d0, d1);
-                        p2[k] = pk(ex2(d0), ex2(d1));
-                        S2 = add2(S2, p2[k]);
-                    }
-                    float S0, S1;
-                    upk(S2, S0, S1);
-                    const bool bad0 = v0 && !(S0 >= 0x1p-64f && S0 <= 0x1p64f);
-                    const bool bad1 = v1 && !(S1 >= 0x1p-64f && S1 <= 0x1p64f);
-                    if (bad0 || bad1) {  // re-shift the pair's rows exactly
-                        float M0 = -INFINITY, M1 = -INFINITY;
-#pragma unroll
-                        for (int k = 0; k < NCB; ++k) {
-                            if (EXACT || k < nc) {
-                                float gkk, gdup, c0, c1;
-                                upk(g2[k], gkk, gdup);
-                                upk(c2[rp][k], c0, c1);
-                                M0 = fmaxf(M0, gkk - c0);
-                                M1 = fmaxf(M1, gkk - c1);
-                            }
+                            for (int j = 0; j < GPL; ++j) Gm[j] = ex2(gm[j] - g0m[j]);
+                            bcast_g<NCB, GPL>(Gm, gk);
+                        } else {
+                            bcast_g<NCB, GPL>(gm, gk);
                         }
-                        const f2 M2 = pk(bad0 ? M0 : 0.f, bad1 ? M1 : 0.f);
-                        S2 = 0ull;
+#pragma unroll
+                        for (int k = 0; k < NCB; ++k) g2[k] = pk(gk[k], gk[k]);
+                    }
+#pragma unroll
+                    for (int rp = 0; rp < RP; ++rp) {
+                        const bool v0 = vr[2 * rp], v1 = vr[2 * rp + 1];
+                        f2 p2[NCB];
+                        f2 S2 = 0ull;
 #pragma unroll
                         for (int k = 0; k < NCB; ++k) {
-                            if (EXACT || k < nc) c2[rp][k] = add2(c2[rp][k], M2);
-                            float d0, d1;
-                            upk(sub2(g2[k], c2[rp][k]), d0, d1);
-                            p2[k] = pk(ex2(d0), ex2(d1));
+                            if constexpr (EXPF) {
+                                p2[k] = mul2(c2[rp][k], g2[k]);
+                            } else {
+                                float d0, d1;
+                                upk(sub2(g2[k], c2[rp][k]), d0, d1);
+                                p2[k] = pk(ex2(d0), ex2(d1));
+                            }
                             S2 = add2(S2, p2[k]);
                         }
+                        float S0, S1;
                         upk(S2, S0, S1);
-                    }
-                    const float inv0 = v0 ? rcp_approx(S0) : 0.f;
-                    const float inv1 = v1 ? rcp_approx(S1) : 0.f;
-                    const f2 inv2 = pk(inv0, inv1);
+                        if constexpr (!EXPF) {
+                            const bool bad0 = v0 && !(S0 >= 0x1p-64f && S0 <= 0x1p64f);
+                            const bool bad1 = v1 && !(S1 >= 0x1p-64f && S1 <= 0x1p64f);
+                            if (bad0 || bad1) {  // re-shift the pair's rows exactly
+                                float M0 = -INFINITY, M1 = -INFINITY;
 #pragma unroll
-                    for (int k = 0; k < NCB; ++k) cs2[k] = fma2(p2[k], inv2, cs2[k]);
-                    if (last) {
-                        float w0 = 0.f, w1 = 0.f;
+                                for (int k = 0; k < NCB; ++k) {
+                                    if (EXACT || k < nc) {
+                                        float gkk, gdup, c0, c1;
+                                        upk(g2[k], gkk, gdup);
+                                        upk(c2[rp][k], c0, c1);
+                                        M0 = fmaxf(M0, gkk - c0);
+                                        M1 = fmaxf(M1, gkk - c1);
+                                    }
+                                }
+                                const f2 M2 = pk(bad0 ? M0 : 0.f, bad1 ? M1 : 0.f);
+                                S2 = 0ull;
 #pragma unroll
-                        for (int k = 0; k < NCB; ++k) {
-                            if (k < a.K) {
-                                float p0, p1;
-                                upk(p2[k], p0, p1);
-                                w0 += s.e[k] * p0;
-                                w1 += s.e[k] * p1;
+                                for (int k = 0; k < NCB; ++k) {
+                                    if (EXACT || k < nc) c2[rp][k] = add2(c2[rp][k], M2);
+                                    float d0, d1;
+                                    upk(sub2(g2[k], c2[rp][k]), d0, d1);
+                                    p2[k] = pk(ex2(d0), ex2(d1));
+                                    S2 = add2(S2, p2[k]);
+                                }
+                                upk(S2, S0, S1);
                             }
                         }
-                        acc_imp[2 * rp] += rr[2 * rp] * (w0 * inv0);
-                        acc_imp[2 * rp + 1] += rr[2 * rp + 1] * (w1 * inv1);
+                        const float inv0 = v0 ? rcp_approx(S0) : 0.f;
+                        const float inv1 = v1 ? rcp_approx(S1) : 0.f;
+                        const f2 inv2 = pk(inv0, inv1);
+#pragma unroll
+                        for (int k = 0; k < NCB; ++k) cs2[k] = fma2(p2[k], inv2, cs2[k]);
+                        if (last) {
+                            float w0 = 0.f, w1 = 0.f;
+#pragma unroll
+                            for (int k = 0; k < NCB; ++k) {
+                                if (k < a.K) {
+                                    float p0, p1;
+                                    upk(p2[k], p0, p1);
+                                    w0 += s.e[k] * p0;
+                                    w1 += s.e[k] * p1;
+                                }
+                            }
+                            acc_imp[2 * rp] += rr[2 * rp] * (w0 * inv0);
+                            acc_imp[2 * rp + 1] += rr[2 * rp + 1] * (w1 * inv1);
+                        }
                     }
+                };
+                if constexpr (EXPF_OK) {
+                    if (__builtin_expect(lg, 0))
+                        sweep(BoolTag<false>{});
+                    else
+                        sweep(BoolTag<true>{});
+                } else {
+                    sweep(BoolTag<false>{});
                 }
                 float cs[NCB];
 #pragma unroll

@@ -258,10 +258,9 @@ def test_rows_leaving_the_exponent_range_are_reshifted(I, K, scale):
                 gg.astype(np.float64), 0)
     tol = 4.0 * float(np.abs(C).max()) / (eps * np.log(2.0)) * 2.0 ** -24
     imp, _, F = g.impacts()
-    # the tile sweep leaves its exponential form in every consumer's solve; the register sweep
-    # has only the log form
-    tiled = g.kernel_variant()["tile_stride"] > 0
-    assert g.log_form_solves() == (U if tiled else 0)
+    # every consumer's solve leaves the sweep's exponential form (tile sweep, and the register
+    # sweep of at most 11 columns) for the log form
+    assert g.log_form_solves() == U
     oimp, _, oF = o.impacts()
     assert rel(F, oF) < NSW_RTOL
     np.testing.assert_allclose(imp, oimp, rtol=tol)
