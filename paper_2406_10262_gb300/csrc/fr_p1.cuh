@@ -808,9 +808,28 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
                                      : reinterpret_cast<const float4*>(s.r)[i4];
                 const float lv[4] = {l4.x, l4.y, l4.z, l4.w}, av[4] = {a4.x, a4.y, a4.z, a4.w};
                 const float wv[4] = {o4.x * r4.x, o4.y * r4.y, o4.z * r4.z, o4.w * r4.w};
+                // Adam moments two columns ahead (their loads would otherwise wait for the stores
+                // of the previous column: the compiler cannot tell the addresses apart)
+                constexpr bool ADAM = MODE == MODE_UPDATE_SWEEP;
+                const bool adam = ADAM && a.optimizer == 0;
+                const int ncc = EXACT ? NCB : nc;
+                float4 mA = make_float4(0.f, 0.f, 0.f, 0.f), vA = mA, mB = mA, vB = mA;
+                auto ldmv = [&](int k, float4& m, float4& v) {
+                    const size_t off = tile + (size_t)k * ld + i;
+                    m = *reinterpret_cast<const float4*>(m1g + off);
+                    v = *reinterpret_cast<const float4*>(m2g + off);
+                };
+                if (adam) {
+                    ldmv(0, mA, vA);
+                    if (1 < ncc) ldmv(1, mB, vB);
+                }
 #pragma unroll 4
                 for (int k = 0; k < NCB; ++k) {
                     if (!EXACT && k >= nc) break;
+                    const float4 mm4 = mA, vv4 = vA;
+                    mA = mB;
+                    vA = vB;
+                    if (adam && k + 2 < ncc) ldmv(k + 2, mB, vB);
                     const int qs = k * (lds / 4) + i4;  // float4 index in the shared tile
                     const float4 c4 = reinterpret_cast<const float4*>(s.C)[qs];
                     const float gpk = s.gp[k], ek = s.e[k], bk = s.beta[k];
@@ -833,8 +852,6 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
 #pragma unroll
                             for (int j = 0; j < 4; ++j) cv[j] += a.lr * gr[j];
                         } else {
-                            const float4 mm4 = *reinterpret_cast<const float4*>(m1g + off);
-                            const float4 vv4 = *reinterpret_cast<const float4*>(m2g + off);
                             float mm[4] = {mm4.x, mm4.y, mm4.z, mm4.w};
                             float vv[4] = {vv4.x, vv4.y, vv4.z, vv4.w};
 #pragma unroll
