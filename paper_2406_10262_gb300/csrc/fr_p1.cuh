@@ -7,20 +7,25 @@
 // consumer's Sinkhorn iterations run; in the tile sweep, whose solve keeps reading the tile, right
 // after the previous solve, from L2 where that solve prefetched it.
 //
-// Sinkhorn (Problem (7)) runs in the fused single-pass log-domain form, in log2 units
+// Sinkhorn (Problem (7)) runs as one fused pass per iteration, in log2 units
 // c' = c / (eps ln 2), g' = g / (eps ln 2):
 //   p_ik = 2^(g'_k - c~_ik),  S_i = sum_k p_ik,  x_ik = p_ik / S_i       (row update, Eq. 1)
 //   cs_k = sum_i x_ik,        g'_k += log2 b_k - log2 cs_k               (column update, Eq. 2)
 // which equals the textbook two-pass update (f_i = -eps LSE_k, g_k = eps log b_k - eps LSE_i)
-// algebraically and costs one exp2 per cell per iteration. In the register sweep a thread owns R
-// consecutive items (rows) and keeps their costs in registers for the whole solve; in the tile
-// sweep (tile_sweep below) it owns R / 2 pairs of rows and reads their costs from the resident
-// shared tile every iteration. c~_ik = c'_ik + shift_i carries
-// a per-row shift fixed at the start of the solve (the row max), so 2^(.) stays in range without
-// a max pass per iteration; a row whose S_i leaves [2^-64, 2^64] is re-shifted exactly.
+// algebraically. c~_ik = c'_ik + shift_i carries a per-row shift fixed at the start of the solve
+// (the row max), so 2^(.) stays in range without a max pass per iteration. In the register sweep
+// a thread owns R consecutive items (rows) and keeps their costs in registers for the whole solve;
+// in the tile sweep (tile_sweep below) it owns R / 2 pairs of rows and reads them from the
+// resident shared tile every iteration. Both sweeps (the register sweep up to 11 columns) hold
+// the row-shifted kernel in its exponential form, E_ik = 2^(g0_k - c~_ik) with g0 the potentials
+// at the start of the solve, and form p_ik = E_ik G_k with G_k = 2^(g'_k - g0_k): one multiply
+// per cell and one exp2 per column and iteration. While the potentials stay within TS_DRIFT of g0
+// this is the same iteration up to FP32 rounding; beyond that (and in the wider register sweeps
+// throughout) they use the log form, one exp2 per cell, re-shifting exactly a row whose S_i leaves
+// [2^-64, 2^64].
 //
-// Inner loop: two rows at a time in packed f32x2 arithmetic (one instruction per pair of cells),
-// one exp2 per cell on the MUFU. Column sums: per-warp reduce-scatter by shuffles, one
+// Inner loop: two rows at a time in packed f32x2 arithmetic (one instruction per pair of cells).
+// Column sums: per-warp reduce-scatter by shuffles, one
 // __syncthreads per iteration on double-buffered partials, after which every warp sums the
 // per-warp partials of its lanes' columns in the same fixed order and updates its own copy of the
 // column potentials (so no second barrier is needed and every warp holds identical g').
@@ -257,7 +262,8 @@ struct RowBlock {  // one load / store of a block's BR consecutive floats (8- or
 };
 
 // Largest drift |g'_k - g0_k| (log2 units) of a column potential from its value at the start of
-// the solve for which the tile sweep keeps its exponential form (below).
+// the solve for which the sweeps keep their exponential form (the tile sweep below, and the
+// register sweep of at most 11 columns in p1_kernel).
 constexpr float TS_DRIFT = 30.f;
 
 // Tile sweep: the Sinkhorn phase of consumer u with its costs read from the resident shared tile
@@ -296,8 +302,9 @@ __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u
     // Block b starts at row rb = BR (b T + tid); ld is a multiple of 8, so a block lies inside the
     // tile (rb < ld) or past it. Row j of the block is a consumer row if rb + j < I.
     //
-    // The row shifts of costs cb[k LDS] (BR rows, column k) at potentials gk; EXPF: then E in place
-    // of the costs at cd, else c~.
+    // Rows rb .. rb + BR - 1: reads their costs at cb + k cstride (column k; the shared tile, or the
+    // consumer's costs in global memory), shifts each row at potentials gk and writes to the tile
+    // at cd + k LDS either E (form BoolTag<true>) or c~ (BoolTag<false>).
     auto shift_rows = [&](const float* cb, int cstride, float* cd, int rb, const float (&gk)[NCB],
                           auto form) {
         constexpr bool EXPF = decltype(form)::value;
