@@ -163,11 +163,17 @@ __device__ __forceinline__ void stage_consumer(const P1Args& a, int un, int nc, 
     const unsigned tile = (unsigned)(sizeof(float) * (size_t)nc * ld);
     const unsigned row = (unsigned)(sizeof(float) * ld);
     fence_proxy_async_smem();
-    mbar_arrive_expect_tx(s.bar, ts ? tile : tile + row);
     if (ts) {
+        // a column slot of the tile holds ts floats, at least the item count rounded up to 8; a
+        // caller's row stride ld may be longer (the allocation-free entry point), and what lies
+        // beyond the slot is padding, so each column copies min(ld, ts) floats (a multiple of 8)
+        const int lc = ld < ts ? ld : ts;
+        const unsigned rowc = (unsigned)(sizeof(float) * lc);
+        mbar_arrive_expect_tx(s.bar, (unsigned)nc * rowc);
         for (int k = 0; k < nc; ++k)
-            bulk_g2s(s.C + (size_t)k * ts, a.C + ((size_t)un * nc + k) * ld, row, s.bar);
+            bulk_g2s(s.C + (size_t)k * ts, a.C + ((size_t)un * nc + k) * ld, rowc, s.bar);
     } else {
+        mbar_arrive_expect_tx(s.bar, tile + row);
         bulk_g2s(s.C, a.C + (size_t)un * nc * ld, tile, s.bar);
         bulk_g2s(s.r, a.r + (size_t)un * ld, row, s.bar);
     }

@@ -50,12 +50,12 @@ def via_context(U, I, K, r, C, L, eps):
     return imp, util, F
 
 
-def via_noalloc(torch, U, I, K, r, C, L, eps):
+def via_noalloc(torch, U, I, K, r, C, L, eps, ld=None, pad=0.0):
     m = fr.num_cols(I, K)
-    ld = (I + 7) // 8 * 8
-    Ck = np.zeros((U, m, ld), np.float32)
+    ld = ld or (I + 7) // 8 * 8
+    Ck = np.full((U, m, ld), pad, np.float32)
     Ck[:, :, :I] = C.transpose(0, 2, 1)
-    rk = np.zeros((U, ld), np.float32)
+    rk = np.full((U, ld), pad, np.float32)
     rk[:, :I] = r
     Cd = torch.from_numpy(Ck).cuda()
     rd = torch.from_numpy(rk).cuda()
@@ -84,6 +84,23 @@ def test_matches_fr_impacts_on_consecutive_calls(torch):
         elif (U, I, K) == cases[0][:3]:
             np.testing.assert_array_equal(imp, first[0])  # nothing left over from the call between
             assert F == first[1]
+
+
+@pytest.mark.parametrize("U,I,K,ld", [
+    (30, 1000, 10, 2048),  # tile sweep: 1024-float column slots, a longer caller row stride
+    (12, 300, 10, 512),    # register sweep: the staged tile takes the caller's stride
+])
+def test_row_stride_longer_than_the_items(torch, U, I, K, ld):
+    """A caller's row stride ld beyond the item count (allowed: a multiple of 8, >= n_items), with
+    garbage in the entries past n_items: the result equals the context's, which packs its rows at
+    the item count rounded up to 8."""
+    L, eps = 20, 1.0
+    r, C = problem(U, I, K, 5)
+    imp_ref, util_ref, F_ref = via_context(U, I, K, r, C, L, eps)
+    imp, util, F = via_noalloc(torch, U, I, K, r, C, L, eps, ld=ld, pad=7.0)
+    assert abs(F - F_ref) <= NSW_RTOL * abs(F_ref)
+    assert abs(util - util_ref) <= NSW_RTOL * abs(util_ref)
+    np.testing.assert_allclose(imp, imp_ref, rtol=NSW_RTOL)
 
 
 def test_rejects_problems_larger_than_the_static_scratch(torch):
