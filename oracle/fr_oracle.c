@@ -19,7 +19,13 @@
  *                       differences of the exact L-step map
  *   orc_adam / orc_sgd  torch.optim.Adam(maximize=True) / torch.optim.SGD in float64
  *   orc_step/orc_solve  monotone ascent under small-step SGD; F -> F* of brute force on tiny
- *                       instances; certificate >= F* - F
+ *                       instances; certificate >= F* - F; the stop rule of Algorithm 1: one step
+ *                       when the uniform policy is optimal (|U| = 1, separable r), every step at
+ *                       t = 0, and exactly j steps for a threshold between the j-th gradient norm
+ *                       and the smaller earlier ones (brute-force instances); the traced norm is
+ *                       that of orc_grad before the step
+ *   orc_grad (omega)    central differences of sum_i omega_i Imp_i for a random omega, both
+ *                       gradient modes, free costs and per-item variables, and in r
  *   orc_metrics         utility identity; envy and better/worse-off against brute force at the
  *                       optimum (envy-freeness, dominance over uniform) on small cases
  *   orc_certificate     bound checked against brute-force F*

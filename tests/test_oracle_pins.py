@@ -397,3 +397,134 @@ def test_item_parametrisation_cost_and_gradients():
             rm[u, i] -= h
             fd = (F_theta(theta, rp, L) - F_theta(theta, rm, L)) / (2 * h)
             assert abs(fd - dr[u, i]) < 1e-7 + 1e-6 * abs(fd)
+
+
+# ---- Algorithm 1's threshold loop -----------------------------------------------------------
+@pytest.mark.parametrize("kind", ["single", "separable"])
+def test_solve_stops_after_one_step_when_uniform_policy_is_optimal(kind):
+    """|U| = 1 or separable r: the uniform policy (C = 0) is optimal, so the gradient of the first
+    step is at rounding level and Algorithm 1 with t = 1e-12 stops after exactly one step, with F
+    equal to the uniform policy's closed form."""
+    I, K = 8, 3
+    if kind == "single":
+        U, r = 1, synth.relevance_uniform(1, I, 2) + 0.1
+    else:
+        U = 4
+        g = rng(4)
+        r = np.outer(g.uniform(0.2, 1, U), g.uniform(0.2, 1, I))
+    e = synth.dcg_exposure(K)
+    F_unif = np.log(r.sum(0) * e.sum() / I).sum()
+    for opt in (oracle.SGD, oracle.ADAM):
+        o = engine(U, I, K, r, optimizer=opt, lr=0.1)
+        done, F = o.solve(1e-12, 50)
+        assert done == 1
+        np.testing.assert_allclose(F, F_unif, rtol=1e-12)
+
+
+def test_solve_with_zero_threshold_runs_every_step():
+    """A non-separable market has a nonzero gradient at every iterate, so t = 0 never stops the
+    loop early: max_steps steps run (and max_steps = 0 runs none)."""
+    U, I, K = 3, 6, 2
+    r = synth.relevance_uniform(U, I, 6) + 0.05
+    o = engine(U, I, K, r)
+    done, F = o.solve(0.0, 17)
+    assert done == 17
+    _, gn = engine(U, I, K, r).step(17)
+    assert np.all(gn > 0)
+    o0 = engine(U, I, K, r)
+    done0, F0 = o0.solve(0.0, 0)
+    assert done0 == 0
+    np.testing.assert_allclose(F0, engine(U, I, K, r).impacts()[2], rtol=0)
+
+
+def test_step_trace_reports_the_norm_of_the_gradient_it_ascends():
+    """The norm tested by Algorithm 1's stop rule is ||dF/dC||_2 of the step's own gradient: each
+    entry of the step trace equals the norm of orc_grad (pinned by finite differences) taken at
+    the state before that step."""
+    U, I, K = 3, 5, 2
+    r = synth.relevance_uniform(U, I, 8) + 0.05
+    o = engine(U, I, K, r)
+    for _ in range(4):
+        d = o.grad()
+        _, gn = o.step(1)
+        np.testing.assert_allclose(gn[0], np.linalg.norm(d), rtol=1e-12)
+
+
+@pytest.mark.parametrize("U,I,seed", [(2, 3, 1), (3, 4, 4)])
+def test_solve_stops_at_the_first_step_below_threshold(U, I, seed):
+    """On brute-force instances (where the step trajectory reaches F*, pinned above): for a
+    threshold strictly between the gradient norm of step j and the smallest norm of the earlier
+    steps, solve(t) runs exactly j steps (1-based) and returns the F the step trajectory has
+    after step j. A stop tested before the update, or on the next step's norm, fails this."""
+    r = synth.relevance_uniform(U, I, seed)
+    bf = nsw_bruteforce(r, synth.dcg_exposure(I))
+    F_tr, gn = engine(U, I, I, r, lr=0.1, iters=50).step(400)
+    assert bf["F"] - F_tr[-1] < 1e-3 * (1 + abs(bf["F"]))
+    running_min = np.minimum.accumulate(gn)
+    records = [j for j in range(1, len(gn)) if gn[j] < running_min[j - 1]]
+    picks = sorted({records[0], records[len(records) // 2], records[-1]})
+    for j in picks:
+        t = 0.5 * (gn[j] + running_min[j - 1])
+        assert gn[j] <= t < running_min[j - 1]
+        done, F = engine(U, I, I, r, lr=0.1, iters=50).solve(t, 400)
+        assert done == j + 1
+        assert F == F_tr[j]
+
+
+# ---- gradient of a weighted impact sum (the backward of Imp) --------------------------------
+def imp_of(param_kind, P, r, e_pad, b, eps, L):
+    """Imp (Eq. 4) for all consumers from cold-started Sinkhorn solves of the oracle, for free
+    costs C [U, I, m] or per-item variables theta [I]."""
+    U, I = r.shape
+    imp = np.zeros(I)
+    for u in range(U):
+        if param_kind == "C":
+            cu = P[u]
+        else:
+            cu = -r[u][:, None] * e_pad[None, :] * np.exp(P)[:, None]
+        x, _, _ = oracle.sinkhorn(cu, b, eps, L)
+        imp += r[u] * (x @ e_pad)
+    return imp
+
+
+@pytest.mark.parametrize("param_kind", ["C", "theta"])
+@pytest.mark.parametrize("mode,L", [(oracle.GRAD_IMPLICIT, 3000), (oracle.GRAD_UNROLLED, 9)])
+def test_omega_weighted_gradient_matches_finite_differences(param_kind, mode, L):
+    """orc_grad with an explicit omega is the gradient of L = sum_i omega_i Imp_i (not of F):
+    central differences of that sum for a random omega, in the parameters and in r."""
+    U, I, K = 3, 6, 2
+    eps = 1.0 if param_kind == "theta" else 0.8
+    r = synth.relevance_uniform(U, I, 31) + 0.05
+    e = synth.dcg_exposure(K)
+    b, e_pad = oracle.marginals(I, K, e)
+    g = rng(77)
+    omega = g.uniform(-1.0, 2.0, size=I)
+    if param_kind == "C":
+        P = g.normal(size=(U, I, len(b))) * 0.6
+        o = oracle.Oracle(U, I, K, param=oracle.PARAM_FULL_C, epsilon=eps, iters=L,
+                          warm_start=False, grad_mode=mode)
+    else:
+        P = g.normal(size=I) * 0.5
+        o = oracle.Oracle(U, I, K, param=oracle.PARAM_ITEM, iters=L, warm_start=False,
+                          grad_mode=mode)
+    o.set_relevance(r)
+    o.set_exposure(e)
+    o.set_state(param=P)
+    dP, dr = o.grad(omega=omega, want_dr=True)
+    dP_F = o.grad()
+    assert np.abs(dP - dP_F).max() > 1e-3  # omega is not 1/Imp: the two gradients differ
+    Lw = lambda PP, rr: omega @ imp_of(param_kind, PP, rr, e_pad, b, eps, L)
+    h = 1e-5
+    coords = [tuple(g.integers(0, s) for s in P.shape) for _ in range(8)]
+    for j in coords:
+        Pp, Pm = P.copy(), P.copy()
+        Pp[j] += h
+        Pm[j] -= h
+        fd = (Lw(Pp, r) - Lw(Pm, r)) / (2 * h)
+        assert abs(fd - dP[j]) < 1e-7 + 1e-6 * abs(fd), (j, fd, dP[j])
+    for (u, i) in [(0, 0), (1, 3), (2, 5)]:
+        rp, rm = r.copy(), r.copy()
+        rp[u, i] += h
+        rm[u, i] -= h
+        fd = (Lw(P, rp) - Lw(P, rm)) / (2 * h)
+        assert abs(fd - dr[u, i]) < 1e-7 + 1e-6 * abs(fd), ((u, i), fd, dr[u, i])
