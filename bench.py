@@ -41,11 +41,24 @@ METRIC = "time-to-NSW (rel err≤1e-5 vs FP64) & Sinkhorn cell-updates/s vs roof
 UNIT = "cell-updates/s"
 NSW_TOL = 1e-5
 SMS_NOMINAL, SM_MAX_MHZ = 152, 2070.0
-# Cell-updates per clock per SM that bound the Sinkhorn sweep: each cell-update reads one 4-byte
-# entry of the shared tile (the exponential form's E_ik, or the log form's c~_ik), and an SM loads
-# 128 B/clk from shared memory. The log form's other bound, ex2 on the MUFU (32 results per clock
-# per SM on Blackwell Ultra, measured by the microbenchmark below), is the same number.
-CELLS_PER_CLK_SM = 128 // 4
+# The Sinkhorn sweep's on-chip bound: each cell-update reads one 4-byte entry of the shared tile
+# (the exponential form's E_ik, or the log form's c~_ik), at the shared-memory load bandwidth that
+# fr_measure_peaks measures with the sweep's 8-byte conflict-free loads (nominally 128 B/clk/SM,
+# 32 cell-updates per clock per SM). The bound the method's statement names -- the slower of the
+# HBM bytes at the measured copy bandwidth and the MUFU operations (one ex2 per cell-update plus
+# one rcp per row and one lg2 per column, (1 + 2/m) per cell-update) at the measured ex2 rate --
+# is reported beside it.
+CELL_BYTES_SMEM = 4
+HBM_FALLBACK_GBS = 6800.0
+
+
+def hbm_peak_gbs():
+    """Measured copy bandwidth (MEASURED_PEAKS.json), else the fallback figure; and its source."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return HBM_FALLBACK_GBS, "fallback"
 
 
 def p1_kernel_name(g):
@@ -152,14 +165,15 @@ class Clocks:
 
 
 # ---- the oracle (CPU baseline and reference arm) --------------------------------------------
-def oracle_sample(w, seed, budget_s, min_steps=1):
+def oracle_sample(w, seed, budget_s, min_steps=1, threads=None, n_sub=200):
     """Times the FP64 oracle on a sub-market of the workload (first n_sub consumers, all items)
-    until `budget_s` of CPU time: initial solve plus ascent steps. Returns (cell-updates/s, info)."""
+    until `budget_s` of CPU time: initial solve plus ascent steps, on `threads` host threads (all
+    cores by default). Returns (cell-updates/s, info, seconds)."""
     import oracle
     from paper_2406_10262_gb300 import synth
-    n_sub = max(1, min(w["n_users"], 200))
+    n_sub = max(1, min(w["n_users"], n_sub))
     r = synth.relevance_lowrank(w["n_users"], w["n_items"], seed=seed, rows=n_sub)
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     o = oracle.Oracle(n_sub, w["n_items"], w["n_slots"], iters=w["iters"], lr=0.1, threads=cores)
     o.set_relevance(r.astype(np.float32).astype(np.float64))
     o.set_exposure(synth.dcg_exposure(w["n_slots"]))
@@ -339,18 +353,35 @@ def run_ours(args, w):
     kms = g.time_kernels(20)
     cu_alg = float(cells) * L  # one cell-update per cell per Sinkhorn iteration
     achieved = cu_alg / (kms[0] * 1e-3)
-    ex2_measured = fr.measure_ex2_rate()
-    peak_nominal = SMS_NOMINAL * CELLS_PER_CLK_SM * SM_MAX_MHZ * 1e6
+    peaks = fr.measure_peaks()
+    peak_smem = peaks["smem_bytes_per_s_8B"] / CELL_BYTES_SMEM  # cell-updates/s
     bytes_alg = cells * 4 * 6 + U * I * 4  # read C, m, v + write C, m, v; read r
+    hbm_gbs, hbm_src = hbm_peak_gbs()
+    t_hbm = bytes_alg / (hbm_gbs * 1e9)
+    t_mufu = cu_alg * (1.0 + 2.0 / nc) / peaks["ex2_per_s"]
+    t_roof = max(t_hbm, t_mufu)
     roof = {"bound": "alu", "unit": "Gcell-updates/s", "achieved": achieved / 1e9,
-            "peak": peak_nominal / 1e9, "frac": achieved / peak_nominal,
+            "peak": peak_smem / 1e9, "frac": achieved / peak_smem,
             "traffic": recorded_traffic(p1_kernel_name(g)),
             "kernel": p1_kernel_name(g), "kernel_ms": kms[0], "reduce_ms": kms[1],
-            "sweep_only_ms": kms[2], "sweep_only_frac": cu_alg / (kms[2] * 1e-3) / peak_nominal,
+            "sweep_only_ms": kms[2], "sweep_only_frac": cu_alg / (kms[2] * 1e-3) / peak_smem,
             "cell_updates_per_launch": cu_alg,
-            "peak_source": f"nominal {SMS_NOMINAL} SMs x {CELLS_PER_CLK_SM} cell-updates/clk "
-            f"(128 B/clk of shared-memory loads, 4 B per cell-update) x {SM_MAX_MHZ:.0f} MHz",
-            "ex2_microbench": ex2_measured / 1e9,
+            "peak_source": "measured shared-memory load bandwidth (fr_measure_peaks, 8-byte "
+            f"conflict-free loads: {peaks['smem_bytes_per_s_8B'] / 1e12:.2f} TB/s at "
+            f"{peaks['sm_mhz']:.0f} MHz) / 4 B per cell-update",
+            "method_bound": {
+                "what": "slower of HBM bytes at the measured copy bandwidth and (1 + 2/m) MUFU "
+                        "operations per cell-update at the measured ex2 rate",
+                "bound": "mufu" if t_mufu >= t_hbm else "hbm", "t_roof_ms": t_roof * 1e3,
+                "t_mufu_ms": t_mufu * 1e3, "t_hbm_ms": t_hbm * 1e3, "hbm_peak_gbs": hbm_gbs,
+                "hbm_peak_source": hbm_src, "frac": t_roof / (kms[0] * 1e-3),
+                "sweep_only_frac": t_mufu / (kms[2] * 1e-3)},
+            "measured_peaks": {"ex2_per_s": peaks["ex2_per_s"],
+                               "smem_bytes_per_s_8B": peaks["smem_bytes_per_s_8B"],
+                               "smem_bytes_per_s_16B": peaks["smem_bytes_per_s_16B"],
+                               "ffma_per_s": peaks["ffma_per_s"],
+                               "ffma2_fmas_per_s": peaks["ffma2_fmas_per_s"],
+                               "sm_mhz": peaks["sm_mhz"]},
             "log_form_solves": g.log_form_solves(),
             "hbm_bytes_per_launch": bytes_alg, "hbm_gbs": bytes_alg / (kms[0] * 1e-3) / 1e9}
 
@@ -368,6 +399,9 @@ def run_ours(args, w):
         rate, info, _ = oracle_sample(w, seed=0, budget_s=12.0)
         info["value"] = rate
         info["unit"] = UNIT
+        rate1, info1, _ = oracle_sample(w, seed=0, budget_s=6.0, threads=1, n_sub=40)
+        info["single_thread"] = {"value": rate1, "unit": UNIT, "cores": 1,
+                                 "sample": info1["sample"]}
         line["cpu_baseline"] = info
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -74,7 +74,14 @@ typedef struct fr_config {
     int32_t optimizer;      /* FR_ADAM (PyTorch Adam, maximize) | FR_SGD */
     double  lr, beta1, beta2, adam_eps;
     int32_t rel_dtype;      /* storage of r on the device: FR_F32 | FR_BF16 */
-    int32_t reserved[7];    /* must be zero */
+    int32_t max_wait_polls; /* polls a bounded device-side wait makes (the wait of a kernel for its
+                               staged bulk copies, and of the envy contraction for its tensor-core
+                               work) before it gives up: the kernel then records FR_ETIMEOUT, waits
+                               for its own copies in flight with the default bound and stops, so
+                               the CUDA context stays usable. 0: the default (2^26 polls, many
+                               seconds); -1: no poll at all, every such wait expires at once (for
+                               testing the failure path); other negative values: FR_EINVAL */
+    int32_t reserved[6];    /* must be zero */
 } fr_config;
 
 /* Fills cfg with the defaults: epsilon 1, L = 50, warm start, implicit gradient, checkpoint every
@@ -168,6 +175,11 @@ FR_API fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, dou
    max_{u,k} |sum_i x_uik - b_k|, reported beside it. Needs e non-increasing for the bound. */
 FR_API fr_status fr_certificate(fr_ctx* ctx, double* gap, double* col_residual);
 
+/* Replaces ctx's max_wait_polls (see fr_config; 0 restores the default). After an FR_ETIMEOUT the
+   optimiser state is undefined: fr_reset, or fr_set_state, brings the context back to a defined
+   state. FR_EINVAL for a value below -1. */
+FR_API fr_status fr_set_wait_limit(fr_ctx* ctx, int32_t max_wait_polls);
+
 /* Message of the last failing call on ctx (or of the last failing fr_create on this thread when
    ctx is NULL). Valid until the next call on ctx. */
 FR_API const char* fr_last_error(const fr_ctx* ctx);
@@ -255,6 +267,16 @@ FR_API fr_status fr_sweep_stats(fr_ctx* ctx, int64_t* log_form_solves);
    microbenchmark (grid = SMs x 4 CTAs): writes exp2 evaluations per second. Used as the measured
    denominator of the Sinkhorn roofline. */
 FR_API fr_status fr_measure_ex2_rate(double* ex2_per_second);
+
+/* Measures the on-chip rates that bound the Sinkhorn sweeps on the current device (each probe one
+   launch of SMs x 4 or 8 CTAs, timed with CUDA events after a warm-up launch) and writes the first
+   n of: out[0] ex2.approx.f32 results per second; out[1] shared-memory load bandwidth in bytes per
+   second with 8-byte loads and out[2] with 16-byte loads (consecutive lanes, conflict-free: the
+   sweeps' access pattern); out[3] FP32 fused multiply-adds per second (scalar fma.rn.f32) and
+   out[4] with packed fma.rn.f32x2 (two per instruction); out[5] the SM clock in MHz during the
+   probes (clock64 cycles over global-timer nanoseconds, median of the probes). These are the
+   measured denominators of the rooflines the benchmark reports. 1 <= n <= 6, else FR_EINVAL. */
+FR_API fr_status fr_measure_peaks(double* out, int32_t n);
 
 /* ---- allocation-free evaluation --------------------------------------------------------- */
 

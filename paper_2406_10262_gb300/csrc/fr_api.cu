@@ -113,6 +113,7 @@ P1Args p1_args(fr_ctx* c) {
     a.adam_eps = (float)c->cfg.adam_eps;
     a.optimizer = c->cfg.optimizer == FR_SGD ? 1 : 0;
     a.warm = c->cfg.warm_start ? 1 : 0;
+    a.max_polls = polls_of(c->cfg.max_wait_polls);
     return a;
 }
 
@@ -127,6 +128,7 @@ P2Args p2_args(fr_ctx* c, float* part) {
     a.inv_eps = (float)(1.0 / c->cfg.epsilon);
     a.warm = c->cfg.warm_start ? 1 : 0;
     a.ck = c->ck; a.ce = c->ce; a.nck = c->nck;
+    a.max_polls = polls_of(c->cfg.max_wait_polls);
     return a;
 }
 
@@ -457,8 +459,10 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
         return fail(nullptr, FR_EINVAL, "rel_dtype must be FR_F32 or FR_BF16");
     if (c.param == FR_PARAM_FULL_C && c.rel_dtype != FR_F32)
         return fail(nullptr, FR_EUNSUPPORTED, "FR_PARAM_FULL_C stores relevance in FP32");
-    for (int j = 0; j < 7; ++j)
+    for (int j = 0; j < 6; ++j)
         if (c.reserved[j]) return fail(nullptr, FR_EINVAL, "reserved fields must be zero");
+    if (c.max_wait_polls < -1)
+        return fail(nullptr, FR_EINVAL, "max_wait_polls must be >= -1 (got %d)", c.max_wait_polls);
 
     const int nc = fr_num_cols(c.n_items, c.n_slots);
     const bool p2 = c.param == FR_PARAM_ITEM;
@@ -795,8 +799,7 @@ fr_status fr_grad(fr_ctx* ctx, const float* omega, float* dparam, float* dr, int
         CU(cudaMemcpyAsync(dparam, dP, sizeof(float) * nP, cudaMemcpyDeviceToHost, ctx->s));
         if (dr) CU(cudaMemcpyAsync(dr, dR, sizeof(float) * nr, cudaMemcpyDeviceToHost, ctx->s));
     }
-    CU(cudaStreamSynchronize(ctx->s));
-    return FR_OK;
+    return read_state(ctx);  // synchronises; reports an expired wait of the gradient kernels
 }
 
 fr_status fr_set_state(fr_ctx* ctx, const float* param, const float* m1, const float* m2,
@@ -912,7 +915,7 @@ fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* be
     CU(launch_envy(ctx->r, ctx->r_bf16, V, ctx->U, ctx->I, ctx->ld, ctx->imp, ctx->esum,
                    reinterpret_cast<float*>(base + oM), reinterpret_cast<float*>(base + oD),
                    reinterpret_cast<double*>(base + oR), reinterpret_cast<double*>(base + oP), out,
-                   ctx->flags, ctx->s));
+                   ctx->flags, polls_of(ctx->cfg.max_wait_polls), ctx->s));
     ctx->launches += 5;
     double h[3];
     int hf[4];
@@ -1011,6 +1014,79 @@ fr_status fr_time_kernels(fr_ctx* ctx, int32_t n_steps, double* ms) {
     ms[1] = acc[1] / n_steps;
     ms[2] = acc[2] / n_steps;
     return read_state(ctx);
+}
+
+fr_status fr_measure_peaks(double* out, int32_t n) {
+    fr_ctx* ctx = nullptr;
+    if (!out || n < 1 || n > 6) return fail(nullptr, FR_EINVAL, "need out and 1 <= n <= 6");
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    const fr_status s0 = fr_measure_ex2_rate(&v[0]);
+    if (s0 != FR_OK) return s0;
+    int dev = 0, sms = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    float* sink = nullptr;
+    unsigned long long* clk = nullptr;
+    CU(cudaMalloc(&sink, sizeof(float) * sms * 8));
+    if (cudaMalloc(&clk, sizeof(unsigned long long) * 2) != cudaSuccess) {
+        cudaFree(sink);
+        return fail(nullptr, FR_ENOMEM, "cudaMalloc of the probe's clock record failed");
+    }
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    std::vector<double> mhz;
+    cudaError_t e = cudaSuccess;
+    // kind, CTAs per SM, threads, iterations, units per thread and iteration (bytes or FMAs)
+    const int kinds[4][4] = {{0, 4, 256, 4096}, {1, 4, 256, 2048}, {2, 8, 256, 16384},
+                             {3, 8, 256, 8192}};
+    const double per_it[4] = {8.0 * 8, 8.0 * 16, 8.0, 16.0};
+    for (int q = 0; q < 4 && e == cudaSuccess; ++q) {
+        const int kind = kinds[q][0], blocks = sms * kinds[q][1], threads = kinds[q][2];
+        const int iters = kinds[q][3];
+        e = launch_peak_bench(kind, sink, blocks, threads, 64, clk, nullptr);  // warm-up
+        if (e != cudaSuccess) break;
+        cudaEventRecord(a);
+        e = launch_peak_bench(kind, sink, blocks, threads, iters, clk, nullptr);
+        cudaEventRecord(b);
+        if (e != cudaSuccess) break;
+        if ((e = cudaEventSynchronize(b)) != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        unsigned long long hc[2] = {0, 0};
+        if ((e = cudaMemcpy(hc, clk, sizeof hc, cudaMemcpyDeviceToHost)) != cudaSuccess) break;
+        if (hc[1] > 0) mhz.push_back((double)hc[0] / (double)hc[1] * 1e3);
+        v[1 + q] = (double)blocks * threads * (double)iters * per_it[q] / (ms * 1e-3);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(sink);
+    cudaFree(clk);
+    CU(e);
+    if (!mhz.empty()) {
+        std::sort(mhz.begin(), mhz.end());
+        v[5] = mhz[mhz.size() / 2];
+    }
+    for (int j = 0; j < n; ++j) out[j] = v[j];
+    return FR_OK;
+}
+
+fr_status fr_set_wait_limit(fr_ctx* ctx, int32_t max_wait_polls) {
+    if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
+    if (max_wait_polls < -1)
+        return fail(ctx, FR_EINVAL, "max_wait_polls must be >= -1 (got %d)", max_wait_polls);
+    if (max_wait_polls == ctx->cfg.max_wait_polls) return FR_OK;
+    CU(cudaStreamSynchronize(ctx->s));  // the captured graphs hold the old limit: recapture
+    if (ctx->chunk_exec) {
+        cudaGraphExecDestroy(ctx->chunk_exec);
+        ctx->chunk_exec = nullptr;
+    }
+    if (ctx->solve_exec) {
+        cudaGraphExecDestroy(ctx->solve_exec);
+        ctx->solve_exec = nullptr;
+    }
+    ctx->cfg.max_wait_polls = max_wait_polls;
+    return FR_OK;
 }
 
 const char* fr_last_error(const fr_ctx* ctx) {

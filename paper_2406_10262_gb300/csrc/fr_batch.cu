@@ -146,6 +146,7 @@ P2Args market_args(const fr_batch* b, const BMarket& m, float* part) {
     a.inv_eps_ln2 = (float)(1.0 / (b->cfg.epsilon * std::log(2.0)));
     a.inv_eps = (float)(1.0 / b->cfg.epsilon);
     a.warm = b->cfg.warm_start ? 1 : 0;
+    a.max_polls = polls_of(b->cfg.max_wait_polls);
     return a;
 }
 
@@ -536,9 +537,9 @@ fr_status fr_batch_create(const fr_config* cfgs, int32_t n_markets, void* stream
         if (c.epsilon != c0.epsilon || c.sinkhorn_iters != c0.sinkhorn_iters ||
             c.warm_start != c0.warm_start || c.optimizer != c0.optimizer || c.lr != c0.lr ||
             c.beta1 != c0.beta1 || c.beta2 != c0.beta2 || c.adam_eps != c0.adam_eps ||
-            c.rel_dtype != c0.rel_dtype)
+            c.rel_dtype != c0.rel_dtype || c.max_wait_polls != c0.max_wait_polls)
             return bfail(nullptr, FR_EINVAL, "market %d: every field but the sizes must equal market 0's", i);
-        for (int j = 0; j < 7; ++j)
+        for (int j = 0; j < 6; ++j)
             if (c.reserved[j]) return bfail(nullptr, FR_EINVAL, "reserved fields must be zero");
         const int nc = fr_num_cols(c.n_items, c.n_slots);
         if (nc > 32 || warps_at(c.n_items, 8) * 32 > 512)
@@ -549,7 +550,7 @@ fr_status fr_batch_create(const fr_config* cfgs, int32_t n_markets, void* stream
     if (!(c0.epsilon > 0.0) || !std::isfinite(c0.epsilon) || c0.sinkhorn_iters < 1 || !(c0.lr > 0.0) ||
         !(c0.beta1 >= 0.0 && c0.beta1 < 1.0) || !(c0.beta2 >= 0.0 && c0.beta2 < 1.0) ||
         !(c0.adam_eps >= 0.0) || (c0.optimizer != FR_ADAM && c0.optimizer != FR_SGD) ||
-        (c0.rel_dtype != FR_F32 && c0.rel_dtype != FR_BF16))
+        (c0.rel_dtype != FR_F32 && c0.rel_dtype != FR_BF16) || c0.max_wait_polls < -1)
         return bfail(nullptr, FR_EINVAL, "invalid shared configuration");
 
     b = new fr_batch();

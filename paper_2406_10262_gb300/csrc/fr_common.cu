@@ -242,6 +242,109 @@ __global__ void ex2_bench_kernel(float* sink, int iters) {
     if (s == 12345.f) sink[blockIdx.x] = s;
 }
 
+// ---- on-chip peak probes (fr_measure_peaks) ------------------------------------------------------
+// Block 0's thread 0 records the SM clock and the global timer around its loop (clk[0..1]: cycles,
+// nanoseconds), which gives the clock the SMs ran at during the probe.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Shared-memory load bandwidth: every thread loads VB-byte vectors (8 or 16) from consecutive
+// addresses (conflict-free, the sweeps' access pattern), eight independent loads per iteration,
+// with the offset advanced each iteration so that no load can be hoisted; the loaded values are
+// summed with packed adds so that they are used.
+template <int VB>
+__global__ void smem_bench_kernel(float* sink, int iters, unsigned long long* clk) {
+    extern __shared__ __align__(16) float sbuf[];  // 16 KB
+    constexpr int NF = 16384 / 4;
+    for (int i = threadIdx.x; i < NF; i += blockDim.x) sbuf[i] = 1e-3f * (i & 63);
+    __syncthreads();
+    const unsigned base = (unsigned)__cvta_generic_to_shared(sbuf);
+    constexpr unsigned span = 16384u;
+    unsigned off = (unsigned)(threadIdx.x * VB) % span;
+    f2 acc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = 0ull;
+    unsigned long long c0 = 0, t0 = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c0 = clock64();
+        t0 = global_ns();
+    }
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const unsigned a = base + ((off + (unsigned)j * 1024u * VB / 8u) & (span - 1u));
+            if constexpr (VB == 8) {
+                f2 v;
+                asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(a));
+                acc[j] = add2(acc[j], v);
+            } else {
+                f2 v0, v1;
+                asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(v0), "=l"(v1) : "r"(a));
+                acc[j] = add2(acc[j], add2(v0, v1));
+            }
+        }
+        off = (off + 32u * VB) & (span - 1u);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        clk[0] = clock64() - c0;
+        clk[1] = global_ns() - t0;
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        float a, b;
+        upk(acc[j], a, b);
+        s += a + b;
+    }
+    if (s == 12345.f) sink[blockIdx.x] = s;
+}
+
+// FP32 fused multiply-add rate: eight independent chains per thread, scalar (PACKED = false) or
+// packed f32x2 (each instruction two multiply-adds).
+template <bool PACKED>
+__global__ void fma_bench_kernel(float* sink, int iters, unsigned long long* clk) {
+    unsigned long long c0 = 0, t0 = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c0 = clock64();
+        t0 = global_ns();
+    }
+    float s = 0.f;
+    if constexpr (PACKED) {
+        f2 x[8];
+        const f2 m = pk(0.999f, 0.998f), c = pk(1e-3f, 2e-3f);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = pk(0.1f * j, 1e-3f * (threadIdx.x & 31));
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) x[j] = fma2(x[j], m, c);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float a, b;
+            upk(x[j], a, b);
+            s += a + b;
+        }
+    } else {
+        float x[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = 0.1f * j + 1e-3f * (threadIdx.x & 31);
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) x[j] = fmaf(x[j], 0.999f, 1e-3f);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s += x[j];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        clk[0] = clock64() - c0;
+        clk[1] = global_ns() - t0;
+    }
+    if (s == 12345.f) sink[blockIdx.x] = s;
+}
+
 __global__ void solve_cond_kernel(const DevState* st, int* ctl, cudaGraphConditionalHandle h) {
     const int it = ctl[0] + 1;
     ctl[0] = it;
@@ -323,6 +426,17 @@ cudaError_t launch_solve_cond(const DevState* st, int* ctl, cudaGraphConditional
 
 cudaError_t launch_ex2_bench(float* sink, int blocks, int threads, int iters, cudaStream_t s) {
     ex2_bench_kernel<<<blocks, threads, 0, s>>>(sink, iters);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_peak_bench(int kind, float* sink, int blocks, int threads, int iters,
+                              unsigned long long* clk, cudaStream_t s) {
+    switch (kind) {
+        case 0: smem_bench_kernel<8><<<blocks, threads, 16384, s>>>(sink, iters, clk); break;
+        case 1: smem_bench_kernel<16><<<blocks, threads, 16384, s>>>(sink, iters, clk); break;
+        case 2: fma_bench_kernel<false><<<blocks, threads, 0, s>>>(sink, iters, clk); break;
+        default: fma_bench_kernel<true><<<blocks, threads, 0, s>>>(sink, iters, clk); break;
+    }
     return cudaGetLastError();
 }
 

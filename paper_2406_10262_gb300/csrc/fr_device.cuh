@@ -85,6 +85,22 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
     return false;
 }
 
+// Bounded wait of every thread of a CTA for phase `parity` of `bar` (a staged bulk copy), with one
+// outcome for the whole CTA: true if every thread saw the phase complete within `max_polls` polls.
+// Otherwise thread 0 sets `flag` in *err and every thread waits again, with `drain_polls`, for the
+// copy to land, so that the caller can stop without a bulk copy still writing into this CTA's
+// shared memory; the result is then false in every thread. Contains one __syncthreads_or (which
+// also makes the caller's earlier shared-memory writes visible); every thread must call it.
+__device__ __forceinline__ bool cta_wait_or_drain(unsigned long long* bar, unsigned parity,
+                                                  unsigned max_polls, unsigned drain_polls,
+                                                  int* err, int flag) {
+    const bool ok = mbar_wait(bar, parity, max_polls);
+    if (!__syncthreads_or(!ok)) return true;
+    if (threadIdx.x == 0) atomicOr(err, flag);
+    mbar_wait(bar, parity, drain_polls);
+    return false;
+}
+
 // ---- packed pairs of FP32 values (sm_100+ f32x2 arithmetic: two lanes per instruction) ---------
 typedef unsigned long long f2;
 

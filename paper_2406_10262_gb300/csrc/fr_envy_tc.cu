@@ -34,7 +34,6 @@ constexpr int OPER_BYTES = TM * TK * 4;       // one operand part (hi or lo) of 
 constexpr int STAGE_BYTES = 4 * OPER_BYTES;   // A_hi, A_lo, B_hi, B_lo
 constexpr int LBO = 128;                      // bytes between K-adjacent core matrices
 constexpr int SBO = (TK / 4) * 128;           // bytes between 8-row groups
-constexpr unsigned kPolls = 1u << 20;
 constexpr unsigned kTmemCols = 2 * TN;        // two FP32 accumulator regions of TN columns
 constexpr int CHUNK = 8;                      // stages (8 x 32 consumers) per accumulator chunk
 constexpr int NTHREADS = 512;                 // staging threads (warps 0-3 also run the epilogue)
@@ -140,7 +139,8 @@ __device__ __forceinline__ void store_stage(unsigned char* st, const StageRegs& 
 __global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const void* __restrict__ r, int r_bf16,
                                                         const float* __restrict__ V, int U, int I,
                                                         int ld, float* __restrict__ rmax,
-                                                        float* __restrict__ diag, int* err) {
+                                                        float* __restrict__ diag, int* err,
+                                                        unsigned max_polls) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* stages = smem_raw;                                    // 2 x STAGE_BYTES
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + 2 * STAGE_BYTES);
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const void* __rest
         const int st = kc & 1;
         unsigned char* sbuf = stages + st * STAGE_BYTES;
         if (kc >= 2 && ok) {  // the MMAs that read this buffer two stages ago are done
-            if (!mbar_wait(bar + st, ((kc - 2) >> 1) & 1u, kPolls)) ok = false;
+            if (!mbar_wait(bar + st, ((kc - 2) >> 1) & 1u, max_polls)) ok = false;
         }
         if (!__syncthreads_and(ok)) {
             ok = false;
@@ -235,8 +235,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const void* __rest
         }
         issued = kc;
     }
-    // all MMAs complete: the last commit tracks every earlier one of the issuing thread
-    if (issued >= 0 && !mbar_wait(bar + (issued & 1), (issued >> 1) & 1u, kPolls)) ok = false;
+    // all MMAs complete: the last commit tracks every earlier one of the issuing thread. If this
+    // wait (or an earlier one) expired, the CTA still waits, with the default bound, for its own
+    // MMAs before it frees the tensor memory and leaves.
+    if (issued >= 0 && !mbar_wait(bar + (issued & 1), (issued >> 1) & 1u, ok ? max_polls : 0u))
+        ok = false;
+    if (issued >= 0 && !__syncthreads_and(ok))
+        mbar_wait(bar + (issued & 1), (issued >> 1) & 1u, kDefaultPolls);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!__syncthreads_and(ok)) {
         if (tid == 0) atomicOr(err, 4);
@@ -276,12 +281,13 @@ int envy_tc_tiles(int I) { return (I + TM - 1) / TM; }
 size_t envy_tc_smem() { return 2 * STAGE_BYTES + 64; }
 
 cudaError_t launch_envy_tc(const void* r, int r_bf16, const float* V, int U, int I, int ld,
-                           float* rmax, float* diag, int* err, cudaStream_t s) {
+                           float* rmax, float* diag, int* err, unsigned max_polls,
+                           cudaStream_t s) {
     const int nt = envy_tc_tiles(I);
     cudaError_t e = raise_smem_limit((const void*)envy_tc_kernel, envy_tc_smem());
     if (e != cudaSuccess) return e;
     envy_tc_kernel<<<dim3(nt, nt), NTHREADS, envy_tc_smem(), s>>>(r, r_bf16, V, U, I, ld, rmax, diag,
-                                                                 err);
+                                                                 err, max_polls);
     return cudaGetLastError();
 }
 

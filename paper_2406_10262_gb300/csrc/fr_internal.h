@@ -59,6 +59,7 @@ struct P1Args {
     float lr, beta1, beta2, adam_eps;
     int optimizer;        // 0 Adam, 1 SGD
     int warm;
+    unsigned max_polls;   // bounded waits: polls before a wait gives up (0: expires at once)
 };
 
 struct ReduceArgs {
@@ -96,6 +97,7 @@ struct P2Args {
     int warm;
     float* ck;            // unrolled gradient: column-potential checkpoints [U][nck][nc] (nullable)
     int ce, nck;          // checkpoint interval (iterations) and count ceil(L / ce)
+    unsigned max_polls;   // bounded waits: polls before a wait gives up (0: expires at once)
 };
 
 // Batched markets: a launch processes a list of chunks, each a range of consumers of one market
@@ -140,6 +142,14 @@ struct P2AdamArgs {
     int apply;            // 0: gradient only
     int nblk;             // batched launches: update blocks of this problem
 };
+
+// Polls of a bounded device-side wait by default (fr_config.max_wait_polls = 0), and the polls of
+// the drain that follows an expired wait (a kernel never leaves with its own copies in flight).
+constexpr unsigned kDefaultPolls = 1u << 26;
+// fr_config.max_wait_polls -> polls per wait
+inline unsigned polls_of(int32_t max_wait_polls) {
+    return max_wait_polls == 0 ? kDefaultPolls : max_wait_polls < 0 ? 0u : (unsigned)max_wait_polls;
+}
 
 // Raises a kernel's dynamic shared-memory limit to at least `bytes` (never lowers it: the limit is
 // per function, shared by every context that launches it). Serialised by a process-wide lock.
@@ -202,6 +212,10 @@ cudaError_t launch_relevance_check(const void* r, int r_bf16, int U, int I, int 
                                    cudaStream_t s);
 cudaError_t launch_policy(const P1Args& a, int u0, int n_u, float* x_out, cudaStream_t s);
 cudaError_t launch_ex2_bench(float* sink, int blocks, int threads, int iters, cudaStream_t s);
+// kind 0 / 1: shared-memory loads of 8 / 16 bytes; 2 / 3: scalar / packed FP32 FMA. clk[0..1]: SM
+// cycles and nanoseconds of block 0's loop.
+cudaError_t launch_peak_bench(int kind, float* sink, int blocks, int threads, int iters,
+                              unsigned long long* clk, cudaStream_t s);
 // Body end of fr_solve's device-side while loop: ctl[0] counts body iterations, ctl[1] caps them;
 // sets the loop's condition to continue while no stop / error flag is raised and the cap is not hit.
 cudaError_t launch_solve_cond(const DevState* st, int* ctl, cudaGraphConditionalHandle h,
@@ -218,10 +232,11 @@ size_t envy_tc_smem();
 cudaError_t launch_v_p1(const P1Args& a, float* V, cudaStream_t s);
 cudaError_t launch_v_p2(const P2Args& a, float* V, cudaStream_t s);
 cudaError_t launch_envy_tc(const void* r, int r_bf16, const float* V, int U, int I, int ld,
-                           float* rmax, float* diag, int* err, cudaStream_t s);
+                           float* rmax, float* diag, int* err, unsigned max_polls, cudaStream_t s);
 cudaError_t launch_envy(const void* r, int r_bf16, const float* V, int U, int I, int ld,
                         const double* imp, double esum, float* rmax, float* diag, double* ru,
-                        double* ru_part, double* out, int* err, cudaStream_t s);
+                        double* ru_part, double* out, int* err, unsigned max_polls,
+                        cudaStream_t s);
 int colsum_chunks();  // FP64 partials [colsum_chunks()][ld] of the column sums of r (ru_part)
 // Frank-Wolfe certificate (fr_metrics.cu): one of a1 / a2 non-null (the policy's form); G CTAs
 // (cert_grid), per-CTA partials gap_part [G] doubles and res_part [G] floats; out[0] = gap,

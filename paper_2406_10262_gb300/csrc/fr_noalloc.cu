@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <mutex>
 
 #include "fairrank.h"
@@ -73,13 +74,22 @@ extern "C" fr_status fr_nsw_eval_noalloc(const float* C, const float* r, int64_t
         set_thread_error(msg);
         return st;
     };
+    // A failed CUDA call: the message names the step and the runtime's error string; the
+    // runtime's last-error slot is cleared so that the caller's next error check does not see it.
+    auto cuda_fail = [](const char* what, cudaError_t err) {
+        char buf[256];
+        std::snprintf(buf, sizeof buf, "fr_nsw_eval_noalloc: %s: %s", what, cudaGetErrorString(err));
+        set_thread_error(buf);
+        (void)cudaGetLastError();
+        return FR_ECUDA;
+    };
     if (!C || !r || !e || !imp_out || !nsw_util_out)
         return bad(FR_EINVAL, "fr_nsw_eval_noalloc: NULL pointer argument");
     if (n_users < 1 || n_items < 1 || n_slots < 1 || n_slots > n_items)
         return bad(FR_EINVAL, "fr_nsw_eval_noalloc: need n_users >= 1 and 1 <= n_slots <= n_items");
     if (!(epsilon > 0.0) || !std::isfinite(epsilon) || sinkhorn_iters < 1)
         return bad(FR_EINVAL, "fr_nsw_eval_noalloc: need epsilon > 0 and sinkhorn_iters >= 1");
-    if (ld < n_items || ld % 8 != 0)
+    if (ld < n_items || ld % 8 != 0 || ld > (int64_t)1 << 30)
         return bad(FR_EINVAL, "fr_nsw_eval_noalloc: ld must be a multiple of 8 and >= n_items");
     if (reinterpret_cast<uintptr_t>(C) % 16 || reinterpret_cast<uintptr_t>(r) % 16)
         return bad(FR_EINVAL, "fr_nsw_eval_noalloc: C and r must be 16-byte aligned");
@@ -94,29 +104,50 @@ extern "C" fr_status fr_nsw_eval_noalloc(const float* C, const float* r, int64_t
     for (int k = 0; k < nc; ++k) pack.invb[k] = 1.f;  // 1 / b_k
     if (nc > n_slots) pack.invb[n_slots] = (float)(1.0 / (double)(n_items - n_slots));
     P1Variant var;
-    if (!p1_select(nc, n_items, &var)) {
-        set_thread_error("fr_nsw_eval_noalloc: n_cols / n_items outside the compiled kernel variants");
-        return FR_EUNSUPPORTED;
-    }
+    if (!p1_select(nc, n_items, &var))
+        return bad(FR_EUNSUPPORTED,
+                   "fr_nsw_eval_noalloc: n_cols / n_items outside the compiled kernel variants");
 
-    int dev = 0, sms = 0, occ = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return FR_ECUDA;
+    int dev = 0, sms = 0, occ = 0, max_optin = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_fail("cudaGetDevice", ce);
+    if (dev < 0 || dev >= kMaxDevices)
+        return bad(FR_EUNSUPPORTED, "fr_nsw_eval_noalloc: device ordinal above 63");
     {
         // once per device, with that device current: the device address of the static array
         std::lock_guard<std::mutex> lock(g_mu);
         if (!g_scratch_ptr[dev]) {
             void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return FR_ECUDA;
+            ce = cudaGetSymbolAddress(&p, g_scratch);
+            if (ce != cudaSuccess) return cuda_fail("cudaGetSymbolAddress of the scratch array", ce);
+            if (!p) return bad(FR_ECUDA, "fr_nsw_eval_noalloc: scratch array has no device address");
             g_scratch_ptr[dev] = p;
         }
     }
     unsigned char* base = static_cast<unsigned char*>(g_scratch_ptr[dev]);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return FR_ECUDA;
+    if ((ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return cuda_fail("cudaDeviceGetAttribute(multiprocessor count)", ce);
+    if ((ce = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
+        cudaSuccess)
+        return cuda_fail("cudaDeviceGetAttribute(shared memory per block)", ce);
+    // The kernel's dynamic shared memory grows with ld (the staged cost tile); above the 48 KB
+    // default its limit must be raised, which a context of the same variant may or may not have
+    // done already in this process. Raising it allocates nothing.
     const size_t smem = p1_smem_bytes(var, MODE_SWEEP, nc, (int)ld);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, var.fn[MODE_SWEEP], var.threads, smem) !=
-            cudaSuccess || occ < 1)
-        return FR_EUNSUPPORTED;
+    if (smem > (size_t)max_optin) {
+        char buf[192];
+        std::snprintf(buf, sizeof buf,
+                      "fr_nsw_eval_noalloc: the cost tile needs %zu bytes of shared memory per "
+                      "block (device limit %d): reduce ld or n_items",
+                      smem, max_optin);
+        return bad(FR_EUNSUPPORTED, buf);
+    }
+    if ((ce = raise_smem_limit(var.fn[MODE_SWEEP], smem)) != cudaSuccess)
+        return cuda_fail("raising the kernel's shared-memory limit", ce);
+    ce = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, var.fn[MODE_SWEEP], var.threads, smem);
+    if (ce != cudaSuccess) return cuda_fail("cudaOccupancyMaxActiveBlocksPerMultiprocessor", ce);
+    if (occ < 1)
+        return bad(FR_EUNSUPPORTED, "fr_nsw_eval_noalloc: the kernel variant cannot be resident");
 
     // scratch layout: state | e | invb | omega | blk | gn2_part | gL | gP | part
     const int nblk = reduce_blocks(n_items);
@@ -128,11 +159,10 @@ extern "C" fr_status fr_nsw_eval_noalloc(const float* C, const float* r, int64_t
     const size_t room = kScratchBytes > fixed ? kScratchBytes - fixed : 0;
     // gn2_part takes G doubles ahead of the partials
     while (G > 0 && align256(sizeof(double) * G) + (size_t)G * part_row > room) --G;
-    if (G < 1) {  // problem larger than the static scratch
-        set_thread_error("fr_nsw_eval_noalloc: 8 MiB static scratch too small: needs "
-                         "2*n_users*n_cols + n_items (+ one partial row of ld) floats");
-        return FR_EUNSUPPORTED;
-    }
+    if (G < 1)  // problem larger than the static scratch
+        return bad(FR_EUNSUPPORTED,
+                   "fr_nsw_eval_noalloc: 8 MiB static scratch too small: needs "
+                   "2*n_users*n_cols + n_items (+ one partial row of ld) floats");
 
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -149,11 +179,16 @@ extern "C" fr_status fr_nsw_eval_noalloc(const float* C, const float* r, int64_t
     float* gL = reinterpret_cast<float*>(take(sizeof(float) * (size_t)n_users * nc));
     float* gP = reinterpret_cast<float*>(take(sizeof(float) * (size_t)n_users * nc));
     float* part = reinterpret_cast<float*>(take((size_t)G * part_row));
-    if (off > kScratchBytes) return FR_EUNSUPPORTED;
+    if (off > kScratchBytes)
+        return bad(FR_EUNSUPPORTED, "fr_nsw_eval_noalloc: 8 MiB static scratch too small");
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    noalloc_prepare<<<1, 64, 0, s>>>(pack, nc, ed, ib, st);
-    if (cudaGetLastError() != cudaSuccess) return FR_ECUDA;
+    {
+        int nc_arg = nc;
+        void* args[] = {&pack, &nc_arg, &ed, &ib, &st};
+        ce = cudaLaunchKernel((const void*)noalloc_prepare, dim3(1), dim3(64), args, 0, s);
+        if (ce != cudaSuccess) return cuda_fail("launch of the set-up kernel", ce);
+    }
 
     P1Args a{};
     a.U = n_users; a.I = n_items; a.K = n_slots; a.nc = nc; a.ld = (int)ld;
@@ -164,15 +199,22 @@ extern "C" fr_status fr_nsw_eval_noalloc(const float* C, const float* r, int64_t
     a.inv_eps_ln2 = (float)(1.0 / (epsilon * std::log(2.0)));
     a.inv_eps = (float)(1.0 / epsilon);
     a.warm = 0;  // cold start: the first solve begins from zero column potentials
-    if (p1_launch(var, MODE_SWEEP, a, s) != cudaSuccess) return FR_ECUDA;
+    a.max_polls = kDefaultPolls;
+    if ((ce = p1_launch(var, MODE_SWEEP, a, s)) != cudaSuccess)
+        return cuda_fail("launch of the Sinkhorn kernel", ce);
 
     ReduceArgs ra{};
     ra.I = n_items; ra.ld = (int)ld; ra.G = G; ra.U = n_users;
     ra.part = part; ra.gn2_part = gn2; ra.imp = imp_out; ra.omega = omega; ra.blk = blk; ra.st = st;
     ra.F_hist = nullptr; ra.gn_hist = nullptr; ra.hist_cap = 0; ra.after_update = 0;
     ra.Ggn = 0;
-    if (reduce_launch(ra, s) != cudaSuccess) return FR_ECUDA;
-    noalloc_finish<<<1, 1, 0, s>>>(st, nsw_util_out);
-    if (cudaGetLastError() != cudaSuccess) return FR_ECUDA;
+    if ((ce = reduce_launch(ra, s)) != cudaSuccess)
+        return cuda_fail("launch of the impact reduction", ce);
+    {
+        const DevState* stc = st;
+        void* args[] = {&stc, &nsw_util_out};
+        ce = cudaLaunchKernel((const void*)noalloc_finish, dim3(1), dim3(1), args, 0, s);
+        if (ce != cudaSuccess) return cuda_fail("launch of the result kernel", ce);
+    }
     return FR_OK;
 }

@@ -678,19 +678,21 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
         }
         if (MODE != MODE_SWEEP && tid < ncx) s.gp[tid] = tid < nc ? a.gP[(size_t)u * nc + tid] : 0.f;
         // the consumer's tile was staged one consumer ago (the register sweep) or right after the
-        // previous solve (the tile sweep); a bounded wait records a timeout instead of hanging (the
-        // CTA then continues on whatever data is there). In the tile sweep's update modes the
-        // first gradient pass reads the costs from global memory (L2, where the previous solve
-        // prefetched them) while the copy lands, and the wait follows that pass.
+        // previous solve (the tile sweep), and it is the only copy in flight. The wait is bounded:
+        // if it expires, the CTA records a timeout, waits (with the default bound) for the copy to
+        // land and stops, so that no bulk copy is still writing into its shared memory when it
+        // leaves. In the tile sweep's update modes the first gradient pass reads the costs from
+        // global memory (L2, where the previous solve prefetched them) while the copy lands, and
+        // the wait follows that pass.
         constexpr bool LATE_WAIT = TS != 0 && MODE != MODE_SWEEP;
-        auto wait_tile = [&]() {
-            if (!mbar_wait(s.bar, phase, 1u << 26)) {
-                if (tid == 0) atomicOr(&a.st->err, 4);
-            }
+        bool tile_ok = true;  // the same in every thread (cta_wait_or_drain)
+        if constexpr (!LATE_WAIT) {
+            tile_ok = cta_wait_or_drain(s.bar, phase, a.max_polls, kDefaultPolls, &a.st->err, 4);
             phase ^= 1u;
-        };
-        if constexpr (!LATE_WAIT) wait_tile();
-        __syncthreads();  // s.gp / s.e / s.ib / s.om / s.coef visible
+        } else {
+            __syncthreads();  // s.gp / s.e / s.ib / s.om / s.coef visible
+        }
+        if (!tile_ok) break;
 
         if constexpr (MODE != MODE_SWEEP) {
             if (TS && MODE == MODE_UPDATE_SWEEP && a.optimizer == 0 && tid == 0) {
@@ -748,7 +750,11 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
                 }
                 cta_reduce<NCB, 3>(acc, nc, s.red, s.out, ncp);  // s.out: [q | cs | X^T h]
             }
-            if constexpr (LATE_WAIT) wait_tile();  // the shared tile from here on
+            if constexpr (LATE_WAIT) {  // the shared tile from here on
+                tile_ok = cta_wait_or_drain(s.bar, phase, a.max_polls, kDefaultPolls, &a.st->err, 4);
+                phase ^= 1u;
+                if (!tile_ok) break;
+            }
             // Gram block M[0:n,0:n] of diag(cs) - X^T X; rows of x sum to 1, so the diagonal is
             // sum_i x_ik (1 - x_ik) without cancellation.
             if constexpr (REG_GRAM) {

@@ -288,10 +288,12 @@ __device__ __forceinline__ void sweep_consumers(const P2Args& a, int u_first, in
     for (int r = 0; r < R; ++r) vr[r] = i0 + r < I;
 
     for (int u = u_first; u < u_end; u += u_step, b ^= 1) {
-        if (!mbar_wait(s.bar + b, (phase_bits >> b) & 1u, 1u << 26)) {
-            if (tid == 0) atomicOr(&a.st->err, 4);
-        }
+        // the consumer's relevance row is the only copy in flight; if the bounded wait expires,
+        // the CTA records a timeout, waits (default bound) for the copy to land and stops
+        const bool row_ok = cta_wait_or_drain(s.bar + b, (phase_bits >> b) & 1u, a.max_polls,
+                                              kDefaultPolls, &a.st->err, 4);
         phase_bits ^= 1u << b;
+        if (!row_ok) break;
         const unsigned char* rrow = s.rbuf + (size_t)b * esz * ld;
         float sv[R];
 #pragma unroll
@@ -484,10 +486,12 @@ __device__ __forceinline__ void grad_consumers(const P2Args& a, int u_first, int
         s.eh[k] = k < nc ? a.e[k] - a.emax : 0.f;
     }
     for (int u = u_first; u < u_end; u += u_step, b ^= 1) {
-        if (!mbar_wait(s.bar + b, (phase_bits >> b) & 1u, 1u << 26)) {
-            if (tid == 0) atomicOr(&a.st->err, 4);
-        }
+        // the consumer's relevance row is the only copy in flight; if the bounded wait expires,
+        // the CTA records a timeout, waits (default bound) for the copy to land and stops
+        const bool row_ok = cta_wait_or_drain(s.bar + b, (phase_bits >> b) & 1u, a.max_polls,
+                                              kDefaultPolls, &a.st->err, 4);
         phase_bits ^= 1u << b;
+        if (!row_ok) break;
         const unsigned char* rrow = s.rbuf + (size_t)b * esz * ld;
         for (int k = tid; k < nx; k += T) s.gp[k] = k < nc ? a.gP[(size_t)u * nc + k] : -INFINITY;
         __syncthreads();

@@ -140,10 +140,12 @@ __global__ void __launch_bounds__(256) p2_adj_kernel(const P2Args a) {
     unsigned phase_bits = 0u;
     int b = 0;
     for (int u = blockIdx.x; u < a.U; u += gridDim.x, b ^= 1) {
-        if (!mbar_wait(s.bar + b, (phase_bits >> b) & 1u, 1u << 26)) {
-            if (tid == 0) atomicOr(&a.st->err, 4);
-        }
+        // the consumer's relevance row is the only copy in flight; if the bounded wait expires,
+        // the CTA records a timeout, waits (default bound) for the copy to land and stops
+        const bool row_ok = cta_wait_or_drain(s.bar + b, (phase_bits >> b) & 1u, a.max_polls,
+                                              kDefaultPolls, &a.st->err, 4);
         phase_bits ^= 1u << b;
+        if (!row_ok) break;
         const unsigned char* rrow = s.rbuf + (size_t)b * esz * ld;
         float sv[R], rho[R];
 #pragma unroll

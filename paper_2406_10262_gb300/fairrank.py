@@ -30,7 +30,7 @@ class Config(ct.Structure):
         ("warm_start", ct.c_int32), ("grad_mode", ct.c_int32), ("ckpt_every", ct.c_int32),
         ("optimizer", ct.c_int32), ("lr", ct.c_double), ("beta1", ct.c_double),
         ("beta2", ct.c_double), ("adam_eps", ct.c_double), ("rel_dtype", ct.c_int32),
-        ("reserved", ct.c_int32 * 7),
+        ("max_wait_polls", ct.c_int32), ("reserved", ct.c_int32 * 6),
     ]
 
 
@@ -76,6 +76,8 @@ def lib():
             "fr_time_kernels": (i32, [_vp, i32, _dp]),
             "fr_kernel_variant": (i32, [_vp, ct.POINTER(i32)]),
             "fr_sweep_stats": (i32, [_vp, ct.POINTER(i64)]),
+            "fr_set_wait_limit": (i32, [_vp, i32]),
+            "fr_measure_peaks": (i32, [_dp, i32]),
             "fr_batch_create": (i32, [ct.POINTER(Config), i32, _vp, ct.POINTER(_vp)]),
             "fr_batch_destroy": (i32, [_vp]),
             "fr_batch_reset": (i32, [_vp]),
@@ -138,6 +140,17 @@ def measure_ex2_rate() -> float:
     return out.value
 
 
+def measure_peaks() -> dict:
+    """Measured on-chip rates of the current device (fr_measure_peaks)."""
+    out = (ct.c_double * 6)()
+    st = lib().fr_measure_peaks(out, 6)
+    if st:
+        raise FairRankError(st, lib().fr_last_error(None).decode())
+    keys = ["ex2_per_s", "smem_bytes_per_s_8B", "smem_bytes_per_s_16B", "ffma_per_s",
+            "ffma2_fmas_per_s", "sm_mhz"]
+    return dict(zip(keys, list(out)))
+
+
 class FairRank:
     """One fair-ranking problem on the current CUDA device (wraps an fr_ctx)."""
 
@@ -198,6 +211,10 @@ class FairRank:
 
     def reset(self):
         self._check(lib().fr_reset(self.h))
+
+    def set_wait_limit(self, max_wait_polls: int):
+        """Polls of the bounded device-side waits (fr_config.max_wait_polls; 0 = default)."""
+        self._check(lib().fr_set_wait_limit(self.h, max_wait_polls))
 
     # ---- Algorithm 1 ----------------------------------------------------------------------
     def step(self, n: int, trace: bool = True):

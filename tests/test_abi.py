@@ -44,7 +44,8 @@ def test_config_defaults_and_columns(lib):
 
 
 @pytest.mark.parametrize("field,value", [("n_slots", 0), ("n_items", 3), ("epsilon", 0.0),
-                                         ("sinkhorn_iters", 0), ("lr", -1.0), ("optimizer", 7)])
+                                         ("sinkhorn_iters", 0), ("lr", -1.0), ("optimizer", 7),
+                                         ("max_wait_polls", -2)])
 def test_create_rejects_invalid_config_before_touching_the_device(lib, field, value):
     cfg = fr.Config()
     lib.fr_config_default(ct.byref(cfg), 4, 5, 4, fr.PARAM_FULL_C)

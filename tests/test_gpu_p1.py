@@ -98,6 +98,29 @@ def test_parity50_trajectory_against_golden():
     np.testing.assert_allclose(imp, gold["imp_final"], rtol=1e-5)
 
 
+def test_plain2000x1000_trajectory_against_golden():
+    """The benchmarked workload in full: 2000 consumers x 1000 items, K = 10 (11 columns),
+    low-rank-sigmoid relevance (seed 0), 500 Adam steps x 50 Sinkhorn iterations. F after every
+    step against the FP64 oracle's stored trajectory (1e-6 relative), the final impacts at 1e-5
+    relative, as for the 100-step square workload."""
+    gold = json.load(open(os.path.join(GOLDEN, "plain2000x1000.json")))
+    U, I, K = gold["n_users"], gold["n_items"], gold["n_slots"]
+    r = synth.workload_relevance("plain2000x1000")
+    g = fr.FairRank(U, I, K, lr=gold["lr"], sinkhorn_iters=gold["iters"])
+    g.set_relevance(np.ascontiguousarray(r, dtype=np.float32))
+    g.set_exposure(synth.dcg_exposure(K))
+    _, _, F0 = g.impacts()
+    assert rel(F0, gold["F0"]) < NSW_RTOL
+    F = g.step(gold["steps"])
+    Fo = np.array(gold["F"])
+    errs = np.abs(F - Fo) / np.abs(Fo)
+    assert errs.max() < NSW_RTOL, f"max rel F error {errs.max():.2e} at step {errs.argmax()}"
+    imp, _, _ = g.impacts()
+    np.testing.assert_allclose(imp, gold["imp_final"], rtol=1e-5)
+    assert g.log_form_solves() == 0
+    g.close()
+
+
 def test_sgd_trajectory_policy_parity():
     U, I, K = 9, 40, 6
     r = synth.relevance_lowrank(U, I, seed=5)

@@ -9,6 +9,10 @@ cold-start solve) within the suite's tolerance; a repeated call must reproduce i
 exactly, whatever ran in between. The file is named to be collected last.
 """
 import ctypes as ct
+import json
+import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -103,6 +107,49 @@ def test_row_stride_longer_than_the_items(torch, U, I, K, ld):
     np.testing.assert_allclose(imp, imp_ref, rtol=NSW_RTOL)
 
 
+FRESH_CASES = [
+    (20, 2000, 20, 2000),  # 21-column tile sweep: about 172 KB of shared memory per block
+    (12, 300, 10, 2048),   # register sweep staging its tile at the caller's stride: about 98 KB
+]
+
+
+def fresh_process_results():
+    """Runs in a fresh process: the allocation-free entry point first, for every case, before any
+    context exists (so no earlier call has raised a kernel's shared-memory limit), then the
+    context-based results of the same problems. Prints both as JSON."""
+    import torch
+    from paper_2406_10262_gb300 import build as frbuild
+
+    frbuild.build()
+    out = []
+    for U, I, K, ld in FRESH_CASES:
+        r, C = problem(U, I, K, 9)
+        imp, util, F = via_noalloc(torch, U, I, K, r, C, 20, 1.0, ld=ld, pad=3.0)
+        out.append({"noalloc": list(map(float, imp)) + [util, F]})
+    for j, (U, I, K, ld) in enumerate(FRESH_CASES):
+        r, C = problem(U, I, K, 9)
+        imp, util, F = via_context(U, I, K, r, C, 20, 1.0)
+        out[j]["context"] = list(map(float, imp)) + [util, F]
+    print("RESULT " + json.dumps(out))
+
+
+def test_first_call_in_a_fresh_process_needs_no_context(torch):
+    """Shapes whose kernels need more than the default 48 KB of dynamic shared memory, called
+    before any context of the same kernel variant exists in the process: the entry point raises
+    the kernel's limit itself (which allocates nothing) and matches fr_impacts."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PYTHONPATH=os.pathsep.join([root, os.path.join(root, "tests")]))
+    res = subprocess.run([sys.executable, os.path.abspath(__file__), "--fresh"], env=env,
+                         capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stdout[-2000:] + res.stderr[-4000:]
+    line = [l for l in res.stdout.splitlines() if l.startswith("RESULT ")][-1]
+    for case in json.loads(line[len("RESULT "):]):
+        na, cx = np.array(case["noalloc"]), np.array(case["context"])
+        np.testing.assert_allclose(na[:-2], cx[:-2], rtol=NSW_RTOL)  # impacts
+        assert abs(na[-2] - cx[-2]) <= NSW_RTOL * abs(cx[-2])        # utility
+        assert abs(na[-1] - cx[-1]) <= NSW_RTOL * abs(cx[-1])        # F
+
+
 def test_rejects_problems_larger_than_the_static_scratch(torch):
     small = torch.zeros(64, dtype=torch.float32, device="cuda")
     out = torch.zeros(8, dtype=torch.float64, device="cuda")
@@ -115,3 +162,7 @@ def test_rejects_problems_larger_than_the_static_scratch(torch):
     st = entry()(small.data_ptr(), small.data_ptr(), 12, e.ctypes.data_as(ct.POINTER(ct.c_double)),
                  4, 8, 7, 1.0, 10, out.data_ptr(), out.data_ptr(), 0)
     assert st == 1  # ld not a multiple of 8
+
+
+if __name__ == "__main__" and "--fresh" in sys.argv:
+    fresh_process_results()
