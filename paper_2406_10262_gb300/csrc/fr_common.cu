@@ -245,11 +245,6 @@ __global__ void ex2_bench_kernel(float* sink, int iters) {
 // ---- on-chip peak probes (fr_measure_peaks) ------------------------------------------------------
 // Block 0's thread 0 records the SM clock and the global timer around its loop (clk[0..1]: cycles,
 // nanoseconds), which gives the clock the SMs ran at during the probe.
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 
 // Shared-memory load bandwidth: every thread loads VB-byte vectors (8 or 16) from consecutive
 // addresses (conflict-free, the sweeps' access pattern), eight independent loads per iteration,

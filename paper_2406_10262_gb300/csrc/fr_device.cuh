@@ -85,6 +85,13 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
     return false;
 }
 
+// Nanoseconds of the global timer.
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Bounded wait of every thread of a CTA for phase `parity` of `bar` (a staged bulk copy), with one
 // outcome for the whole CTA: true if every thread saw the phase complete within `max_polls` polls.
 // Otherwise thread 0 sets `flag` in *err and every thread waits again, with `drain_polls`, for the

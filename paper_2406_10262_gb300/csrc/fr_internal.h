@@ -32,6 +32,8 @@ struct DevState {
     unsigned int counter; // last-block-done counter of the reduction (returns to 0)
     int max_steps;        // > 0: the reduction raises stop once steps_done reaches it
     unsigned long long log_solves;  // tile-sweep solves that finished in the log form
+    unsigned long long cta_ns;      // free-cost update step: CTA 0's duration per consumer (ns) in
+                                    // the last launch (0 before the first), for the stagger below
     double F, utility, gnorm;
     double thresh;        // < 0: never stop
 };

@@ -632,6 +632,28 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
 
     if (a.st->stop) return;  // fr_solve reached its threshold: the remaining steps are no-ops
 
+    // Staggered start of the ascent step. Every CTA alternates a gradient step (its Adam pass
+    // streams the moments from HBM) and an on-chip Sinkhorn solve, and CTAs that start together
+    // stay in phase, so their memory-bound phases coincide. CTAs in the upper half of the grid that
+    // have fewer consumers than the busiest CTA (which sets the kernel's duration) start a quarter
+    // of a consumer period late -- time they would otherwise spend idle at the end -- so that their
+    // gradient steps fall into the other CTAs' solves (2000 x 1000 x 11: 4 % shorter step). The
+    // period is CTA 0's time per consumer in the previous launch. Only the timing changes.
+    const int n_mine = (a.U - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int n_most = (a.U + (int)gridDim.x - 1) / (int)gridDim.x;
+    unsigned long long t_launch = 0;
+    if constexpr (MODE == MODE_UPDATE_SWEEP) {
+        if (blockIdx.x == 0 && tid == 0) t_launch = global_ns();
+        const unsigned long long period = a.st->cta_ns;
+        if (n_mine < n_most && blockIdx.x >= gridDim.x / 2 && period > 0) {
+            const unsigned long long t0 = global_ns(), delay = period / 4;
+            for (int it = 0; it < 8192; ++it) {  // bounded: at most ~8 ms of 1 us naps
+                if (global_ns() - t0 >= delay) break;
+                __nanosleep(1000);
+            }
+        }
+    }
+
     if (tid == 0) {
         mbar_init(s.bar, 1);
         fence_mbar_init();
@@ -1216,6 +1238,7 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
             double t = 0.0;
             for (int w = 0; w < W; ++w) t += s_d[w];
             a.gn2_part[blockIdx.x] = t;
+            if (blockIdx.x == 0 && n_mine > 0) a.st->cta_ns = (global_ns() - t_launch) / n_mine;
         }
     }
 }
