@@ -77,9 +77,12 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="plain2000x1000")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--full-oracle", action="store_true",
+                    help="with --compare precision: also one FP64 oracle forward over all consumers")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling driver: set up the workload, run this many ascent steps, exit")
-    ap.add_argument("--compare", choices=["batch", "unrolled", "bf16", "paper-shapes", "p1-scale"],
+    ap.add_argument("--compare", choices=["batch", "unrolled", "bf16", "paper-shapes", "p1-scale",
+                                          "precision"],
                     default=None,
                     help="compare a layered form against the plain FP32 method (one JSON line)")
     ap.add_argument("--profile-item", choices=["implicit", "unrolled", "bf16", "batch", "metrics"],
@@ -525,6 +528,80 @@ def compare_bf16(args):
     return out
 
 
+def compare_precision(args):
+    """The precision workload against the FP64 oracle: |U| = 200000, |I| = 10^4, K = 20, L = 50,
+    rank-32 sigmoid relevance with 5% boosted items stored in BF16, S ascent steps from theta = 0
+    on the GPU. The oracle then solves a seeded sample of 1000 consumers at the GPU's final theta
+    from the GPU's warm start of the last solve (the same L iterations), once on the BF16-rounded
+    relevance the GPU used (the kernels' error) and once on the FP32 relevance (with the
+    quantisation error): the policy's largest absolute difference and the relative error of the
+    sample's impacts and of its NSW (sum_i log of the sample's impacts). With --full-oracle it also
+    runs one oracle forward over all consumers (in chunks of 2000; about 2 x 10^12 cell-updates of
+    host time) and reports F against the GPU's F of the whole market."""
+    import oracle
+    from paper_2406_10262_gb300 import fairrank as fr
+    from paper_2406_10262_gb300 import synth
+    U, I, K, L, S = 200000, 10000, 20, 50, max(args.steps, 1) * 2
+    n_sample, blk = 1000, 20000
+    r32 = np.empty((U, I), dtype=np.float32)
+    for u0 in range(0, U, blk):
+        r32[u0:u0 + blk] = synth.relevance_lowrank_fast(U, I, seed=0, boost_frac=0.05, row0=u0,
+                                                        rows=min(blk, U - u0))
+    rb = synth.to_bf16_bits(r32)
+    e = synth.dcg_exposure(K)
+    g = fr.FairRank(U, I, K, param=fr.PARAM_ITEM, sinkhorn_iters=L, rel_dtype=fr.BF16)
+    g.set_relevance(rb)
+    g.set_exposure(e)
+    g.impacts()
+    if S > 1:
+        g.step(S - 1, trace=False)
+    _, _, _, g0, _ = g.get_state()  # warm start of the last solve
+    F_trace = g.step(1)
+    theta, _, _, _, t = g.get_state()
+    imp_gpu, _, F_gpu = g.impacts()
+    sample = np.sort(np.random.default_rng(2026).choice(U, n_sample, replace=False))
+    X_gpu = np.stack([g.policy(int(u), 1)[0] for u in sample]).astype(np.float64)
+    del g
+    nc = fr.num_cols(I, K)
+    e_pad = np.r_[e, np.zeros(nc - K)]
+    out = {"compare": "precision", "n_users": U, "n_items": I, "n_slots": K, "sinkhorn_iters": L,
+           "ascent_steps": S, "relevance": "bf16", "sample_consumers": n_sample,
+           "sample": "seeded uniform sample of consumers (numpy default_rng(2026))",
+           "F_gpu": float(F_gpu), "F_trace_last": float(F_trace[-1])}
+    rs_b = synth.bf16_bits_to_f64(rb[sample])
+    for name, r_s in (("vs_bf16_relevance", rs_b), ("vs_fp32_relevance", r32[sample].astype(np.float64))):
+        o = oracle.Oracle(n_sample, I, K, param=oracle.PARAM_ITEM, iters=L, warm_start=True)
+        o.set_relevance(r_s)
+        o.set_exposure(e)
+        o.set_state(param=theta.astype(np.float64), g=g0[sample].astype(np.float64))
+        imp_o, _, F_o = o.impacts()
+        X_o = o.policy()
+        imp_g = (r_s * (X_gpu @ e_pad)).sum(axis=0)  # the sample's impacts from the GPU policy
+        F_g = float(np.sum(np.log(imp_g)))
+        out[name] = {"x_max_abs_err": float(np.max(np.abs(X_gpu - X_o))),
+                     "sample_imp_max_rel_err": float(np.max(np.abs(imp_g - imp_o) / imp_o)),
+                     "sample_F_oracle": float(F_o), "sample_F_gpu_policy": F_g,
+                     "sample_F_rel_err": abs(F_g - F_o) / abs(F_o)}
+        del o, X_o
+    if args.full_oracle:
+        chunk, imp_full = 2000, np.zeros(I)
+        t0 = time.perf_counter()
+        for u0 in range(0, U, chunk):
+            u1 = min(U, u0 + chunk)
+            o = oracle.Oracle(u1 - u0, I, K, param=oracle.PARAM_ITEM, iters=L, warm_start=True)
+            o.set_relevance(synth.bf16_bits_to_f64(rb[u0:u1]))
+            o.set_exposure(e)
+            o.set_state(param=theta.astype(np.float64), g=g0[u0:u1].astype(np.float64))
+            imp_full += o.impacts()[0]
+            del o
+        F_full = float(np.sum(np.log(imp_full)))
+        out["full_oracle"] = {"F_oracle": F_full, "F_rel_err": abs(F_gpu - F_full) / abs(F_full),
+                              "imp_max_rel_err": float(np.max(np.abs(imp_gpu - imp_full) / imp_full)),
+                              "oracle_seconds": time.perf_counter() - t0,
+                              "oracle_threads": os.cpu_count()}
+    return out
+
+
 def compare_p1_scale(args):
     """The free-cost parametrisation (the paper's Problem (8)) at the sizes of the differentiation
     and batching workloads: (a) |U| = 20000, |I| = 2000, K = 20 (21 columns), L = 100, S ascent
@@ -679,7 +756,8 @@ def main():
         from paper_2406_10262_gb300 import build as frbuild
         frbuild.build()
         fn = {"batch": compare_batch, "unrolled": compare_unrolled, "bf16": compare_bf16,
-              "paper-shapes": compare_paper_shapes, "p1-scale": compare_p1_scale}[args.compare]
+              "paper-shapes": compare_paper_shapes, "p1-scale": compare_p1_scale,
+              "precision": compare_precision}[args.compare]
         print(json.dumps(fn(args)), flush=True)
         return
     w = workload(args.workload)

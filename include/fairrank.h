@@ -63,11 +63,12 @@ typedef struct fr_config {
     int32_t sinkhorn_iters; /* L >= 1 Sinkhorn iterations per consumer per step */
     int32_t warm_start;     /* 1: each solve starts from the previous solve's column potentials */
     int32_t grad_mode;      /* FR_GRAD_IMPLICIT: differentiates the optimality conditions of
-                               Problem (7) at the emitted policy. FR_GRAD_UNROLLED (FR_PARAM_ITEM
-                               only): the exact derivative of the L-iteration Sinkhorn map that
-                               produced the policy (reverse sweep over the iterations, the warm
-                               start held constant); needs n_items <= 6144 (2048 unless n_cols is
-                               6, 11 or 21), else FR_EUNSUPPORTED */
+                               Problem (7) at the emitted policy. FR_GRAD_UNROLLED: the exact
+                               derivative of the L-iteration Sinkhorn map that produced the policy
+                               (reverse sweep over the iterations, the warm start held constant);
+                               FR_PARAM_ITEM needs n_items <= 6144 (2048 unless n_cols is 6, 11 or
+                               21), FR_PARAM_FULL_C (dL/dc for every cell) n_cols <= 32 and
+                               n_items <= 1024 (n_cols <= 16) or 512, else FR_EUNSUPPORTED */
     int32_t ckpt_every;     /* FR_GRAD_UNROLLED: every ckpt_every-th iterate of the column
                                potentials is stored per consumer (ceil(L / ckpt_every) n_cols
                                floats); the rest are recomputed. >= 1 */
@@ -186,17 +187,20 @@ FR_API const char* fr_last_error(const fr_ctx* ctx);
 
 /* ---- batched markets ---------------------------------------------------------------------- */
 
-/* Many independent instances of Problem (8) under FR_PARAM_ITEM (each market its own consumers,
-   items, slots, relevance, exposure and theta), advanced together: per ascent step one gradient and
-   one Sinkhorn launch per kernel shape (concurrent), one theta update and one impact reduction over
-   all markets, chunks of steps replayed as a CUDA graph. Results equal those of one FairRank
-   context per market (same kernels, same arithmetic per consumer). The paper runs Algorithm 1 on one
-   market at a time; batching is this library's packaging for many small markets on one GPU. */
+/* Many independent instances of Problem (8) (each market its own consumers, items, slots,
+   relevance, exposure and parameters), advanced together. FR_PARAM_ITEM: per ascent step one
+   gradient and one Sinkhorn launch per kernel shape (concurrent), one theta update and one impact
+   reduction over all markets. FR_PARAM_FULL_C (free costs, the paper's parametrisation): per ascent
+   step one launch of the fused gradient + Adam + Sinkhorn kernel per kernel shape (concurrent) and
+   one impact reduction over all markets. Chunks of steps are replayed as a CUDA graph. Results
+   equal those of one FairRank context per market (same per-consumer arithmetic). The paper runs
+   Algorithm 1 on one market at a time; batching is this library's packaging for many small
+   markets on one GPU. */
 typedef struct fr_batch fr_batch; /* opaque; owns all device state of the markets */
 
-/* cfgs[0 .. n_markets): each FR_PARAM_ITEM with FR_GRAD_IMPLICIT, n_cols <= 32, n_items <= 4096;
-   every field except n_users, n_items and n_slots must equal cfgs[0]'s (FR_EINVAL). stream: as
-   fr_create. */
+/* cfgs[0 .. n_markets): all FR_PARAM_ITEM (n_cols <= 32, n_items <= 4096) or all FR_PARAM_FULL_C
+   (FP32 relevance, the single-market limits of fr_create), each FR_GRAD_IMPLICIT; every field except
+   n_users, n_items and n_slots must equal cfgs[0]'s (FR_EINVAL). stream: as fr_create. */
 FR_API fr_status fr_batch_create(const fr_config* cfgs, int32_t n_markets, void* stream,
                                  fr_batch** out);
 FR_API fr_status fr_batch_destroy(fr_batch* b);
@@ -207,8 +211,9 @@ FR_API fr_status fr_batch_set_relevance(fr_batch* b, int32_t market, const void*
                                         int64_t ld, int32_t on_device);
 FR_API fr_status fr_batch_set_exposure(fr_batch* b, int32_t market, const double* e, int32_t K);
 /* Times, for every kernel shape, each candidate of rows per thread (8 / 16 / 24 where a kernel
-   exists) and consumers per chunk (4 / 16) with one Sinkhorn launch on the markets' own data and
-   keeps the fastest. Runs by itself before the first solve; the warm-start potentials are kept. */
+   exists; free-cost shapes fix it) and consumers per chunk (4 / 16) with one Sinkhorn launch on the
+   markets' own data and keeps the fastest. Runs by itself before the first solve; the warm-start
+   potentials are kept. */
 FR_API fr_status fr_batch_autotune(fr_batch* b);
 /* n_steps >= 0 ascent steps of Algorithm 1 in every market (first solves every market if stale).
    nsw_trace (host, nullable): [n_steps][n_markets] doubles, F of each market after each step. */
@@ -218,7 +223,7 @@ FR_API fr_status fr_batch_impacts(fr_batch* b, int32_t market, double* imp_out, 
                                   double* nsw_out);
 FR_API fr_status fr_batch_policy(fr_batch* b, int32_t market, int32_t u0, int32_t n_u, float* x_out,
                                  int32_t on_device);
-/* theta of one market (host, n_items floats). */
+/* theta of one market (host, n_items floats); FR_EINVAL for free-cost markets. */
 FR_API fr_status fr_batch_get_theta(fr_batch* b, int32_t market, float* theta_out);
 /* Kernel shapes and the autotuner's choices: *n_buckets shapes; table (nullable, cap rows of 6
    int32): kernel columns, markets, largest n_items, rows per thread, CTA threads, consumers per
@@ -241,8 +246,10 @@ FR_API int64_t fr_launch_count(const fr_ctx* ctx);
    in milliseconds. FR_PARAM_FULL_C: the fused gradient+Adam+Sinkhorn kernel (ms[0]), the
    cross-consumer reduction kernel (ms[1]) and a Sinkhorn-only solve of the same costs (ms[2],
    launched after each step). FR_PARAM_ITEM: the Sinkhorn kernel (ms[0]), the reduction kernel
-   (ms[1]) and the gradient kernel (implicit or adjoint) plus the theta update (ms[2]). Advances
-   the optimiser state like fr_step. */
+   (ms[1]) and the gradient kernel (implicit or adjoint) plus the theta update (ms[2]).
+   FR_PARAM_FULL_C with FR_GRAD_UNROLLED: the Sinkhorn kernel (ms[0]), the reduction (ms[1]) and
+   the adjoint kernel with the optimiser step on C (ms[2]). Advances the optimiser state like
+   fr_step. */
 FR_API fr_status fr_time_kernels(fr_ctx* ctx, int32_t n_steps, double* ms);
 
 /* The compiled kernel variant that serves ctx's Sinkhorn sweep (diagnostics, e.g. to name the

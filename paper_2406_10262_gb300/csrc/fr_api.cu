@@ -34,6 +34,8 @@ struct fr_ctx {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     P1Variant var{};
     P2Variant var2{};
+    P1AdjVariant var1a{};  // free costs, unrolled gradient
+    float* g0 = nullptr;   // free costs, unrolled gradient: [U][nc] starting potentials of the last solve
     int r_bf16 = 0;
     float emax = 0.f;
     double esum = 0.0;  // sum of the K real exposures (uniform-policy impacts of the metrics)
@@ -114,6 +116,9 @@ P1Args p1_args(fr_ctx* c) {
     a.optimizer = c->cfg.optimizer == FR_SGD ? 1 : 0;
     a.warm = c->cfg.warm_start ? 1 : 0;
     a.max_polls = polls_of(c->cfg.max_wait_polls);
+    a.g0 = c->g0;
+    a.ce = c->ce;
+    a.nck = c->nck;
     return a;
 }
 
@@ -163,7 +168,7 @@ ReduceArgs red_args(fr_ctx* c, int after_update) {
         a.Ggn = 1;
     } else {
         a.gn2_part = c->gn2_part;
-        a.Ggn = c->G;
+        a.Ggn = c->unrolled ? c->Gg : c->G;  // the adjoint kernel's grid writes the norm partials
     }
     return a;
 }
@@ -186,6 +191,10 @@ fr_status launch_one_step(fr_ctx* ctx) {
         CU(p2_launch_adam(adam_args(ctx, 1, nullptr), ctx->s));
         CU(p2_launch_sweep(ctx->var2, p2_args(ctx, ctx->part), ctx->s));
         ctx->launches += 3;
+    } else if (ctx->unrolled) {  // adjoint + optimiser, then Sinkhorn on the new costs
+        CU(p1_launch_adj(ctx->var1a, 1, p1_args(ctx), ctx->Gg, ctx->s));
+        CU(p1_launch(ctx->var, MODE_SWEEP, p1_args(ctx), ctx->s));
+        ctx->launches += 2;
     } else {
         CU(p1_launch(ctx->var, MODE_UPDATE_SWEEP, p1_args(ctx), ctx->s));
         ctx->launches += 1;
@@ -195,7 +204,7 @@ fr_status launch_one_step(fr_ctx* ctx) {
     return FR_OK;
 }
 
-int kernels_per_step(const fr_ctx* c) { return c->p2 ? 4 : 2; }
+int kernels_per_step(const fr_ctx* c) { return c->p2 ? 4 : c->unrolled ? 3 : 2; }
 
 fr_status ensure_fresh(fr_ctx* ctx) {
     if (!ctx->have_r || !ctx->have_e)
@@ -354,7 +363,7 @@ void free_all(fr_ctx* c) {
     if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
     cudaFree(c->solve_ctl);
     float* fs[] = {c->C, c->m1, c->m2, c->theta, c->tm1, c->tm2, c->w, c->gpart, c->gL, c->gP,
-                   c->e, c->invb, c->omega, c->part, c->tmp, c->ck};
+                   c->e, c->invb, c->omega, c->part, c->tmp, c->ck, c->g0};
     for (float* p : fs) cudaFree(p);
     double* ds[] = {c->gn2_part, c->imp, c->blk, c->F_hist, c->gn_hist, c->ad_blk, c->gn2_one};
     for (double* p : ds) cudaFree(p);
@@ -449,10 +458,6 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
         return fail(nullptr, FR_EINVAL, "unknown param %d", c.param);
     if (c.grad_mode != FR_GRAD_IMPLICIT && c.grad_mode != FR_GRAD_UNROLLED)
         return fail(nullptr, FR_EINVAL, "unknown grad_mode %d", c.grad_mode);
-    if (c.grad_mode == FR_GRAD_UNROLLED && c.param != FR_PARAM_ITEM)
-        return fail(nullptr, FR_EUNSUPPORTED,
-                    "unrolled differentiation is built for FR_PARAM_ITEM; FR_PARAM_FULL_C "
-                    "differentiates implicitly");
     if (c.grad_mode == FR_GRAD_UNROLLED && c.ckpt_every < 1)
         return fail(nullptr, FR_EINVAL, "ckpt_every must be >= 1 (got %d)", c.ckpt_every);
     if (c.rel_dtype != FR_F32 && c.rel_dtype != FR_BF16)
@@ -468,6 +473,7 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
     const bool p2 = c.param == FR_PARAM_ITEM;
     P1Variant var{};
     P2Variant var2{};
+    P1AdjVariant var1a{};
     if (p2) {
         if (!p2_select(nc, c.n_items, &var2))
             return fail(nullptr, FR_EUNSUPPORTED,
@@ -484,6 +490,11 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
                     "FR_PARAM_FULL_C needs n_cols <= 64 and n_items <= 512 * rows per thread "
                     "(2048 for n_cols <= 16, 1024 for <= 32, 512 for <= 64); got n_cols %d, n_items %d",
                     nc, c.n_items);
+    } else if (c.grad_mode == FR_GRAD_UNROLLED && !p1_select_adj(nc, c.n_items, &var1a)) {
+        return fail(nullptr, FR_EUNSUPPORTED,
+                    "unrolled differentiation of FR_PARAM_FULL_C needs n_cols <= 32 and n_items <= "
+                    "1024 (n_cols <= 16) or 512 (n_cols up to 32); got n_cols %d, n_items %d",
+                    nc, c.n_items);
     }
     ctx = new fr_ctx();
     ctx->cfg = c;
@@ -495,6 +506,7 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
     ctx->ld = (c.n_items + 7) / 8 * 8;
     ctx->var = var;
     ctx->var2 = var2;
+    ctx->var1a = var1a;
     ctx->r_bf16 = c.rel_dtype == FR_BF16 ? 1 : 0;
     ctx->user = (cudaStream_t)stream;
     ctx->unrolled = c.grad_mode == FR_GRAD_UNROLLED;
@@ -560,9 +572,21 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
         CUC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &occ, var.fn[MODE_UPDATE_SWEEP], var.threads,
             p1_smem_bytes(var, MODE_UPDATE_SWEEP, nc, ctx->ld)));
+        if (ctx->unrolled) {
+            const size_t ba = p1_adj_smem(var1a, nc, ctx->ld, ctx->ce, ctx->nck);
+            int og = 0;
+            for (int m = 0; m < 2; ++m) {
+                fr_status st = set_smem(var1a.fn[m], ba);
+                if (st != FR_OK) return bail(st);
+            }
+            CUC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&og, var1a.fn[1], var1a.threads, ba));
+            if (og < 1) return bail(fail(ctx, FR_EUNSUPPORTED, "adjoint kernel does not fit on an SM"));
+            ctx->Gg = std::min(ctx->U, og * sms);
+        }
     }
     if (occ < 1) return bail(fail(ctx, FR_EUNSUPPORTED, "kernel does not fit on an SM"));
     ctx->G = std::min(ctx->U, occ * sms);
+    if (!p2 && ctx->unrolled) ctx->Gg = std::min(ctx->Gg, ctx->G);  // gn2_part holds G partials
     ctx->nblk = reduce_blocks(ctx->I);
 
     const size_t ld = ctx->ld;
@@ -581,6 +605,10 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
         CUC(cudaMalloc(&ctx->gn2_one, sizeof(double)));
     } else {
         const size_t cells = (size_t)ctx->U * nc * ld;
+        if (ctx->unrolled) {
+            CUC(cudaMalloc(&ctx->g0, sizeof(float) * (size_t)ctx->U * nc));
+            CUC(cudaMemset(ctx->g0, 0, sizeof(float) * (size_t)ctx->U * nc));
+        }
         CUC(cudaMalloc(&ctx->C, sizeof(float) * cells));
         CUC(cudaMalloc(&ctx->m1, sizeof(float) * cells));
         CUC(cudaMalloc(&ctx->m2, sizeof(float) * cells));
@@ -792,7 +820,10 @@ fr_status fr_grad(fr_ctx* ctx, const float* omega, float* dparam, float* dr, int
         a.omega = om;
         a.dC = dP;
         a.dr = dR;
-        CU(p1_launch(ctx->var, MODE_GRAD, a, ctx->s));
+        if (ctx->unrolled)
+            CU(p1_launch_adj(ctx->var1a, 0, a, ctx->Gg, ctx->s));
+        else
+            CU(p1_launch(ctx->var, MODE_GRAD, a, ctx->s));
         ctx->launches += 1;
     }
     if (!on_device) {
@@ -984,6 +1015,14 @@ fr_status fr_time_kernels(fr_ctx* ctx, int32_t n_steps, double* ms) {
             CU(reduce_launch(red_args(ctx, 1), ctx->s));
             CU(cudaEventRecord(ev[3], ctx->s));
             ctx->launches += 4;
+        } else if (ctx->unrolled) {  // [adjoint + optimiser] [Sinkhorn] [reduction]
+            CU(p1_launch_adj(ctx->var1a, 1, p1_args(ctx), ctx->Gg, ctx->s));
+            CU(cudaEventRecord(ev[1], ctx->s));
+            CU(p1_launch(ctx->var, MODE_SWEEP, p1_args(ctx), ctx->s));
+            CU(cudaEventRecord(ev[2], ctx->s));
+            CU(reduce_launch(red_args(ctx, 1), ctx->s));
+            CU(cudaEventRecord(ev[3], ctx->s));
+            ctx->launches += 3;
         } else {  // [fused step] [reduction] [Sinkhorn only, same costs]
             CU(p1_launch(ctx->var, MODE_UPDATE_SWEEP, p1_args(ctx), ctx->s));
             CU(cudaEventRecord(ev[1], ctx->s));
@@ -999,7 +1038,7 @@ fr_status fr_time_kernels(fr_ctx* ctx, int32_t n_steps, double* ms) {
         CU(cudaEventElapsedTime(&a, ev[0], ev[1]));
         CU(cudaEventElapsedTime(&b, ev[1], ev[2]));
         CU(cudaEventElapsedTime(&c, ev[2], ev[3]));
-        if (ctx->p2) {
+        if (ctx->p2 || ctx->unrolled) {
             acc[0] += b;  // Sinkhorn kernel
             acc[1] += c;  // reduction
             acc[2] += a;  // gradient + theta update

@@ -1,5 +1,13 @@
-// fr_batch.cu -- many independent markets (each its own instance of Problem (8) under the per-item
-// parametrisation) advanced together: the extern "C" fr_batch_* entry points of include/fairrank.h.
+// fr_batch.cu -- many independent markets (each its own instance of Problem (8), all under the
+// per-item parametrisation or all with free costs) advanced together: the extern "C" fr_batch_*
+// entry points of include/fairrank.h.
+//
+// Free-cost markets: a bucket is one kernel variant of the fused step kernel (column count, rows
+// per thread, tile stride), its markets' consumers are cut into chunks with their own partial rows
+// and squared-gradient partials, and per ascent step every bucket runs one persistent launch of the
+// batched step kernel (gradient, Adam on the costs, Sinkhorn; concurrent branches) followed by one
+// batched impact reduction. The autotuner chooses the chunk length per bucket. The rest of this
+// header describes the per-item markets.
 //
 // Markets are grouped into buckets that share one kernel shape: the column count the kernel is
 // compiled for (exactly 6, 11 or 21 columns, or a padded 8 / 16 / 32 bucket) and the CTA size
@@ -38,6 +46,7 @@ struct BMarket {
     float emax = 0.f;
     bool have_r = false, have_e = false;
     void* r = nullptr;
+    float *C = nullptr, *m1 = nullptr, *m2 = nullptr;  // free costs: C and Adam moments [U][nc][ld]
     float *theta = nullptr, *tm1 = nullptr, *tm2 = nullptr, *w = nullptr, *gL = nullptr,
           *gP = nullptr, *e = nullptr, *invb = nullptr, *omega = nullptr, *part = nullptr,
           *gpart = nullptr;
@@ -50,6 +59,12 @@ struct BBucket {
     int ncb = 0, exact = 0, warps8 = 0, I_max = 0, ld_max = 0;
     std::vector<int> markets;
     P2Variant var{};
+    // free costs: the batched kernel variant (rows per thread and tile stride fixed by the variant
+    // table), its shared memory and occupancy-bound grids for MODE_SWEEP / MODE_UPDATE_SWEEP
+    P1Variant var1{};
+    int tile_stride = 0, threads1 = 0;
+    size_t smem1[2] = {0, 0};
+    int G1[2] = {0, 0};
     int R = 8, cpc = kCpcMin, n_chunks = 0, G_sweep = 0, G_grad = 0, occ_sweep = 0, occ_grad = 0;
     P2Chunk* d_chunks = nullptr;
     size_t smem_sweep = 0, smem_grad = 0;
@@ -57,6 +72,8 @@ struct BBucket {
 
 struct fr_batch {
     fr_config cfg{};  // shared fields (sizes of market 0)
+    bool p1 = false;  // free-cost markets (FR_PARAM_FULL_C), else per-item variables
+    P1Args* d_args_p1 = nullptr;
     int M = 0, device = 0, sms = 0, max_optin = 0;
     int esz = 4;
     std::vector<BMarket> mk;
@@ -150,9 +167,52 @@ P2Args market_args(const fr_batch* b, const BMarket& m, float* part) {
     return a;
 }
 
+// Free costs: the arguments of market m's step kernels (one partial row and one squared-gradient
+// partial per chunk).
+P1Args market_args_p1(const fr_batch* b, const BMarket& m) {
+    P1Args a{};
+    a.U = m.U; a.I = m.I; a.K = m.K; a.nc = m.nc; a.ld = m.ld; a.L = b->cfg.sinkhorn_iters;
+    a.G = m.rows;
+    a.C = m.C; a.m1 = m.m1; a.m2 = m.m2; a.gL = m.gL; a.gP = m.gP;
+    a.r = static_cast<const float*>(m.r); a.e = m.e; a.invb = m.invb; a.omega = m.omega;
+    a.part = m.part; a.gn2_part = m.gn2; a.st = m.st;
+    a.inv_eps_ln2 = (float)(1.0 / (b->cfg.epsilon * std::log(2.0)));
+    a.inv_eps = (float)(1.0 / b->cfg.epsilon);
+    a.lr = (float)b->cfg.lr; a.beta1 = (float)b->cfg.beta1; a.beta2 = (float)b->cfg.beta2;
+    a.adam_eps = (float)b->cfg.adam_eps;
+    a.optimizer = b->cfg.optimizer == FR_SGD ? 1 : 0;
+    a.warm = b->cfg.warm_start ? 1 : 0;
+    a.max_polls = polls_of(b->cfg.max_wait_polls);
+    return a;
+}
+
+fr_status upload_tables_p1(fr_batch* b) {
+    std::vector<P1Args> a1(b->M);
+    std::vector<ReduceArgs> ra(b->M);
+    for (int i = 0; i < b->M; ++i) {
+        BMarket& m = b->mk[i];
+        const BBucket& k = b->bk[m.bucket];
+        m.rows = (m.U + k.cpc - 1) / k.cpc;
+        a1[i] = market_args_p1(b, m);
+        ReduceArgs& r = ra[i];
+        r = ReduceArgs{};
+        r.I = m.I; r.ld = m.ld; r.G = m.rows; r.U = m.U; r.Ggn = m.rows;
+        r.part = m.part; r.gn2_part = m.gn2; r.imp = m.imp; r.omega = m.omega; r.blk = m.blk;
+        r.st = m.st; r.F_hist = m.F_hist; r.gn_hist = m.gn_hist; r.hist_cap = b->hist_cap;
+        r.after_update = 1; r.nblk = reduce_blocks(m.I);
+    }
+    BCU(cudaMemcpyAsync(b->d_args_p1, a1.data(), sizeof(P1Args) * b->M, cudaMemcpyHostToDevice, b->s));
+    BCU(cudaMemcpyAsync(b->d_red, ra.data(), sizeof(ReduceArgs) * b->M, cudaMemcpyHostToDevice, b->s));
+    for (auto& r : ra) r.after_update = 0;
+    BCU(cudaMemcpyAsync(b->d_red0, ra.data(), sizeof(ReduceArgs) * b->M, cudaMemcpyHostToDevice, b->s));
+    BCU(cudaStreamSynchronize(b->s));
+    return FR_OK;
+}
+
 // Device argument tables (market arguments, reduction and update arguments) from the host state;
 // the partial-row counts follow each bucket's chosen chunk length.
 fr_status upload_tables(fr_batch* b) {
+    if (b->p1) return upload_tables_p1(b);
     std::vector<P2Args> as(b->M), ag(b->M);
     std::vector<ReduceArgs> ra(b->M);
     std::vector<P2AdamArgs> aa(b->M);
@@ -197,8 +257,8 @@ std::vector<P2Chunk> make_chunks(const fr_batch* b, const BBucket& k, int cpc) {
         for (int u = 0; u < m.U; u += cpc, ++row) ch.push_back({mi, u, std::min(u + cpc, m.U), row});
     }
     std::stable_sort(ch.begin(), ch.end(), [&](const P2Chunk& x, const P2Chunk& y) {
-        const double cx = (double)(x.u1 - x.u0) * b->mk[x.market].I;
-        const double cy = (double)(y.u1 - y.u0) * b->mk[y.market].I;
+        const double cx = (double)(x.u1 - x.u0) * b->mk[x.market].I * b->mk[x.market].nc;
+        const double cy = (double)(y.u1 - y.u0) * b->mk[y.market].I * b->mk[y.market].nc;
         return cx > cy;
     });
     return ch;
@@ -240,6 +300,62 @@ fr_status configure_bucket(fr_batch* b, BBucket& k, int R, int cpc) {
     return FR_OK;
 }
 
+// Free costs: configures bucket k for chunks of cpc consumers (the rows per thread and the tile
+// stride come with the bucket's kernel variant).
+fr_status configure_bucket_p1(fr_batch* b, BBucket& k, int cpc) {
+    k.cpc = cpc;
+    k.R = k.var1.rows;
+    for (int m = 0; m < 2; ++m) {
+        const int mode = m ? MODE_UPDATE_SWEEP : MODE_SWEEP;
+        k.smem1[m] = p1_smem_bytes_batch(k.var1, mode, k.ld_max);
+        if (k.smem1[m] > (size_t)b->max_optin)
+            return bfail(b, FR_EUNSUPPORTED, "shared memory for %d items and %d columns exceeds the "
+                         "device limit", k.I_max, k.ncb);
+        BCU(raise_smem_limit(k.var1.fb[m], k.smem1[m]));
+    }
+    const std::vector<P2Chunk> ch = make_chunks(b, k, cpc);
+    k.n_chunks = (int)ch.size();
+    for (int m = 0; m < 2; ++m) {
+        int o = 0;
+        BCU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k.var1.fb[m], k.var1.threads, k.smem1[m]));
+        if (o < 1) return bfail(b, FR_EUNSUPPORTED, "bucket kernel does not fit on an SM");
+        k.G1[m] = std::min(k.n_chunks, o * b->sms);
+    }
+    cudaFree(k.d_chunks);
+    k.d_chunks = nullptr;
+    BCU(cudaMalloc(&k.d_chunks, sizeof(P2Chunk) * std::max<size_t>(ch.size(), 1)));
+    BCU(cudaMemcpyAsync(k.d_chunks, ch.data(), sizeof(P2Chunk) * ch.size(), cudaMemcpyHostToDevice, b->s));
+    BCU(cudaStreamSynchronize(b->s));
+    return FR_OK;
+}
+
+P1Batch batch_of_p1(const fr_batch* b, const BBucket& k) {
+    P1Batch bt{};
+    bt.mk = b->d_args_p1;
+    bt.ch = k.d_chunks;
+    bt.n_chunks = k.n_chunks;
+    bt.ld_max = k.ld_max;
+    return bt;
+}
+
+// Free costs: one step kernel per bucket (MODE_SWEEP or MODE_UPDATE_SWEEP), buckets on the side
+// streams.
+fr_status launch_phase_p1(fr_batch* b, int mode) {
+    BCU(cudaEventRecord(b->ev_fork, b->s));
+    for (int j = 0; j < b->nside; ++j) BCU(cudaStreamWaitEvent(b->side[j], b->ev_fork, 0));
+    for (size_t i = 0; i < b->bk.size(); ++i) {
+        const BBucket& k = b->bk[i];
+        BCU(p1_launch_batch(k.var1, mode, batch_of_p1(b, k), k.G1[mode == MODE_UPDATE_SWEEP],
+                            b->side[i % b->nside]));
+        b->launches += 1;
+    }
+    for (int j = 0; j < b->nside; ++j) {
+        BCU(cudaEventRecord(b->ev_join[j], b->side[j]));
+        BCU(cudaStreamWaitEvent(b->s, b->ev_join[j], 0));
+    }
+    return FR_OK;
+}
+
 P2Batch batch_of(const fr_batch* b, const BBucket& k, bool grad) {
     P2Batch bt{};
     bt.mk = grad ? b->d_args_grad : b->d_args_sweep;
@@ -271,7 +387,7 @@ fr_status launch_phase(fr_batch* b, bool grad) {
 }
 
 fr_status launch_solve(fr_batch* b) {
-    fr_status st = launch_phase(b, false);
+    fr_status st = b->p1 ? launch_phase_p1(b, MODE_SWEEP) : launch_phase(b, false);
     if (st != FR_OK) return st;
     BCU(reduce_launch_batch(b->d_red0, b->d_red_map, b->n_red_blocks, b->s));
     b->launches += 1;
@@ -279,6 +395,13 @@ fr_status launch_solve(fr_batch* b) {
 }
 
 fr_status launch_step(fr_batch* b) {
+    if (b->p1) {  // fused gradient + Adam + Sinkhorn per bucket, then the impact reduction
+        fr_status st = launch_phase_p1(b, MODE_UPDATE_SWEEP);
+        if (st != FR_OK) return st;
+        BCU(reduce_launch_batch(b->d_red, b->d_red_map, b->n_red_blocks, b->s));
+        b->launches += 1;
+        return FR_OK;
+    }
     fr_status st = launch_phase(b, true);
     if (st != FR_OK) return st;
     BCU(p2_launch_adam_batch(b->d_adam, b->d_adam_map, b->n_adam_blocks, b->s));
@@ -288,7 +411,9 @@ fr_status launch_step(fr_batch* b) {
     return FR_OK;
 }
 
-int kernels_per_step(const fr_batch* b) { return 2 * (int)b->bk.size() + 2; }
+int kernels_per_step(const fr_batch* b) {
+    return b->p1 ? (int)b->bk.size() + 1 : 2 * (int)b->bk.size() + 2;
+}
 
 fr_status ensure_graph(fr_batch* b) {
     if (b->chunk_exec) return FR_OK;
@@ -365,10 +490,17 @@ fr_status ensure_hist(fr_batch* b, int n) {
 
 fr_status zero_state(fr_batch* b) {
     for (auto& m : b->mk) {
-        BCU(cudaMemsetAsync(m.theta, 0, sizeof(float) * m.ld, b->s));
-        BCU(cudaMemsetAsync(m.tm1, 0, sizeof(float) * m.ld, b->s));
-        BCU(cudaMemsetAsync(m.tm2, 0, sizeof(float) * m.ld, b->s));
-        BCU(launch_exp_theta(m.theta, m.w, m.I, m.ld, b->s));
+        if (b->p1) {  // C = 0 (the uniform policy) and zero moments
+            const size_t cells = sizeof(float) * (size_t)m.U * m.nc * m.ld;
+            BCU(cudaMemsetAsync(m.C, 0, cells, b->s));
+            BCU(cudaMemsetAsync(m.m1, 0, cells, b->s));
+            BCU(cudaMemsetAsync(m.m2, 0, cells, b->s));
+        } else {
+            BCU(cudaMemsetAsync(m.theta, 0, sizeof(float) * m.ld, b->s));
+            BCU(cudaMemsetAsync(m.tm1, 0, sizeof(float) * m.ld, b->s));
+            BCU(cudaMemsetAsync(m.tm2, 0, sizeof(float) * m.ld, b->s));
+            BCU(launch_exp_theta(m.theta, m.w, m.I, m.ld, b->s));
+        }
         BCU(cudaMemsetAsync(m.gL, 0, sizeof(float) * (size_t)m.U * m.nc, b->s));
         BCU(cudaMemsetAsync(m.gP, 0, sizeof(float) * (size_t)m.U * m.nc, b->s));
         DevState z{};
@@ -386,9 +518,13 @@ fr_status time_bucket(fr_batch* b, const BBucket& k, int reps, float* ms) {
     cudaEvent_t e0, e1;
     BCU(cudaEventCreate(&e0));
     BCU(cudaEventCreate(&e1));
-    BCU(p2_launch_sweep_batch(k.var, batch_of(b, k, false), k.G_sweep, b->s));
+    auto sweep = [&]() {
+        return b->p1 ? p1_launch_batch(k.var1, MODE_SWEEP, batch_of_p1(b, k), k.G1[0], b->s)
+                     : p2_launch_sweep_batch(k.var, batch_of(b, k, false), k.G_sweep, b->s);
+    };
+    BCU(sweep());
     BCU(cudaEventRecord(e0, b->s));
-    for (int r = 0; r < reps; ++r) BCU(p2_launch_sweep_batch(k.var, batch_of(b, k, false), k.G_sweep, b->s));
+    for (int r = 0; r < reps; ++r) BCU(sweep());
     BCU(cudaEventRecord(e1, b->s));
     BCU(cudaEventSynchronize(e1));
     float t = 0.f;
@@ -415,6 +551,24 @@ fr_status autotune(fr_batch* b) {
     }
     BCU(cudaStreamSynchronize(b->s));
     for (auto& k : b->bk) {
+        if (b->p1) {  // free costs: the chunk length (rows per thread come with the variant)
+            int bestC = kCpcMin;
+            float best = 1e30f;
+            for (int cpc : kCpcCand) {
+                fr_status st = configure_bucket_p1(b, k, cpc);
+                if (st != FR_OK) return st;
+                if ((st = upload_tables(b)) != FR_OK) return st;
+                float ms = 0.f;
+                if ((st = time_bucket(b, k, 2, &ms)) != FR_OK) return st;
+                if (ms < best) {
+                    best = ms;
+                    bestC = cpc;
+                }
+            }
+            fr_status st = configure_bucket_p1(b, k, bestC);
+            if (st != FR_OK) return st;
+            continue;
+        }
         int bestR = 8, bestC = kCpcMin;
         float best = 1e30f;
         const int Rs[] = {8, 16, 24};
@@ -489,6 +643,7 @@ void free_batch(fr_batch* b) {
     cudaFree(b->d_red);
     cudaFree(b->d_red0);
     cudaFree(b->d_adam);
+    cudaFree(b->d_args_p1);
     cudaFree(b->d_red_map);
     cudaFree(b->d_adam_map);
     cudaFree(b->flags);
@@ -530,8 +685,12 @@ fr_status fr_batch_create(const fr_config* cfgs, int32_t n_markets, void* stream
         const fr_config& c = cfgs[i];
         if (c.n_users < 1 || c.n_items < 1 || c.n_slots < 1 || c.n_slots > c.n_items)
             return bfail(nullptr, FR_EINVAL, "market %d: need n_users >= 1 and 1 <= n_slots <= n_items", i);
-        if (c.param != FR_PARAM_ITEM)
-            return bfail(nullptr, FR_EUNSUPPORTED, "market %d: batches are built for FR_PARAM_ITEM", i);
+        if (c.param != FR_PARAM_ITEM && c.param != FR_PARAM_FULL_C)
+            return bfail(nullptr, FR_EINVAL, "market %d: unknown param %d", i, c.param);
+        if (c.param != c0.param)
+            return bfail(nullptr, FR_EINVAL, "market %d: every market needs market 0's param", i);
+        if (c.param == FR_PARAM_FULL_C && c.rel_dtype != FR_F32)
+            return bfail(nullptr, FR_EUNSUPPORTED, "market %d: FR_PARAM_FULL_C stores relevance in FP32", i);
         if (c.grad_mode != FR_GRAD_IMPLICIT)
             return bfail(nullptr, FR_EUNSUPPORTED, "market %d: batches differentiate implicitly", i);
         if (c.epsilon != c0.epsilon || c.sinkhorn_iters != c0.sinkhorn_iters ||
@@ -542,10 +701,17 @@ fr_status fr_batch_create(const fr_config* cfgs, int32_t n_markets, void* stream
         for (int j = 0; j < 6; ++j)
             if (c.reserved[j]) return bfail(nullptr, FR_EINVAL, "reserved fields must be zero");
         const int nc = fr_num_cols(c.n_items, c.n_slots);
-        if (nc > 32 || warps_at(c.n_items, 8) * 32 > 512)
+        P1Variant v1{};
+        if (c.param == FR_PARAM_FULL_C) {
+            if (!p1_select_batch(nc, c.n_items, &v1))
+                return bfail(nullptr, FR_EUNSUPPORTED,
+                             "market %d: FR_PARAM_FULL_C needs n_cols <= 64 and n_items within the "
+                             "compiled variants (got %d, %d)", i, nc, c.n_items);
+        } else if (nc > 32 || warps_at(c.n_items, 8) * 32 > 512) {
             return bfail(nullptr, FR_EUNSUPPORTED,
                          "market %d: batches need n_cols <= 32 and n_items <= 4096 (got %d, %d)", i,
                          nc, c.n_items);
+        }
     }
     if (!(c0.epsilon > 0.0) || !std::isfinite(c0.epsilon) || c0.sinkhorn_iters < 1 || !(c0.lr > 0.0) ||
         !(c0.beta1 >= 0.0 && c0.beta1 < 1.0) || !(c0.beta2 >= 0.0 && c0.beta2 < 1.0) ||
@@ -555,6 +721,7 @@ fr_status fr_batch_create(const fr_config* cfgs, int32_t n_markets, void* stream
 
     b = new fr_batch();
     b->cfg = c0;
+    b->p1 = c0.param == FR_PARAM_FULL_C;
     b->M = n_markets;
     b->esz = c0.rel_dtype == FR_BF16 ? 2 : 4;
     b->user = (cudaStream_t)stream;
@@ -589,8 +756,33 @@ fr_status fr_batch_create(const fr_config* cfgs, int32_t n_markets, void* stream
         m.nc = fr_num_cols(m.I, m.K);
         m.ld = (m.I + 7) / 8 * 8;
         m.rows = (m.U + kCpcMin - 1) / kCpcMin;
-        const int ncb = ncb_of(m.nc), w8 = warps_at(m.I, 8);
         int kb = -1;
+        if (b->p1) {  // free costs: one bucket per kernel variant (columns, rows, tile stride)
+            P1Variant v{};
+            p1_select_batch(m.nc, m.I, &v);
+            for (size_t j = 0; j < b->bk.size(); ++j) {
+                const P1Variant& w = b->bk[j].var1;
+                if (w.ncb == v.ncb && w.rows == v.rows && w.exact == v.exact &&
+                    w.tile_stride == v.tile_stride)
+                    kb = (int)j;
+            }
+            if (kb < 0) {
+                BBucket k;
+                k.ncb = v.ncb;
+                k.exact = v.exact;
+                k.var1 = v;
+                b->bk.push_back(k);
+                kb = (int)b->bk.size() - 1;
+            }
+            BBucket& k = b->bk[kb];
+            k.var1.threads = std::max(k.var1.threads, v.threads);  // the bucket's largest market
+            k.markets.push_back(i);
+            k.I_max = std::max(k.I_max, m.I);
+            k.ld_max = std::max(k.ld_max, m.ld);
+            m.bucket = kb;
+            continue;
+        }
+        const int ncb = ncb_of(m.nc), w8 = warps_at(m.I, 8);
         for (size_t j = 0; j < b->bk.size(); ++j)
             if (b->bk[j].ncb == ncb && b->bk[j].warps8 == w8) kb = (int)j;
         if (kb < 0) {
@@ -620,19 +812,25 @@ fr_status fr_batch_create(const fr_config* cfgs, int32_t n_markets, void* stream
         total += (bytes + 255) / 256 * 256;
         return o;
     };
-    struct Off { size_t r, th, m1, m2, w, gL, gP, e, lb, om, part, gpart, imp, blk, ad, gn2, st; };
+    struct Off { size_t r, th, m1, m2, w, gL, gP, e, lb, om, part, gpart, imp, blk, ad, gn2, st,
+                 C, c1, c2; };
     std::vector<Off> off(n_markets);
+    const size_t per_item = b->p1 ? 0 : 1, per_cell = b->p1 ? 1 : 0;
     for (int i = 0; i < n_markets; ++i) {
         const BMarket& m = b->mk[i];
         const size_t ld = m.ld, un = (size_t)m.U * m.nc;
         Off& o = off[i];
         o.r = piece((size_t)m.U * ld * b->esz);
-        o.th = piece(4 * ld); o.m1 = piece(4 * ld); o.m2 = piece(4 * ld); o.w = piece(4 * ld);
+        o.th = piece(4 * ld * per_item); o.m1 = piece(4 * ld * per_item);
+        o.m2 = piece(4 * ld * per_item); o.w = piece(4 * ld * per_item);
+        o.C = piece(4 * un * ld * per_cell); o.c1 = piece(4 * un * ld * per_cell);
+        o.c2 = piece(4 * un * ld * per_cell);
         o.gL = piece(4 * un); o.gP = piece(4 * un);
         o.e = piece(4 * (size_t)m.nc); o.lb = piece(4 * (size_t)m.nc); o.om = piece(4 * ld);
-        o.part = piece(4 * (size_t)m.rows * ld); o.gpart = piece(4 * (size_t)m.rows * ld);
+        o.part = piece(4 * (size_t)m.rows * ld); o.gpart = piece(4 * (size_t)m.rows * ld * per_item);
         o.imp = piece(8 * ld); o.blk = piece(16 * (size_t)reduce_blocks(m.I));
-        o.ad = piece(8 * (size_t)p2_adam_blocks(m.I)); o.gn2 = piece(8);
+        o.ad = piece(8 * (size_t)p2_adam_blocks(m.I) * per_item);
+        o.gn2 = piece(8 * (b->p1 ? (size_t)m.rows : 1));  // free costs: one partial per chunk row
         o.st = piece(sizeof(DevState));
     }
     BCC(cudaMalloc(&b->arena, total));
@@ -649,28 +847,34 @@ fr_status fr_batch_create(const fr_config* cfgs, int32_t n_markets, void* stream
         m.imp = (double*)(base + o.imp); m.blk = (double*)(base + o.blk);
         m.ad_blk = (double*)(base + o.ad); m.gn2 = (double*)(base + o.gn2);
         m.st = (DevState*)(base + o.st);
+        if (b->p1) {
+            m.C = (float*)(base + o.C); m.m1 = (float*)(base + o.c1); m.m2 = (float*)(base + o.c2);
+        }
     }
     BCC(cudaMalloc(&b->d_args_sweep, sizeof(P2Args) * n_markets));
     BCC(cudaMalloc(&b->d_args_grad, sizeof(P2Args) * n_markets));
     BCC(cudaMalloc(&b->d_red, sizeof(ReduceArgs) * n_markets));
     BCC(cudaMalloc(&b->d_red0, sizeof(ReduceArgs) * n_markets));
     BCC(cudaMalloc(&b->d_adam, sizeof(P2AdamArgs) * n_markets));
+    if (b->p1) BCC(cudaMalloc(&b->d_args_p1, sizeof(P1Args) * n_markets));
     BCC(cudaMalloc(&b->flags, sizeof(int) * 4));
     BCC(cudaMallocHost(&b->st_host, sizeof(DevState) * n_markets));
     std::vector<int2> rmap, amap;
     for (int i = 0; i < n_markets; ++i) {
         for (int j = 0; j < reduce_blocks(b->mk[i].I); ++j) rmap.push_back(make_int2(i, j));
-        for (int j = 0; j < p2_adam_blocks(b->mk[i].I); ++j) amap.push_back(make_int2(i, j));
+        if (!b->p1)
+            for (int j = 0; j < p2_adam_blocks(b->mk[i].I); ++j) amap.push_back(make_int2(i, j));
     }
     b->n_red_blocks = (int)rmap.size();
     b->n_adam_blocks = (int)amap.size();
     BCC(cudaMalloc(&b->d_red_map, sizeof(int2) * rmap.size()));
-    BCC(cudaMalloc(&b->d_adam_map, sizeof(int2) * amap.size()));
+    BCC(cudaMalloc(&b->d_adam_map, sizeof(int2) * std::max<size_t>(amap.size(), 1)));
     BCC(cudaMemcpy(b->d_red_map, rmap.data(), sizeof(int2) * rmap.size(), cudaMemcpyHostToDevice));
-    BCC(cudaMemcpy(b->d_adam_map, amap.data(), sizeof(int2) * amap.size(), cudaMemcpyHostToDevice));
+    if (!amap.empty())
+        BCC(cudaMemcpy(b->d_adam_map, amap.data(), sizeof(int2) * amap.size(), cudaMemcpyHostToDevice));
 #undef BCC
     for (auto& k : b->bk) {
-        fr_status st = configure_bucket(b, k, 8, kCpcMin);
+        fr_status st = b->p1 ? configure_bucket_p1(b, k, kCpcMin) : configure_bucket(b, k, 8, kCpcMin);
         if (st != FR_OK) return bail(st);
     }
     fr_status st = ensure_hist(b, 64);  // also uploads the argument tables
@@ -826,7 +1030,10 @@ fr_status fr_batch_policy(fr_batch* b, int32_t market, int32_t u0, int32_t n_u, 
         if ((st = ensure_tmp(b, bytes)) != FR_OK) return st;
         dst = b->tmp;
     }
-    BCU(launch_p2_policy(market_args(b, m, m.part), u0, n_u, dst, b->s));
+    if (b->p1)
+        BCU(launch_policy(market_args_p1(b, m), u0, n_u, dst, b->s));
+    else
+        BCU(launch_p2_policy(market_args(b, m, m.part), u0, n_u, dst, b->s));
     b->launches += n_u > 0;
     if (!on_device && n_u > 0) BCU(cudaMemcpyAsync(x_out, dst, bytes, cudaMemcpyDeviceToHost, b->s));
     BCU(cudaStreamSynchronize(b->s));
@@ -837,6 +1044,7 @@ fr_status fr_batch_get_theta(fr_batch* b, int32_t market, float* theta_out) {
     fr_status st = FR_OK;
     if (!checked(b, market, &st)) return st;
     if (!theta_out) return bfail(b, FR_EINVAL, "theta_out is NULL");
+    if (b->p1) return bfail(b, FR_EINVAL, "free-cost markets have no per-item variables");
     BJoin j(b);
     const BMarket& m = b->mk[market];
     BCU(cudaMemcpyAsync(theta_out, m.theta, sizeof(float) * m.I, cudaMemcpyDeviceToHost, b->s));
@@ -855,7 +1063,7 @@ fr_status fr_batch_tuning(const fr_batch* b, int32_t* n_buckets, int32_t* table,
             t[1] = (int32_t)k.markets.size();
             t[2] = k.I_max;
             t[3] = k.R;
-            t[4] = k.var.threads;
+            t[4] = b->p1 ? k.var1.threads : k.var.threads;
             t[5] = k.cpc;
         }
     return FR_OK;

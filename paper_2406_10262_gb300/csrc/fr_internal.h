@@ -62,6 +62,9 @@ struct P1Args {
     int optimizer;        // 0 Adam, 1 SGD
     int warm;
     unsigned max_polls;   // bounded waits: polls before a wait gives up (0: expires at once)
+    float* g0;            // unrolled gradient: [U][nc] log2-unit potentials each solve started
+                          // from, stored by the sweeps when non-null
+    int ce, nck;          // unrolled gradient: checkpoint interval and count ceil(L / ce)
 };
 
 struct ReduceArgs {
@@ -192,9 +195,35 @@ struct P1Variant {
     int threads;          // CTA size
     size_t smem;          // dynamic shared memory (bytes) of the largest mode
     const void* fn[3];    // kernels by Mode
+    const void* fb[2];    // batched-market kernels (argument: P1Batch) for MODE_SWEEP and
+                          // MODE_UPDATE_SWEEP; set by p1_select_batch only
+};
+
+// Batched free-cost markets: a launch walks a chunk list (P2Chunk: market, consumer range, partial
+// row); every market's arguments are in a device table. All markets of a launch share the kernel
+// variant; the shared-memory layout is the variant's at ld_max.
+struct P1Batch {
+    const P1Args* mk;
+    const P2Chunk* ch;
+    int n_chunks;
+    int ld_max;
 };
 
 bool p1_select(int nc, int I, P1Variant* out);
+// The same variant table as p1_select, with fb set (and fn left null).
+bool p1_select_batch(int nc, int I, P1Variant* out);
+size_t p1_smem_bytes_batch(const P1Variant& v, int mode, int ld_max);
+cudaError_t p1_launch_batch(const P1Variant& v, int mode, const P1Batch& bt, int G, cudaStream_t s);
+
+// Unrolled gradient of the free-cost parametrisation (fr_p1_adj.cu): fn[0] writes dL/dC and
+// dL/dr, fn[1] applies the optimiser step to C (mode = 0 / 1).
+struct P1AdjVariant {
+    int ncb, rows, exact, threads;
+    const void* fn[2];
+};
+bool p1_select_adj(int nc, int I, P1AdjVariant* out);
+size_t p1_adj_smem(const P1AdjVariant& v, int nc, int ld, int ce, int nck);
+cudaError_t p1_launch_adj(const P1AdjVariant& v, int mode, const P1Args& a, int G, cudaStream_t s);
 cudaError_t p1_launch(const P1Variant& v, int mode, const P1Args& a, cudaStream_t s);
 size_t p1_smem_bytes(const P1Variant& v, int mode, int nc, int ld);
 cudaError_t reduce_launch(const ReduceArgs& a, cudaStream_t s);

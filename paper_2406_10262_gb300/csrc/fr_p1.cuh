@@ -159,7 +159,7 @@ __host__ __device__ inline size_t smem_layout(int ncb, int nc, int ld, int W, in
 // thread of the CTA must be done reading them (the caller sits after a __syncthreads).
 __device__ __forceinline__ void stage_consumer(const P1Args& a, int un, int nc, int ld,
                                                const Smem& s, bool prefetch_moments, int ts) {
-    if (un >= a.U) return;
+    if (un < 0 || un >= a.U) return;
     const unsigned tile = (unsigned)(sizeof(float) * (size_t)nc * ld);
     const unsigned row = (unsigned)(sizeof(float) * ld);
     fence_proxy_async_smem();
@@ -187,7 +187,7 @@ __device__ __forceinline__ void stage_consumer(const P1Args& a, int un, int nc, 
 // L2 while the current consumer's solve still holds the shared tile.
 __device__ __forceinline__ void prefetch_consumer(const P1Args& a, int un, int nc, int ld,
                                                   bool moments) {
-    if (un >= a.U) return;
+    if (un < 0 || un >= a.U) return;
     const unsigned tile = (unsigned)(sizeof(float) * (size_t)nc * ld);
     bulk_prefetch_l2(a.C + (size_t)un * nc * ld, tile);
     bulk_prefetch_l2(a.r + (size_t)un * ld, (unsigned)(sizeof(float) * ld));
@@ -278,8 +278,9 @@ constexpr float TS_DRIFT = 30.f;
 // is one 8- or 16-byte load per lane and conflict-free (consecutive lanes, consecutive words), at
 // a compile-time offset k LDS from the block's base (no address arithmetic per load), and no
 // costs stay in registers between iterations, which is what allows eight rows per thread at four
-// CTAs per SM. The impacts of a block's rows go straight into the CTA's partial row
-// part[blockIdx] (written by its first consumer, accumulated by the later ones).
+// CTAs per SM. The impacts of a block's rows go straight into the partial row part_row (written by
+// its first consumer, first_row, and accumulated by the later ones). (na, nu) is the consumer the
+// CTA solves next (nu < 0: none), prefetched into L2 near the end of this solve.
 //
 // The tile holds one of two forms of the row-shifted kernel; both give the same policy in exact
 // arithmetic (a factor per column or per row cancels in x_ik = p_ik / sum_k p_ik).
@@ -297,7 +298,9 @@ constexpr float TS_DRIFT = 30.f;
 // Each thread rewrites only its own rows, which only it reads during the solve.
 template <int NCB, int R, int BR, int LDS, bool EXACT, int MODE>
 __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u, int nc,
-                                           float (&gm)[(NCB + 31) / 32], int& par) {
+                                           float (&gm)[(NCB + 31) / 32], int& par,
+                                           float* part_row, bool first_row, const P1Args& na,
+                                           int nu) {
     static_assert((BR == 2 || BR == 4) && R % BR == 0, "blocks of two or four rows");
     constexpr int GPL = (NCB + 31) / 32;
     constexpr int NB = R / BR, NP = BR / 2;
@@ -558,10 +561,10 @@ __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u
                             }
                         }
                     }
-                    float* pp = a.part + (size_t)blockIdx.x * ld + rb;
+                    float* pp = part_row + rb;
                     f2 rr[NP], acc[NP];
                     RBk::load(a.r + (size_t)u * ld + rb, rr);
-                    if (u == (int)blockIdx.x) {
+                    if (first_row) {
 #pragma unroll
                         for (int q = 0; q < NP; ++q) acc[q] = 0ull;
                     } else {
@@ -602,21 +605,29 @@ __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u
         // prefetching at once do not evict them again before the copy after the solve (its Adam
         // moments follow at the start of its gradient step, closer to their use)
         if (l == (a.L > 8 ? a.L - 8 : 0) && tid == 0)
-            prefetch_consumer(a, u + gridDim.x, nc, ld, false);
+            prefetch_consumer(na, nu, EXACT ? NCB : na.nc, na.ld, false);
     };
     for (int l = 0; l < a.L - 1; ++l) iteration(l, BoolTag<false>{});
     iteration(a.L - 1, BoolTag<true>{});
 }
 
-// Launch bound: 512 threads, except the tile sweep of more than 16 columns, which serves at most
-// 2048 items (256 threads) and may then use up to 255 registers per thread.
+// One consumer u of market a, as one step of a CTA's persistent loop: the gradient step (update
+// modes) and the Sinkhorn solve (sweep modes). The consumer's tile was staged into shared memory
+// by the previous step (or before the loop); (na, nu) is the consumer this CTA solves next (nu < 0:
+// none), whose tile this step stages. Impacts go into part_row (the tile sweep: written by the
+// row's first consumer, first_row) or are added to acc_imp (the register sweep; the caller writes
+// them out); the squared gradient is added to gn2. Returns false if a bounded wait expired (the CTA
+// then stops). The per-market shared arrays (e, 1/b, omega, the Adam coefficients) must hold a's.
 template <int NCB, int R, bool EXACT, int MODE, int TS>
-__global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(const P1Args a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ bool p1_consumer(const P1Args& a, const Smem& s, int u, const P1Args& na,
+                                            int nu, float* part_row, bool first_row,
+                                            float (&acc_imp)[R], double& gn2, int& par,
+                                            unsigned& phase) {
     constexpr int GPL = (NCB + 31) / 32;
     constexpr bool REG_GRAM = reg_gram(NCB);
     constexpr bool PAIR = R % 2 == 0;
     const int nc = EXACT ? NCB : a.nc;
+    const int ncn = EXACT ? NCB : na.nc;
     const int ncp = ncp_of(nc);
     const int ncx = ncx_of(nc, NCB);
     const int n = nc - 1;
@@ -626,9 +637,587 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
     const int i0 = tid * R;
     const bool any_row = i0 < I;
     const float sc = a.inv_eps_ln2;
+    const int lds = TS ? TS : ld;  // column stride of the shared tile
+    (void)ncn;
+    (void)n;
+    (void)any_row;
+    (void)ncx;
+    // omega_i: the staged copy, or (tile sweep) global memory; omega has ld entries, zero beyond I
+    auto om_at = [&](int i) { return TS ? __ldg(a.omega + i) : s.om[i]; };
+    {
+            const size_t tile = (size_t)u * nc * ld;
+            const float* __restrict__ r_u = a.r + (size_t)u * ld;
+            auto r_at = [&](int i) { return TS ? __ldg(r_u + i) : s.r[i]; };
+            float gm[GPL];  // column potentials of the columns this lane holds (same in every warp)
+    #pragma unroll
+            for (int j = 0; j < GPL; ++j) {
+                const int col = j * 32 + lane;
+                gm[j] = (a.warm && col < nc) ? a.gL[(size_t)u * nc + col] : 0.f;
+                // the potentials this solve starts from, for the unrolled gradient's forward re-run
+                if (MODE != MODE_GRAD && a.g0 && warp == 0 && col < nc) a.g0[(size_t)u * nc + col] = gm[j];
+            }
+            if (MODE != MODE_SWEEP && tid < ncx) s.gp[tid] = tid < nc ? a.gP[(size_t)u * nc + tid] : 0.f;
+            // the consumer's tile was staged one consumer ago (the register sweep) or right after the
+            // previous solve (the tile sweep), and it is the only copy in flight. The wait is bounded:
+            // if it expires, the CTA records a timeout, waits (with the default bound) for the copy to
+            // land and stops, so that no bulk copy is still writing into its shared memory when it
+            // leaves. In the tile sweep's update modes the first gradient pass reads the costs from
+            // global memory (L2, where the previous solve prefetched them) while the copy lands, and
+            // the wait follows that pass.
+            constexpr bool LATE_WAIT = TS != 0 && MODE != MODE_SWEEP;
+            bool tile_ok = true;  // the same in every thread (cta_wait_or_drain)
+            if constexpr (!LATE_WAIT) {
+                tile_ok = cta_wait_or_drain(s.bar, phase, a.max_polls, kDefaultPolls, &a.st->err, 4);
+                phase ^= 1u;
+            } else {
+                __syncthreads();  // s.gp / s.e / s.ib / s.om / s.coef visible
+            }
+            if (!tile_ok) return false;
+
+            if constexpr (MODE != MODE_SWEEP) {
+                if (TS && MODE == MODE_UPDATE_SWEEP && a.optimizer == 0 && tid == 0) {
+                    // the consumer's Adam moments into L2 while the gradient passes run
+                    const unsigned tb = (unsigned)(sizeof(float) * (size_t)nc * ld);
+                    bulk_prefetch_l2(a.m1 + tile, tb);
+                    bulk_prefetch_l2(a.m2 + tile, tb);
+                }
+                // ---------------- gradient of F at the previous policy ------------------------------
+                // x_ik = 2^(g'_k - c'_ik - lse_i) is re-formed from the staged tile and the row
+                // log-normaliser lse_i of the first pass.
+                {
+                    float acc[3][NCB];  // q, cs, X^T h partials
+    #pragma unroll
+                    for (int k = 0; k < NCB; ++k) acc[0][k] = acc[1][k] = acc[2][k] = 0.f;
+                    for (int i = tid; i < I; i += T) {
+                        float x[NCB];
+                        float M = -INFINITY;
+    #pragma unroll
+                        for (int k = 0; k < NCB; ++k) {
+                            float c = 0.f;
+                            if (EXACT || k < nc)
+                                c = LATE_WAIT ? __ldcg(a.C + tile + (size_t)k * ld + i) : s.C[k * lds + i];
+                            x[k] = (EXACT || k < nc) ? s.gp[k] - c * sc : -INFINITY;
+                            M = fmaxf(M, x[k]);
+                        }
+                        float S = 0.f;
+    #pragma unroll
+                        for (int k = 0; k < NCB; ++k) {
+                            x[k] = ex2(x[k] - M);
+                            S += x[k];
+                        }
+                        const float inv = rcp_approx(S);  // S in [1, m]: the row max contributes 1
+                        const float wr = om_at(i) * r_at(i);  // dF/dx_ik = wr_i e_k
+                        float hh = 0.f, vi = 0.f;
+    #pragma unroll
+                        for (int k = 0; k < NCB; ++k) {
+                            x[k] *= inv;
+                            hh += x[k] * (wr * s.e[k]);
+                            if (MODE == MODE_GRAD && k < a.K) vi += s.e[k] * x[k];
+                        }
+    #pragma unroll
+                        for (int k = 0; k < NCB; ++k) {
+                            acc[0][k] += x[k] * (wr * s.e[k]);
+                            acc[1][k] += x[k];
+                            acc[2][k] += x[k] * hh;
+                            if constexpr (!REG_GRAM) {
+                                if (EXACT || k < nc) s.X[k * ld + i] = x[k];
+                            }
+                        }
+                        s.lse[i] = M + lg2_approx(S);
+                        s.h[i] = hh;
+                        // dF/dr(u,i) = (dF/dImp_i) sum_{k<K} e_k x_ik (C does not depend on r)
+                        if (MODE == MODE_GRAD && a.dr) a.dr[(size_t)u * I + i] = om_at(i) * vi;
+                    }
+                    cta_reduce<NCB, 3>(acc, nc, s.red, s.out, ncp);  // s.out: [q | cs | X^T h]
+                }
+                if constexpr (LATE_WAIT) {  // the shared tile from here on
+                    tile_ok = cta_wait_or_drain(s.bar, phase, a.max_polls, kDefaultPolls, &a.st->err, 4);
+                    phase ^= 1u;
+                    if (!tile_ok) return false;
+                }
+                // Gram block M[0:n,0:n] of diag(cs) - X^T X; rows of x sum to 1, so the diagonal is
+                // sum_i x_ik (1 - x_ik) without cancellation.
+                if constexpr (REG_GRAM) {
+                    float* gout = s.out + 3 * ncp;
+                    gram_block<NCB, EXACT>(s, nc, I, lds, sc, gout);
+                    float* Af = reinterpret_cast<float*>(s.A);
+                    float* rf = reinterpret_cast<float*>(s.rhs);
+                    for (int idx = tid; idx < n * n; idx += T) {
+                        int k = idx / n, m = idx % n;
+                        if (k > m) { const int t = k; k = m; m = t; }
+                        Af[idx] = gout[k * (NCB - 1) - k * (k - 1) / 2 + (m - k)];
+                    }
+                    for (int k = tid; k < ncx; k += T) {
+                        if (k < n) rf[k] = s.out[k] - s.out[2 * ncp + k];
+                        s.beta[k] = 0.f;
+                    }
+                    __syncthreads();
+                    if (warp == 0) warp_cholesky_solve_f32<NCB - 1>(Af, rf, n, s.Lt, s.beta, lane);
+                    __syncthreads();
+                } else {
+                    for (int pidx = warp; pidx < n * (n + 1) / 2; pidx += W) {
+                        int k = 0, rem = pidx;
+                        while (rem >= n - k) { rem -= n - k; ++k; }
+                        const int m = k + rem;
+                        const float* xk = s.X + k * ld;
+                        const float* xm = s.X + m * ld;
+                        float sum = 0.f;
+                        if (k == m) {
+                            for (int i = lane; i < I; i += 32) sum += xk[i] * (1.f - xk[i]);
+                        } else {
+                            for (int i = lane; i < I; i += 32) sum -= xk[i] * xm[i];
+                        }
+    #pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
+                        if (lane == 0) {
+                            s.A[k * n + m] = (double)sum;
+                            s.A[m * n + k] = (double)sum;
+                        }
+                    }
+                    for (int k = tid; k < n; k += T)
+                        s.rhs[k] = (double)s.out[k] - (double)s.out[2 * ncp + k];
+                    __syncthreads();
+                    if (warp == 0) warp_cholesky_solve(s.A, s.rhs, n, lane);
+                    __syncthreads();
+                    for (int k = tid; k < ncx; k += T) s.beta[k] = k < n ? (float)s.rhs[k] : 0.f;
+                    __syncthreads();
+                }
+                // alpha_i = h_i - sum_k x_ik beta_k
+                for (int i = tid; i < I; i += T) {
+                    const float l = s.lse[i];
+                    float sb = 0.f;
+    #pragma unroll
+                    for (int k = 0; k < NCB; ++k)
+                        if (EXACT || k < nc) sb += ex2(s.gp[k] - s.C[k * lds + i] * sc - l) * s.beta[k];
+                    s.alpha[i] = s.h[i] - sb;
+                }
+                __syncthreads();
+                // gradient and Adam over the tile: each thread takes four consecutive items (float4)
+                // and runs through the columns, so the per-item values (lse, alpha, omega r) are read
+                // once per four items and eleven columns, and no index needs a division
+                const float step_size = s.coef[0], inv_bc2s = 1.f / s.coef[1];
+                float* __restrict__ Cg = a.C;
+                float* __restrict__ m1g = a.m1;
+                float* __restrict__ m2g = a.m2;
+                float gsq = 0.f;
+                for (int i4 = tid; i4 * 4 < I; i4 += T) {
+                    const int i = i4 * 4;
+                    const float4 l4 = reinterpret_cast<const float4*>(s.lse)[i4];
+                    const float4 a4 = reinterpret_cast<const float4*>(s.alpha)[i4];
+                    const float4 o4 = TS ? __ldg(reinterpret_cast<const float4*>(a.omega) + i4)
+                                         : reinterpret_cast<const float4*>(s.om)[i4];
+                    const float4 r4 = TS ? __ldg(reinterpret_cast<const float4*>(r_u) + i4)
+                                         : reinterpret_cast<const float4*>(s.r)[i4];
+                    const float lv[4] = {l4.x, l4.y, l4.z, l4.w}, av[4] = {a4.x, a4.y, a4.z, a4.w};
+                    const float wv[4] = {o4.x * r4.x, o4.y * r4.y, o4.z * r4.z, o4.w * r4.w};
+                    // Adam moments two columns ahead (their loads would otherwise wait for the stores
+                    // of the previous column: the compiler cannot tell the addresses apart)
+                    constexpr bool ADAM = MODE == MODE_UPDATE_SWEEP;
+                    const bool adam = ADAM && a.optimizer == 0;
+                    const int ncc = EXACT ? NCB : nc;
+                    float4 mA = make_float4(0.f, 0.f, 0.f, 0.f), vA = mA, mB = mA, vB = mA;
+                    auto ldmv = [&](int k, float4& m, float4& v) {
+                        const size_t off = tile + (size_t)k * ld + i;
+                        m = *reinterpret_cast<const float4*>(m1g + off);
+                        v = *reinterpret_cast<const float4*>(m2g + off);
+                    };
+                    if (adam) {
+                        ldmv(0, mA, vA);
+                        if (1 < ncc) ldmv(1, mB, vB);
+                    }
+    #pragma unroll 4
+                    for (int k = 0; k < NCB; ++k) {
+                        if (!EXACT && k >= nc) break;
+                        const float4 mm4 = mA, vv4 = vA;
+                        mA = mB;
+                        vA = vB;
+                        if (adam && k + 2 < ncc) ldmv(k + 2, mB, vB);
+                        const int qs = k * (lds / 4) + i4;  // float4 index in the shared tile
+                        const float4 c4 = reinterpret_cast<const float4*>(s.C)[qs];
+                        const float gpk = s.gp[k], ek = s.e[k], bk = s.beta[k];
+                        float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+                        float gr[4];
+    #pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const bool valid = i + j < I;
+                            const float x = valid ? ex2(gpk - cv[j] * sc - lv[j]) : 0.f;
+                            gr[j] = valid ? -a.inv_eps * x * (wv[j] * ek - av[j] - bk) : 0.f;
+                            gsq += gr[j] * gr[j];
+                        }
+                        if constexpr (MODE == MODE_GRAD) {
+    #pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                if (i + j < I) a.dC[((size_t)u * I + i + j) * nc + k] = gr[j];
+                        } else {
+                            const size_t off = tile + (size_t)k * ld + i;
+                            if (a.optimizer == 1) {
+    #pragma unroll
+                                for (int j = 0; j < 4; ++j) cv[j] += a.lr * gr[j];
+                            } else {
+                                float mm[4] = {mm4.x, mm4.y, mm4.z, mm4.w};
+                                float vv[4] = {vv4.x, vv4.y, vv4.z, vv4.w};
+    #pragma unroll
+                                for (int j = 0; j < 4; ++j) {
+                                    mm[j] = a.beta1 * mm[j] + (1.f - a.beta1) * gr[j];
+                                    vv[j] = a.beta2 * vv[j] + (1.f - a.beta2) * gr[j] * gr[j];
+                                    // sqrt(v) / bc2s + eps with MUFU rsqrt / rcp (IEEE sqrt and
+                                    // division are long instruction sequences on the per-cell path)
+                                    const float sq = vv[j] > 0.f ? vv[j] * rsqrtf(vv[j]) : 0.f;
+                                    cv[j] += __fdividef(step_size * mm[j], fmaf(sq, inv_bc2s, a.adam_eps));
+                                }
+                                *reinterpret_cast<float4*>(m1g + off) = make_float4(mm[0], mm[1], mm[2], mm[3]);
+                                *reinterpret_cast<float4*>(m2g + off) = make_float4(vv[0], vv[1], vv[2], vv[3]);
+                            }
+                            const float4 cn = make_float4(cv[0], cv[1], cv[2], cv[3]);
+                            *reinterpret_cast<float4*>(Cg + off) = cn;
+                            reinterpret_cast<float4*>(s.C)[qs] = cn;
+                        }
+                    }
+                }
+                gn2 += (double)gsq;
+                if constexpr (MODE == MODE_GRAD) {
+                    __syncthreads();
+                    if (tid == 0) stage_consumer(na, nu, ncn, na.ld, s, false, TS);
+                    return true;  // no solve in gradient mode
+                }
+                __syncthreads();  // updated tile visible
+            }
+
+            // ---------------- Sinkhorn solve on the consumer's (new) costs ----------------------------
+            if constexpr (TS != 0) {
+                tile_sweep<NCB, R, 2, TS, EXACT, MODE>(a, s, u, nc, gm, par, part_row, first_row, na, nu);
+            } else {
+            float rr[R];
+            bool vr[R];
+    #pragma unroll
+            for (int r = 0; r < R; ++r) rr[r] = 0.f;
+            if (any_row) ldv<R>(rr, s.r + i0);
+    #pragma unroll
+            for (int r = 0; r < R; ++r) vr[r] = i0 + r < I;
+            float c[R][NCB];
+            {
+                float gk[NCB];
+                bcast_g<NCB, GPL>(gm, gk);
+    #pragma unroll
+                for (int k = 0; k < NCB; ++k) {
+                    float tmp[R];
+    #pragma unroll
+                    for (int r = 0; r < R; ++r) tmp[r] = 0.f;
+                    if ((EXACT || k < nc) && any_row) ldv<R>(tmp, s.C + k * lds + i0);
+    #pragma unroll
+                    for (int r = 0; r < R; ++r) c[r][k] = tmp[r];
+                }
+    #pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    float M = 0.f;
+                    if (vr[r]) {
+                        M = -INFINITY;
+    #pragma unroll
+                        for (int k = 0; k < NCB; ++k)
+                            if (EXACT || k < nc) M = fmaxf(M, gk[k] - c[r][k] * sc);
+                    }
+    #pragma unroll
+                    for (int k = 0; k < NCB; ++k)
+                        c[r][k] = (vr[r] && (EXACT || k < nc)) ? c[r][k] * sc + M : INFINITY;
+                }
+            }
+            // the last iteration (which also writes g^(L-1) and adds the impacts) as a separate
+            // instantiation, where a second copy of the body fits the registers
+            constexpr bool PEEL = NCB <= 11;
+            if constexpr (PAIR) {
+                constexpr int RP = R / 2;
+                // Up to 11 columns the pairs start in the exponential form of the tile sweep (E pairs in
+                // c2, G_k = 2^(g'_k - g0_k) per iteration, one packed multiply per two cells) and switch
+                // to the log form (c~ pairs rebuilt from the costs in global memory at the current g')
+                // when a potential drifts past TS_DRIFT; wider buckets keep the log form throughout.
+                constexpr bool EXPF_OK = NCB <= 11;
+                float g0m[GPL];  // g' at the start of the solve (this lane's columns)
+    #pragma unroll
+                for (int j = 0; j < GPL; ++j) g0m[j] = gm[j];
+                f2 c2[RP][NCB];
+                {
+                    float gk[NCB];
+                    bcast_g<NCB, GPL>(gm, gk);
+    #pragma unroll
+                    for (int rp = 0; rp < RP; ++rp)
+    #pragma unroll
+                        for (int k = 0; k < NCB; ++k) {
+                            if constexpr (EXPF_OK)  // rows and columns outside the tile: c~ = inf, E = 0
+                                c2[rp][k] = pk(ex2(gk[k] - c[2 * rp][k]), ex2(gk[k] - c[2 * rp + 1][k]));
+                            else
+                                c2[rp][k] = pk(c[2 * rp][k], c[2 * rp + 1][k]);
+                        }
+                }
+                bool lg = !EXPF_OK;  // c2 holds the log form (the same in every thread of the CTA)
+                auto iteration = [&](int l, auto tag) {
+                    const bool last = last_of(tag);
+                    if (last && warp == 0) {
+    #pragma unroll
+                        for (int j = 0; j < GPL; ++j)
+                            if (j * 32 + lane < nc) a.gP[(size_t)u * nc + j * 32 + lane] = gm[j];
+                    }
+                    if constexpr (EXPF_OK) {
+                        if (!lg) {
+                            bool far = false;
+    #pragma unroll
+                            for (int j = 0; j < GPL; ++j)
+                                if (j * 32 + lane < nc) far |= !(fabsf(gm[j] - g0m[j]) <= TS_DRIFT);
+                            if (__builtin_expect(__any_sync(FULL, far), 0)) {  // rebuild in the log form
+                                lg = true;
+                                if (tid == 0) atomicAdd(&a.st->log_solves, 1ull);
+                                float gk[NCB];
+                                bcast_g<NCB, GPL>(gm, gk);
+                                float cc[R][NCB];
+    #pragma unroll
+                                for (int k = 0; k < NCB; ++k) {
+                                    float tmp[R];
+    #pragma unroll
+                                    for (int r = 0; r < R; ++r) tmp[r] = 0.f;
+                                    if ((EXACT || k < nc) && any_row) ldv<R>(tmp, a.C + tile + (size_t)k * ld + i0);
+    #pragma unroll
+                                    for (int r = 0; r < R; ++r) cc[r][k] = tmp[r];
+                                }
+    #pragma unroll
+                                for (int r = 0; r < R; ++r) {
+                                    float M = 0.f;
+                                    if (vr[r]) {
+                                        M = -INFINITY;
+    #pragma unroll
+                                        for (int k = 0; k < NCB; ++k)
+                                            if (EXACT || k < nc) M = fmaxf(M, gk[k] - cc[r][k] * sc);
+                                    }
+    #pragma unroll
+                                    for (int k = 0; k < NCB; ++k)
+                                        cc[r][k] = (vr[r] && (EXACT || k < nc)) ? cc[r][k] * sc + M : INFINITY;
+                                }
+    #pragma unroll
+                                for (int rp = 0; rp < RP; ++rp)
+    #pragma unroll
+                                    for (int k = 0; k < NCB; ++k) c2[rp][k] = pk(cc[2 * rp][k], cc[2 * rp + 1][k]);
+                            }
+                        }
+                    }
+                    f2 cs2[NCB];
+    #pragma unroll
+                    for (int k = 0; k < NCB; ++k) cs2[k] = 0ull;
+                    auto sweep = [&](auto form) {
+                        constexpr bool EXPF = decltype(form)::value;
+                        f2 g2[NCB];  // (G_k, G_k) in the exponential form, (g'_k, g'_k) in the log form
+                        {
+                            float gk[NCB];
+                            if constexpr (EXPF) {
+                                float Gm[GPL];
+    #pragma unroll
+                                for (int j = 0; j < GPL; ++j) Gm[j] = ex2(gm[j] - g0m[j]);
+                                bcast_g<NCB, GPL>(Gm, gk);
+                            } else {
+                                bcast_g<NCB, GPL>(gm, gk);
+                            }
+    #pragma unroll
+                            for (int k = 0; k < NCB; ++k) g2[k] = pk(gk[k], gk[k]);
+                        }
+    #pragma unroll
+                        for (int rp = 0; rp < RP; ++rp) {
+                            const bool v0 = vr[2 * rp], v1 = vr[2 * rp + 1];
+                            f2 p2[NCB];
+                            f2 S2 = 0ull;
+    #pragma unroll
+                            for (int k = 0; k < NCB; ++k) {
+                                if constexpr (EXPF) {
+                                    p2[k] = mul2(c2[rp][k], g2[k]);
+                                } else {
+                                    float d0, d1;
+                                    upk(sub2(g2[k], c2[rp][k]), d0, d1);
+                                    p2[k] = pk(ex2(d0), ex2(d1));
+                                }
+                                S2 = add2(S2, p2[k]);
+                            }
+                            float S0, S1;
+                            upk(S2, S0, S1);
+                            if constexpr (!EXPF) {
+                                const bool bad0 = v0 && !(S0 >= 0x1p-64f && S0 <= 0x1p64f);
+                                const bool bad1 = v1 && !(S1 >= 0x1p-64f && S1 <= 0x1p64f);
+                                if (bad0 || bad1) {  // re-shift the pair's rows exactly
+                                    float M0 = -INFINITY, M1 = -INFINITY;
+    #pragma unroll
+                                    for (int k = 0; k < NCB; ++k) {
+                                        if (EXACT || k < nc) {
+                                            float gkk, gdup, c0, c1;
+                                            upk(g2[k], gkk, gdup);
+                                            upk(c2[rp][k], c0, c1);
+                                            M0 = fmaxf(M0, gkk - c0);
+                                            M1 = fmaxf(M1, gkk - c1);
+                                        }
+                                    }
+                                    const f2 M2 = pk(bad0 ? M0 : 0.f, bad1 ? M1 : 0.f);
+                                    S2 = 0ull;
+    #pragma unroll
+                                    for (int k = 0; k < NCB; ++k) {
+                                        if (EXACT || k < nc) c2[rp][k] = add2(c2[rp][k], M2);
+                                        float d0, d1;
+                                        upk(sub2(g2[k], c2[rp][k]), d0, d1);
+                                        p2[k] = pk(ex2(d0), ex2(d1));
+                                        S2 = add2(S2, p2[k]);
+                                    }
+                                    upk(S2, S0, S1);
+                                }
+                            }
+                            const float inv0 = v0 ? rcp_approx(S0) : 0.f;
+                            const float inv1 = v1 ? rcp_approx(S1) : 0.f;
+                            const f2 inv2 = pk(inv0, inv1);
+    #pragma unroll
+                            for (int k = 0; k < NCB; ++k) cs2[k] = fma2(p2[k], inv2, cs2[k]);
+                            if (last) {
+                                float w0 = 0.f, w1 = 0.f;
+    #pragma unroll
+                                for (int k = 0; k < NCB; ++k) {
+                                    if (k < a.K) {
+                                        float p0, p1;
+                                        upk(p2[k], p0, p1);
+                                        w0 += s.e[k] * p0;
+                                        w1 += s.e[k] * p1;
+                                    }
+                                }
+                                acc_imp[2 * rp] += rr[2 * rp] * (w0 * inv0);
+                                acc_imp[2 * rp + 1] += rr[2 * rp + 1] * (w1 * inv1);
+                            }
+                        }
+                    };
+                    if constexpr (EXPF_OK) {
+                        if (__builtin_expect(lg, 0))
+                            sweep(BoolTag<false>{});
+                        else
+                            sweep(BoolTag<true>{});
+                    } else {
+                        sweep(BoolTag<false>{});
+                    }
+                    float cs[NCB];
+    #pragma unroll
+                    for (int k = 0; k < NCB; ++k) {
+                        float lo, hi;
+                        upk(cs2[k], lo, hi);
+                        cs[k] = lo + hi;
+                    }
+                    column_update<NCB, GPL>(cs, gm, nc, s.red, s.ib, par, lane, warp, W);
+                    par ^= 1;
+                    if (l == 0 && tid == 0)
+                        stage_consumer(na, nu, ncn, na.ld, s, MODE == MODE_UPDATE_SWEEP && a.optimizer == 0, false);
+                };
+                if constexpr (PEEL) {
+                    for (int l = 0; l < a.L - 1; ++l) iteration(l, BoolTag<false>{});
+                    iteration(a.L - 1, BoolTag<true>{});
+                } else {
+                    for (int l = 0; l < a.L; ++l) iteration(l, l == a.L - 1);
+                }
+            } else {
+                auto iteration = [&](int l, auto tag) {
+                    const bool last = last_of(tag);
+                    if (last && warp == 0) {
+    #pragma unroll
+                        for (int j = 0; j < GPL; ++j)
+                            if (j * 32 + lane < nc) a.gP[(size_t)u * nc + j * 32 + lane] = gm[j];
+                    }
+                    float gk[NCB];
+                    bcast_g<NCB, GPL>(gm, gk);
+                    float cs[NCB];
+    #pragma unroll
+                    for (int k = 0; k < NCB; ++k) cs[k] = 0.f;
+    #pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        if (!vr[r]) continue;
+                        float p[NCB];
+                        float S = 0.f;
+    #pragma unroll
+                        for (int k = 0; k < NCB; ++k) {
+                            p[k] = ex2(gk[k] - c[r][k]);
+                            S += p[k];
+                        }
+                        if (!(S >= 0x1p-64f && S <= 0x1p64f)) {
+                            float M = -INFINITY;
+    #pragma unroll
+                            for (int k = 0; k < NCB; ++k)
+                                if (EXACT || k < nc) M = fmaxf(M, gk[k] - c[r][k]);
+                            S = 0.f;
+    #pragma unroll
+                            for (int k = 0; k < NCB; ++k) {
+                                if (EXACT || k < nc) c[r][k] += M;
+                                p[k] = ex2(gk[k] - c[r][k]);
+                                S += p[k];
+                            }
+                        }
+                        const float inv = rcp_approx(S);
+    #pragma unroll
+                        for (int k = 0; k < NCB; ++k) cs[k] += p[k] * inv;
+                        if (last) {
+                            float v = 0.f;
+    #pragma unroll
+                            for (int k = 0; k < NCB; ++k)
+                                if (k < a.K) v += s.e[k] * p[k];
+                            acc_imp[r] += rr[r] * (v * inv);
+                        }
+                    }
+                    column_update<NCB, GPL>(cs, gm, nc, s.red, s.ib, par, lane, warp, W);
+                    par ^= 1;
+                    if (l == 0 && tid == 0)
+                        stage_consumer(na, nu, ncn, na.ld, s, MODE == MODE_UPDATE_SWEEP && a.optimizer == 0, false);
+                };
+                if constexpr (PEEL) {
+                    for (int l = 0; l < a.L - 1; ++l) iteration(l, BoolTag<false>{});
+                    iteration(a.L - 1, BoolTag<true>{});
+                } else {
+                    for (int l = 0; l < a.L; ++l) iteration(l, l == a.L - 1);
+                }
+            }
+            }  // register sweep
+            if (warp == 0) {
+    #pragma unroll
+                for (int j = 0; j < GPL; ++j)
+                    if (j * 32 + lane < nc) a.gL[(size_t)u * nc + j * 32 + lane] = gm[j];
+            }
+            // tile sweep: the last column update ended with a barrier after every read of the tile, so
+            // the next consumer's tile can be staged now (its L2 prefetch was issued during the solve)
+            if (TS && tid == 0) stage_consumer(na, nu, ncn, na.ld, s, false, TS);
+    }
+    return true;
+}
+
+// Shared arrays of market a that the consumers of a CTA read: exposure, 1 / b_k, omega (register
+// sweep, update modes) and the Adam step size and bias correction of this step (t counts the steps
+// applied before it). Made visible by the next barrier.
+template <int NCB, bool EXACT, int MODE, int TS>
+__device__ __forceinline__ void p1_market_setup(const P1Args& a, const Smem& s) {
+    const int nc = EXACT ? NCB : a.nc;
+    const int ncx = ncx_of(nc, NCB);
+    const int tid = threadIdx.x, T = blockDim.x;
+    if (tid == 0) {
+        float step_size = a.lr, bc2s = 1.f;
+        if (MODE == MODE_UPDATE_SWEEP && a.optimizer == 0) {
+            const float t1 = (float)(a.st->t + 1);
+            step_size = a.lr / one_minus_pow(a.beta1, t1);
+            bc2s = sqrtf(one_minus_pow(a.beta2, t1));
+        }
+        s.coef[0] = step_size;
+        s.coef[1] = bc2s;
+    }
+    for (int k = tid; k < ncx; k += T) {
+        s.ib[k] = k < nc ? a.invb[k] : 0.f;
+        s.e[k] = k < nc ? a.e[k] : 0.f;
+    }
+    if (MODE != MODE_SWEEP && !TS)
+        for (int i = tid; i < a.ld; i += T) s.om[i] = i < a.I ? a.omega[i] : 0.f;
+}
+
+// Launch bound: 512 threads, except the tile sweep of more than 16 columns, which serves at most
+// 2048 items (256 threads) and may then use up to 255 registers per thread.
+template <int NCB, int R, bool EXACT, int MODE, int TS>
+__global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(const P1Args a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nc = EXACT ? NCB : a.nc;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
+    const int ld = a.ld;
+    const int i0 = tid * R;
     Smem s;
     smem_layout(NCB, nc, ld, W, MODE, TS, &s, smem_raw);
-    const int lds = TS ? TS : ld;  // column stride of the shared tile
 
     if (a.st->stop) return;  // fr_solve reached its threshold: the remaining steps are no-ops
 
@@ -659,27 +1248,9 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
         fence_mbar_init();
     }
     __syncthreads();  // the mbarrier is initialised before any thread waits on it
-    if (tid == 0) {
+    if (tid == 0)
         stage_consumer(a, blockIdx.x, nc, ld, s, MODE == MODE_UPDATE_SWEEP && a.optimizer == 0, TS);
-        // Adam bias corrections for this step (t counts applied steps before this one)
-        float step_size = a.lr, bc2s = 1.f;
-        if (MODE == MODE_UPDATE_SWEEP && a.optimizer == 0) {
-            const float t1 = (float)(a.st->t + 1);
-            step_size = a.lr / one_minus_pow(a.beta1, t1);
-            bc2s = sqrtf(one_minus_pow(a.beta2, t1));
-        }
-        s.coef[0] = step_size;
-        s.coef[1] = bc2s;
-    }
-    for (int k = tid; k < ncx; k += T) {
-        s.ib[k] = k < nc ? a.invb[k] : 0.f;
-        s.e[k] = k < nc ? a.e[k] : 0.f;
-    }
-    if (MODE != MODE_SWEEP && !TS)
-        for (int i = tid; i < ld; i += T) s.om[i] = i < I ? a.omega[i] : 0.f;
-    // omega_i and r(u,i): the staged copies, or (tile sweep) global memory; omega has ld entries,
-    // zero beyond I
-    auto om_at = [&](int i) { return TS ? __ldg(a.omega + i) : s.om[i]; };
+    p1_market_setup<NCB, EXACT, MODE, TS>(a, s);
 
     float acc_imp[R];
 #pragma unroll
@@ -689,538 +1260,11 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
     unsigned phase = 0;
 
     for (int u = blockIdx.x; u < a.U; u += gridDim.x) {
-        const size_t tile = (size_t)u * nc * ld;
-        const float* __restrict__ r_u = a.r + (size_t)u * ld;
-        auto r_at = [&](int i) { return TS ? __ldg(r_u + i) : s.r[i]; };
-        float gm[GPL];  // column potentials of the columns this lane holds (same in every warp)
-#pragma unroll
-        for (int j = 0; j < GPL; ++j) {
-            const int col = j * 32 + lane;
-            gm[j] = (a.warm && col < nc) ? a.gL[(size_t)u * nc + col] : 0.f;
-        }
-        if (MODE != MODE_SWEEP && tid < ncx) s.gp[tid] = tid < nc ? a.gP[(size_t)u * nc + tid] : 0.f;
-        // the consumer's tile was staged one consumer ago (the register sweep) or right after the
-        // previous solve (the tile sweep), and it is the only copy in flight. The wait is bounded:
-        // if it expires, the CTA records a timeout, waits (with the default bound) for the copy to
-        // land and stops, so that no bulk copy is still writing into its shared memory when it
-        // leaves. In the tile sweep's update modes the first gradient pass reads the costs from
-        // global memory (L2, where the previous solve prefetched them) while the copy lands, and
-        // the wait follows that pass.
-        constexpr bool LATE_WAIT = TS != 0 && MODE != MODE_SWEEP;
-        bool tile_ok = true;  // the same in every thread (cta_wait_or_drain)
-        if constexpr (!LATE_WAIT) {
-            tile_ok = cta_wait_or_drain(s.bar, phase, a.max_polls, kDefaultPolls, &a.st->err, 4);
-            phase ^= 1u;
-        } else {
-            __syncthreads();  // s.gp / s.e / s.ib / s.om / s.coef visible
-        }
-        if (!tile_ok) break;
-
-        if constexpr (MODE != MODE_SWEEP) {
-            if (TS && MODE == MODE_UPDATE_SWEEP && a.optimizer == 0 && tid == 0) {
-                // the consumer's Adam moments into L2 while the gradient passes run
-                const unsigned tb = (unsigned)(sizeof(float) * (size_t)nc * ld);
-                bulk_prefetch_l2(a.m1 + tile, tb);
-                bulk_prefetch_l2(a.m2 + tile, tb);
-            }
-            // ---------------- gradient of F at the previous policy ------------------------------
-            // x_ik = 2^(g'_k - c'_ik - lse_i) is re-formed from the staged tile and the row
-            // log-normaliser lse_i of the first pass.
-            {
-                float acc[3][NCB];  // q, cs, X^T h partials
-#pragma unroll
-                for (int k = 0; k < NCB; ++k) acc[0][k] = acc[1][k] = acc[2][k] = 0.f;
-                for (int i = tid; i < I; i += T) {
-                    float x[NCB];
-                    float M = -INFINITY;
-#pragma unroll
-                    for (int k = 0; k < NCB; ++k) {
-                        float c = 0.f;
-                        if (EXACT || k < nc)
-                            c = LATE_WAIT ? __ldcg(a.C + tile + (size_t)k * ld + i) : s.C[k * lds + i];
-                        x[k] = (EXACT || k < nc) ? s.gp[k] - c * sc : -INFINITY;
-                        M = fmaxf(M, x[k]);
-                    }
-                    float S = 0.f;
-#pragma unroll
-                    for (int k = 0; k < NCB; ++k) {
-                        x[k] = ex2(x[k] - M);
-                        S += x[k];
-                    }
-                    const float inv = rcp_approx(S);  // S in [1, m]: the row max contributes 1
-                    const float wr = om_at(i) * r_at(i);  // dF/dx_ik = wr_i e_k
-                    float hh = 0.f, vi = 0.f;
-#pragma unroll
-                    for (int k = 0; k < NCB; ++k) {
-                        x[k] *= inv;
-                        hh += x[k] * (wr * s.e[k]);
-                        if (MODE == MODE_GRAD && k < a.K) vi += s.e[k] * x[k];
-                    }
-#pragma unroll
-                    for (int k = 0; k < NCB; ++k) {
-                        acc[0][k] += x[k] * (wr * s.e[k]);
-                        acc[1][k] += x[k];
-                        acc[2][k] += x[k] * hh;
-                        if constexpr (!REG_GRAM) {
-                            if (EXACT || k < nc) s.X[k * ld + i] = x[k];
-                        }
-                    }
-                    s.lse[i] = M + lg2_approx(S);
-                    s.h[i] = hh;
-                    // dF/dr(u,i) = (dF/dImp_i) sum_{k<K} e_k x_ik (C does not depend on r)
-                    if (MODE == MODE_GRAD && a.dr) a.dr[(size_t)u * I + i] = om_at(i) * vi;
-                }
-                cta_reduce<NCB, 3>(acc, nc, s.red, s.out, ncp);  // s.out: [q | cs | X^T h]
-            }
-            if constexpr (LATE_WAIT) {  // the shared tile from here on
-                tile_ok = cta_wait_or_drain(s.bar, phase, a.max_polls, kDefaultPolls, &a.st->err, 4);
-                phase ^= 1u;
-                if (!tile_ok) break;
-            }
-            // Gram block M[0:n,0:n] of diag(cs) - X^T X; rows of x sum to 1, so the diagonal is
-            // sum_i x_ik (1 - x_ik) without cancellation.
-            if constexpr (REG_GRAM) {
-                float* gout = s.out + 3 * ncp;
-                gram_block<NCB, EXACT>(s, nc, I, lds, sc, gout);
-                float* Af = reinterpret_cast<float*>(s.A);
-                float* rf = reinterpret_cast<float*>(s.rhs);
-                for (int idx = tid; idx < n * n; idx += T) {
-                    int k = idx / n, m = idx % n;
-                    if (k > m) { const int t = k; k = m; m = t; }
-                    Af[idx] = gout[k * (NCB - 1) - k * (k - 1) / 2 + (m - k)];
-                }
-                for (int k = tid; k < ncx; k += T) {
-                    if (k < n) rf[k] = s.out[k] - s.out[2 * ncp + k];
-                    s.beta[k] = 0.f;
-                }
-                __syncthreads();
-                if (warp == 0) warp_cholesky_solve_f32<NCB - 1>(Af, rf, n, s.Lt, s.beta, lane);
-                __syncthreads();
-            } else {
-                for (int pidx = warp; pidx < n * (n + 1) / 2; pidx += W) {
-                    int k = 0, rem = pidx;
-                    while (rem >= n - k) { rem -= n - k; ++k; }
-                    const int m = k + rem;
-                    const float* xk = s.X + k * ld;
-                    const float* xm = s.X + m * ld;
-                    float sum = 0.f;
-                    if (k == m) {
-                        for (int i = lane; i < I; i += 32) sum += xk[i] * (1.f - xk[i]);
-                    } else {
-                        for (int i = lane; i < I; i += 32) sum -= xk[i] * xm[i];
-                    }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
-                    if (lane == 0) {
-                        s.A[k * n + m] = (double)sum;
-                        s.A[m * n + k] = (double)sum;
-                    }
-                }
-                for (int k = tid; k < n; k += T)
-                    s.rhs[k] = (double)s.out[k] - (double)s.out[2 * ncp + k];
-                __syncthreads();
-                if (warp == 0) warp_cholesky_solve(s.A, s.rhs, n, lane);
-                __syncthreads();
-                for (int k = tid; k < ncx; k += T) s.beta[k] = k < n ? (float)s.rhs[k] : 0.f;
-                __syncthreads();
-            }
-            // alpha_i = h_i - sum_k x_ik beta_k
-            for (int i = tid; i < I; i += T) {
-                const float l = s.lse[i];
-                float sb = 0.f;
-#pragma unroll
-                for (int k = 0; k < NCB; ++k)
-                    if (EXACT || k < nc) sb += ex2(s.gp[k] - s.C[k * lds + i] * sc - l) * s.beta[k];
-                s.alpha[i] = s.h[i] - sb;
-            }
-            __syncthreads();
-            // gradient and Adam over the tile: each thread takes four consecutive items (float4)
-            // and runs through the columns, so the per-item values (lse, alpha, omega r) are read
-            // once per four items and eleven columns, and no index needs a division
-            const float step_size = s.coef[0], inv_bc2s = 1.f / s.coef[1];
-            float* __restrict__ Cg = a.C;
-            float* __restrict__ m1g = a.m1;
-            float* __restrict__ m2g = a.m2;
-            float gsq = 0.f;
-            for (int i4 = tid; i4 * 4 < I; i4 += T) {
-                const int i = i4 * 4;
-                const float4 l4 = reinterpret_cast<const float4*>(s.lse)[i4];
-                const float4 a4 = reinterpret_cast<const float4*>(s.alpha)[i4];
-                const float4 o4 = TS ? __ldg(reinterpret_cast<const float4*>(a.omega) + i4)
-                                     : reinterpret_cast<const float4*>(s.om)[i4];
-                const float4 r4 = TS ? __ldg(reinterpret_cast<const float4*>(r_u) + i4)
-                                     : reinterpret_cast<const float4*>(s.r)[i4];
-                const float lv[4] = {l4.x, l4.y, l4.z, l4.w}, av[4] = {a4.x, a4.y, a4.z, a4.w};
-                const float wv[4] = {o4.x * r4.x, o4.y * r4.y, o4.z * r4.z, o4.w * r4.w};
-                // Adam moments two columns ahead (their loads would otherwise wait for the stores
-                // of the previous column: the compiler cannot tell the addresses apart)
-                constexpr bool ADAM = MODE == MODE_UPDATE_SWEEP;
-                const bool adam = ADAM && a.optimizer == 0;
-                const int ncc = EXACT ? NCB : nc;
-                float4 mA = make_float4(0.f, 0.f, 0.f, 0.f), vA = mA, mB = mA, vB = mA;
-                auto ldmv = [&](int k, float4& m, float4& v) {
-                    const size_t off = tile + (size_t)k * ld + i;
-                    m = *reinterpret_cast<const float4*>(m1g + off);
-                    v = *reinterpret_cast<const float4*>(m2g + off);
-                };
-                if (adam) {
-                    ldmv(0, mA, vA);
-                    if (1 < ncc) ldmv(1, mB, vB);
-                }
-#pragma unroll 4
-                for (int k = 0; k < NCB; ++k) {
-                    if (!EXACT && k >= nc) break;
-                    const float4 mm4 = mA, vv4 = vA;
-                    mA = mB;
-                    vA = vB;
-                    if (adam && k + 2 < ncc) ldmv(k + 2, mB, vB);
-                    const int qs = k * (lds / 4) + i4;  // float4 index in the shared tile
-                    const float4 c4 = reinterpret_cast<const float4*>(s.C)[qs];
-                    const float gpk = s.gp[k], ek = s.e[k], bk = s.beta[k];
-                    float cv[4] = {c4.x, c4.y, c4.z, c4.w};
-                    float gr[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const bool valid = i + j < I;
-                        const float x = valid ? ex2(gpk - cv[j] * sc - lv[j]) : 0.f;
-                        gr[j] = valid ? -a.inv_eps * x * (wv[j] * ek - av[j] - bk) : 0.f;
-                        gsq += gr[j] * gr[j];
-                    }
-                    if constexpr (MODE == MODE_GRAD) {
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if (i + j < I) a.dC[((size_t)u * I + i + j) * nc + k] = gr[j];
-                    } else {
-                        const size_t off = tile + (size_t)k * ld + i;
-                        if (a.optimizer == 1) {
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) cv[j] += a.lr * gr[j];
-                        } else {
-                            float mm[4] = {mm4.x, mm4.y, mm4.z, mm4.w};
-                            float vv[4] = {vv4.x, vv4.y, vv4.z, vv4.w};
-#pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                mm[j] = a.beta1 * mm[j] + (1.f - a.beta1) * gr[j];
-                                vv[j] = a.beta2 * vv[j] + (1.f - a.beta2) * gr[j] * gr[j];
-                                // sqrt(v) / bc2s + eps with MUFU rsqrt / rcp (IEEE sqrt and
-                                // division are long instruction sequences on the per-cell path)
-                                const float sq = vv[j] > 0.f ? vv[j] * rsqrtf(vv[j]) : 0.f;
-                                cv[j] += __fdividef(step_size * mm[j], fmaf(sq, inv_bc2s, a.adam_eps));
-                            }
-                            *reinterpret_cast<float4*>(m1g + off) = make_float4(mm[0], mm[1], mm[2], mm[3]);
-                            *reinterpret_cast<float4*>(m2g + off) = make_float4(vv[0], vv[1], vv[2], vv[3]);
-                        }
-                        const float4 cn = make_float4(cv[0], cv[1], cv[2], cv[3]);
-                        *reinterpret_cast<float4*>(Cg + off) = cn;
-                        reinterpret_cast<float4*>(s.C)[qs] = cn;
-                    }
-                }
-            }
-            gn2 += (double)gsq;
-            if constexpr (MODE == MODE_GRAD) {
-                __syncthreads();
-                if (tid == 0) stage_consumer(a, u + gridDim.x, nc, ld, s, false, TS);
-                continue;  // no solve in gradient mode
-            }
-            __syncthreads();  // updated tile visible
-        }
-
-        // ---------------- Sinkhorn solve on the consumer's (new) costs ----------------------------
-        if constexpr (TS != 0) {
-            tile_sweep<NCB, R, 2, TS, EXACT, MODE>(a, s, u, nc, gm, par);
-        } else {
-        float rr[R];
-        bool vr[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) rr[r] = 0.f;
-        if (any_row) ldv<R>(rr, s.r + i0);
-#pragma unroll
-        for (int r = 0; r < R; ++r) vr[r] = i0 + r < I;
-        float c[R][NCB];
-        {
-            float gk[NCB];
-            bcast_g<NCB, GPL>(gm, gk);
-#pragma unroll
-            for (int k = 0; k < NCB; ++k) {
-                float tmp[R];
-#pragma unroll
-                for (int r = 0; r < R; ++r) tmp[r] = 0.f;
-                if ((EXACT || k < nc) && any_row) ldv<R>(tmp, s.C + k * lds + i0);
-#pragma unroll
-                for (int r = 0; r < R; ++r) c[r][k] = tmp[r];
-            }
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float M = 0.f;
-                if (vr[r]) {
-                    M = -INFINITY;
-#pragma unroll
-                    for (int k = 0; k < NCB; ++k)
-                        if (EXACT || k < nc) M = fmaxf(M, gk[k] - c[r][k] * sc);
-                }
-#pragma unroll
-                for (int k = 0; k < NCB; ++k)
-                    c[r][k] = (vr[r] && (EXACT || k < nc)) ? c[r][k] * sc + M : INFINITY;
-            }
-        }
-        // the last iteration (which also writes g^(L-1) and adds the impacts) as a separate
-        // instantiation, where a second copy of the body fits the registers
-        constexpr bool PEEL = NCB <= 11;
-        if constexpr (PAIR) {
-            constexpr int RP = R / 2;
-            // Up to 11 columns the pairs start in the exponential form of the tile sweep (E pairs in
-            // c2, G_k = 2^(g'_k - g0_k) per iteration, one packed multiply per two cells) and switch
-            // to the log form (c~ pairs rebuilt from the costs in global memory at the current g')
-            // when a potential drifts past TS_DRIFT; wider buckets keep the log form throughout.
-            constexpr bool EXPF_OK = NCB <= 11;
-            float g0m[GPL];  // g' at the start of the solve (this lane's columns)
-#pragma unroll
-            for (int j = 0; j < GPL; ++j) g0m[j] = gm[j];
-            f2 c2[RP][NCB];
-            {
-                float gk[NCB];
-                bcast_g<NCB, GPL>(gm, gk);
-#pragma unroll
-                for (int rp = 0; rp < RP; ++rp)
-#pragma unroll
-                    for (int k = 0; k < NCB; ++k) {
-                        if constexpr (EXPF_OK)  // rows and columns outside the tile: c~ = inf, E = 0
-                            c2[rp][k] = pk(ex2(gk[k] - c[2 * rp][k]), ex2(gk[k] - c[2 * rp + 1][k]));
-                        else
-                            c2[rp][k] = pk(c[2 * rp][k], c[2 * rp + 1][k]);
-                    }
-            }
-            bool lg = !EXPF_OK;  // c2 holds the log form (the same in every thread of the CTA)
-            auto iteration = [&](int l, auto tag) {
-                const bool last = last_of(tag);
-                if (last && warp == 0) {
-#pragma unroll
-                    for (int j = 0; j < GPL; ++j)
-                        if (j * 32 + lane < nc) a.gP[(size_t)u * nc + j * 32 + lane] = gm[j];
-                }
-                if constexpr (EXPF_OK) {
-                    if (!lg) {
-                        bool far = false;
-#pragma unroll
-                        for (int j = 0; j < GPL; ++j)
-                            if (j * 32 + lane < nc) far |= !(fabsf(gm[j] - g0m[j]) <= TS_DRIFT);
-                        if (__builtin_expect(__any_sync(FULL, far), 0)) {  // rebuild in the log form
-                            lg = true;
-                            if (tid == 0) atomicAdd(&a.st->log_solves, 1ull);
-                            float gk[NCB];
-                            bcast_g<NCB, GPL>(gm, gk);
-                            float cc[R][NCB];
-#pragma unroll
-                            for (int k = 0; k < NCB; ++k) {
-                                float tmp[R];
-#pragma unroll
-                                for (int r = 0; r < R; ++r) tmp[r] = 0.f;
-                                if ((EXACT || k < nc) && any_row) ldv<R>(tmp, a.C + tile + (size_t)k * ld + i0);
-#pragma unroll
-                                for (int r = 0; r < R; ++r) cc[r][k] = tmp[r];
-                            }
-#pragma unroll
-                            for (int r = 0; r < R; ++r) {
-                                float M = 0.f;
-                                if (vr[r]) {
-                                    M = -INFINITY;
-#pragma unroll
-                                    for (int k = 0; k < NCB; ++k)
-                                        if (EXACT || k < nc) M = fmaxf(M, gk[k] - cc[r][k] * sc);
-                                }
-#pragma unroll
-                                for (int k = 0; k < NCB; ++k)
-                                    cc[r][k] = (vr[r] && (EXACT || k < nc)) ? cc[r][k] * sc + M : INFINITY;
-                            }
-#pragma unroll
-                            for (int rp = 0; rp < RP; ++rp)
-#pragma unroll
-                                for (int k = 0; k < NCB; ++k) c2[rp][k] = pk(cc[2 * rp][k], cc[2 * rp + 1][k]);
-                        }
-                    }
-                }
-                f2 cs2[NCB];
-#pragma unroll
-                for (int k = 0; k < NCB; ++k) cs2[k] = 0ull;
-                auto sweep = [&](auto form) {
-                    constexpr bool EXPF = decltype(form)::value;
-                    f2 g2[NCB];  // (G_k, G_k) in the exponential form, (g'_k, g'_k) in the log form
-                    {
-                        float gk[NCB];
-                        if constexpr (EXPF) {
-                            float Gm[GPL];
-#pragma unroll
-                            for (int j = 0; j < GPL; ++j) Gm[j] = ex2(gm[j] - g0m[j]);
-                            bcast_g<NCB, GPL>(Gm, gk);
-                        } else {
-                            bcast_g<NCB, GPL>(gm, gk);
-                        }
-#pragma unroll
-                        for (int k = 0; k < NCB; ++k) g2[k] = pk(gk[k], gk[k]);
-                    }
-#pragma unroll
-                    for (int rp = 0; rp < RP; ++rp) {
-                        const bool v0 = vr[2 * rp], v1 = vr[2 * rp + 1];
-                        f2 p2[NCB];
-                        f2 S2 = 0ull;
-#pragma unroll
-                        for (int k = 0; k < NCB; ++k) {
-                            if constexpr (EXPF) {
-                                p2[k] = mul2(c2[rp][k], g2[k]);
-                            } else {
-                                float d0, d1;
-                                upk(sub2(g2[k], c2[rp][k]), d0, d1);
-                                p2[k] = pk(ex2(d0), ex2(d1));
-                            }
-                            S2 = add2(S2, p2[k]);
-                        }
-                        float S0, S1;
-                        upk(S2, S0, S1);
-                        if constexpr (!EXPF) {
-                            const bool bad0 = v0 && !(S0 >= 0x1p-64f && S0 <= 0x1p64f);
-                            const bool bad1 = v1 && !(S1 >= 0x1p-64f && S1 <= 0x1p64f);
-                            if (bad0 || bad1) {  // re-shift the pair's rows exactly
-                                float M0 = -INFINITY, M1 = -INFINITY;
-#pragma unroll
-                                for (int k = 0; k < NCB; ++k) {
-                                    if (EXACT || k < nc) {
-                                        float gkk, gdup, c0, c1;
-                                        upk(g2[k], gkk, gdup);
-                                        upk(c2[rp][k], c0, c1);
-                                        M0 = fmaxf(M0, gkk - c0);
-                                        M1 = fmaxf(M1, gkk - c1);
-                                    }
-                                }
-                                const f2 M2 = pk(bad0 ? M0 : 0.f, bad1 ? M1 : 0.f);
-                                S2 = 0ull;
-#pragma unroll
-                                for (int k = 0; k < NCB; ++k) {
-                                    if (EXACT || k < nc) c2[rp][k] = add2(c2[rp][k], M2);
-                                    float d0, d1;
-                                    upk(sub2(g2[k], c2[rp][k]), d0, d1);
-                                    p2[k] = pk(ex2(d0), ex2(d1));
-                                    S2 = add2(S2, p2[k]);
-                                }
-                                upk(S2, S0, S1);
-                            }
-                        }
-                        const float inv0 = v0 ? rcp_approx(S0) : 0.f;
-                        const float inv1 = v1 ? rcp_approx(S1) : 0.f;
-                        const f2 inv2 = pk(inv0, inv1);
-#pragma unroll
-                        for (int k = 0; k < NCB; ++k) cs2[k] = fma2(p2[k], inv2, cs2[k]);
-                        if (last) {
-                            float w0 = 0.f, w1 = 0.f;
-#pragma unroll
-                            for (int k = 0; k < NCB; ++k) {
-                                if (k < a.K) {
-                                    float p0, p1;
-                                    upk(p2[k], p0, p1);
-                                    w0 += s.e[k] * p0;
-                                    w1 += s.e[k] * p1;
-                                }
-                            }
-                            acc_imp[2 * rp] += rr[2 * rp] * (w0 * inv0);
-                            acc_imp[2 * rp + 1] += rr[2 * rp + 1] * (w1 * inv1);
-                        }
-                    }
-                };
-                if constexpr (EXPF_OK) {
-                    if (__builtin_expect(lg, 0))
-                        sweep(BoolTag<false>{});
-                    else
-                        sweep(BoolTag<true>{});
-                } else {
-                    sweep(BoolTag<false>{});
-                }
-                float cs[NCB];
-#pragma unroll
-                for (int k = 0; k < NCB; ++k) {
-                    float lo, hi;
-                    upk(cs2[k], lo, hi);
-                    cs[k] = lo + hi;
-                }
-                column_update<NCB, GPL>(cs, gm, nc, s.red, s.ib, par, lane, warp, W);
-                par ^= 1;
-                if (l == 0 && tid == 0)
-                    stage_consumer(a, u + gridDim.x, nc, ld, s, MODE == MODE_UPDATE_SWEEP && a.optimizer == 0, false);
-            };
-            if constexpr (PEEL) {
-                for (int l = 0; l < a.L - 1; ++l) iteration(l, BoolTag<false>{});
-                iteration(a.L - 1, BoolTag<true>{});
-            } else {
-                for (int l = 0; l < a.L; ++l) iteration(l, l == a.L - 1);
-            }
-        } else {
-            auto iteration = [&](int l, auto tag) {
-                const bool last = last_of(tag);
-                if (last && warp == 0) {
-#pragma unroll
-                    for (int j = 0; j < GPL; ++j)
-                        if (j * 32 + lane < nc) a.gP[(size_t)u * nc + j * 32 + lane] = gm[j];
-                }
-                float gk[NCB];
-                bcast_g<NCB, GPL>(gm, gk);
-                float cs[NCB];
-#pragma unroll
-                for (int k = 0; k < NCB; ++k) cs[k] = 0.f;
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    if (!vr[r]) continue;
-                    float p[NCB];
-                    float S = 0.f;
-#pragma unroll
-                    for (int k = 0; k < NCB; ++k) {
-                        p[k] = ex2(gk[k] - c[r][k]);
-                        S += p[k];
-                    }
-                    if (!(S >= 0x1p-64f && S <= 0x1p64f)) {
-                        float M = -INFINITY;
-#pragma unroll
-                        for (int k = 0; k < NCB; ++k)
-                            if (EXACT || k < nc) M = fmaxf(M, gk[k] - c[r][k]);
-                        S = 0.f;
-#pragma unroll
-                        for (int k = 0; k < NCB; ++k) {
-                            if (EXACT || k < nc) c[r][k] += M;
-                            p[k] = ex2(gk[k] - c[r][k]);
-                            S += p[k];
-                        }
-                    }
-                    const float inv = rcp_approx(S);
-#pragma unroll
-                    for (int k = 0; k < NCB; ++k) cs[k] += p[k] * inv;
-                    if (last) {
-                        float v = 0.f;
-#pragma unroll
-                        for (int k = 0; k < NCB; ++k)
-                            if (k < a.K) v += s.e[k] * p[k];
-                        acc_imp[r] += rr[r] * (v * inv);
-                    }
-                }
-                column_update<NCB, GPL>(cs, gm, nc, s.red, s.ib, par, lane, warp, W);
-                par ^= 1;
-                if (l == 0 && tid == 0)
-                    stage_consumer(a, u + gridDim.x, nc, ld, s, MODE == MODE_UPDATE_SWEEP && a.optimizer == 0, false);
-            };
-            if constexpr (PEEL) {
-                for (int l = 0; l < a.L - 1; ++l) iteration(l, BoolTag<false>{});
-                iteration(a.L - 1, BoolTag<true>{});
-            } else {
-                for (int l = 0; l < a.L; ++l) iteration(l, l == a.L - 1);
-            }
-        }
-        }  // register sweep
-        if (warp == 0) {
-#pragma unroll
-            for (int j = 0; j < GPL; ++j)
-                if (j * 32 + lane < nc) a.gL[(size_t)u * nc + j * 32 + lane] = gm[j];
-        }
-        // tile sweep: the last column update ended with a barrier after every read of the tile, so
-        // the next consumer's tile can be staged now (its L2 prefetch was issued during the solve)
-        if (TS && tid == 0) stage_consumer(a, u + gridDim.x, nc, ld, s, false, TS);
+        const int nu = u + (int)gridDim.x < a.U ? u + (int)gridDim.x : -1;
+        if (!p1_consumer<NCB, R, EXACT, MODE, TS>(a, s, u, a, nu, a.part + (size_t)blockIdx.x * ld,
+                                                  u == (int)blockIdx.x, acc_imp, gn2, par, phase))
+            break;
     }
-
     if constexpr (MODE != MODE_GRAD) {
         if constexpr (TS == 0) {  // (the tile sweep accumulates into part as it goes)
             if (i0 < ld) stv<R>(a.part + (size_t)blockIdx.x * ld + i0, acc_imp);
@@ -1243,10 +1287,109 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
     }
 }
 
+// Batched markets: CTA b walks chunks b, b + G, ... of the list; a chunk is a run of consecutive
+// consumers of one market with its own partial row (impacts, and the squared gradient in update
+// mode). The chunk's market arguments are copied to shared memory; the tile of the next chunk's
+// first consumer is staged during the previous chunk's last consumer, as in p1_kernel. One shared
+// layout (the variant's at ld_max) serves every market of the launch.
+template <int NCB, int R, bool EXACT, int MODE, int TS>
+__global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_batch_kernel(const P1Batch bt) {
+    static_assert(MODE != MODE_GRAD, "batched launches solve");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ P1Args sa;  // the current chunk's market
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
+    const int i0 = tid * R;
+    Smem s;
+    smem_layout(NCB, NCB, bt.ld_max, W, MODE, TS, &s, smem_raw);
+    if ((int)blockIdx.x >= bt.n_chunks) return;
+    if (tid == 0) {
+        mbar_init(s.bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();  // the mbarrier is initialised before any thread waits on it
+    if (tid == 0) {
+        const P2Chunk c0 = bt.ch[blockIdx.x];
+        const P1Args& a0 = bt.mk[c0.market];
+        stage_consumer(a0, c0.u0, EXACT ? NCB : a0.nc, a0.ld, s,
+                       MODE == MODE_UPDATE_SWEEP && a0.optimizer == 0, TS);
+    }
+    float acc_imp[R];
+    int par = 0;
+    unsigned phase = 0;
+    for (int c = blockIdx.x; c < bt.n_chunks; c += gridDim.x) {
+        const P2Chunk ch = bt.ch[c];
+        __syncthreads();  // every thread is done with the previous chunk's market arrays
+        if (tid == 0) sa = bt.mk[ch.market];
+        __syncthreads();
+        const P1Args& a = sa;
+        p1_market_setup<NCB, EXACT, MODE, TS>(a, s);
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc_imp[r] = 0.f;
+        double gn2 = 0.0;
+        const int cn = c + (int)gridDim.x < bt.n_chunks ? c + (int)gridDim.x : -1;
+        float* part_row = a.part + (size_t)ch.row * a.ld;
+        bool ok = true;
+        for (int u = ch.u0; u < ch.u1 && ok; ++u) {
+            const P1Args* na = &a;
+            int nu = u + 1;
+            if (nu >= ch.u1) {
+                if (cn >= 0) {
+                    const P2Chunk nx = bt.ch[cn];
+                    na = bt.mk + nx.market;
+                    nu = nx.u0;
+                } else {
+                    nu = -1;
+                }
+            }
+            ok = p1_consumer<NCB, R, EXACT, MODE, TS>(a, s, u, *na, nu, part_row, u == ch.u0, acc_imp,
+                                                      gn2, par, phase);
+        }
+        if (!ok) break;  // an expired wait (the same in every thread): the CTA stops
+        if constexpr (TS == 0) {
+            if (i0 < a.ld) stv<R>(part_row + i0, acc_imp);
+        }
+        if constexpr (MODE == MODE_UPDATE_SWEEP) {  // the chunk's squared gradient, fixed order
+            __syncthreads();
+            double* s_d = reinterpret_cast<double*>(s.red);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) gn2 += __shfl_xor_sync(FULL, gn2, o);
+            if (lane == 0) s_d[warp] = gn2;
+            __syncthreads();
+            if (tid == 0) {
+                double t = 0.0;
+                for (int w = 0; w < W; ++w) t += s_d[w];
+                a.gn2_part[ch.row] = t;
+            }
+        }
+    }
+}
+
+// Builds P1Variant entries: MkPlain with the single-market kernels (fn), MkBatch with the batched
+// ones (fb). One variant table (p1_select_with) serves both.
+struct MkPlain {
+    template <int NCB, int R, bool EXACT, int TS>
+    P1Variant make(int threads) const;
+};
+struct MkBatch {
+    template <int NCB, int R, bool EXACT, int TS>
+    P1Variant make(int threads) const {
+        P1Variant v{};
+        v.ncb = NCB;
+        v.rows = R;
+        v.exact = EXACT;
+        v.threads = threads;
+        v.tile_stride = TS;
+        v.fb[0] = (const void*)p1_batch_kernel<NCB, R, EXACT, MODE_SWEEP, TS>;
+        v.fb[1] = (const void*)p1_batch_kernel<NCB, R, EXACT, MODE_UPDATE_SWEEP, TS>;
+        return v;
+    }
+};
+
 // TS: 0 register sweep, else the tile sweep with that shared column stride (floats)
 template <int NCB, int R, bool EXACT, int TS = 0>
 P1Variant make_variant(int threads) {
-    P1Variant v;
+    P1Variant v{};
     v.ncb = NCB;
     v.rows = R;
     v.exact = EXACT;
@@ -1257,6 +1400,73 @@ P1Variant make_variant(int threads) {
     v.fn[MODE_UPDATE_SWEEP] = (const void*)p1_kernel<NCB, R, EXACT, MODE_UPDATE_SWEEP, TS>;
     v.fn[MODE_GRAD] = (const void*)p1_kernel<NCB, R, EXACT, MODE_GRAD, TS>;
     return v;
+}
+
+template <int NCB, int R, bool EXACT, int TS>
+P1Variant MkPlain::make(int threads) const {
+    return make_variant<NCB, R, EXACT, TS>(threads);
+}
+
+// 21 columns (20 slots + dummy): the tile sweep with eight rows per thread, at a shared column
+// stride of 512, 1024 or 2048 floats.
+template <class Mk>
+bool p1_k21_with(const Mk& mk, int ld, int threads, P1Variant* out) {
+    if (ld <= 512)
+        *out = mk.template make<21, 8, true, 512>(threads);
+    else if (ld <= 1024)
+        *out = mk.template make<21, 8, true, 1024>(threads);
+    else if (ld <= 2048)
+        *out = mk.template make<21, 8, true, 2048>(threads);
+    else
+        return false;
+    return true;
+}
+
+// Compiled variants: exact column counts for the hot shapes, padded buckets for the rest. k21 builds
+// the 21-column entries (compiled in their own translation units).
+template <class Mk>
+bool p1_select_with(const Mk& mk, int nc, int I, P1Variant* out,
+                    bool (*k21)(int ld, int threads, P1Variant* out)) {
+    // CTA size: one thread per R items, at most 512 threads (the kernels' launch bound)
+    auto threads_for = [&](int R) {
+        int t = (I + R - 1) / R;
+        return (t + 31) / 32 * 32;
+    };
+    P1Variant v;
+    // 11 columns: costs in registers up to 768 items; beyond that the tile sweep (eight rows per
+    // thread, costs read from the resident tile at a compile-time column stride of 1024, 2048 or
+    // 4096 floats), up to 4096 items. Measured fused steps: 2000 x 1000 0.485 vs 0.506 ms,
+    // 2000 x 2000 0.977 vs 1.126 ms, 250 x 2000 0.148 vs 0.174 ms for the tile sweep; at 250 and
+    // 500 items a 1024-float stride leaves one-warp CTAs four to an SM and the tile sweep runs
+    // at half the register sweep's speed.
+    const int ld = (I + 7) / 8 * 8;
+    if (nc == 11 && ld <= 768 && threads_for(4) <= 512) {
+        v = mk.template make<11, 4, true, 0>(threads_for(4));
+    } else if (nc == 11 && threads_for(8) <= 512) {
+        if (ld <= 1024)
+            v = mk.template make<11, 8, true, 1024>(threads_for(8));
+        else if (ld <= 2048)
+            v = mk.template make<11, 8, true, 2048>(threads_for(8));
+        else
+            v = mk.template make<11, 8, true, 4096>(threads_for(8));
+    } else if (nc == 21 && threads_for(8) <= 256 && k21(ld, threads_for(8), &v)) {
+        // 21 columns: the tile sweep (exact, eight rows per thread, at most 256 threads) up to
+        // 2048 items
+    } else if (nc == 50 && threads_for(1) <= 512) {
+        v = mk.template make<50, 1, true, 0>(threads_for(1));
+    } else if (nc <= 8 && threads_for(4) <= 512) {
+        v = mk.template make<8, 4, false, 0>(threads_for(4));
+    } else if (nc <= 16 && threads_for(4) <= 512) {
+        v = mk.template make<16, 4, false, 0>(threads_for(4));
+    } else if (nc <= 32 && threads_for(2) <= 512) {
+        v = mk.template make<32, 2, false, 0>(threads_for(2));
+    } else if (nc <= 64 && threads_for(1) <= 512) {
+        v = mk.template make<64, 1, false, 0>(threads_for(1));
+    } else {
+        return false;
+    }
+    *out = v;
+    return true;
 }
 
 }  // namespace

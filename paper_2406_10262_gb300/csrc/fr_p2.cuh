@@ -104,7 +104,8 @@ __device__ __forceinline__ void p2_stage(const P2Args& a, int un, int b, unsigne
 
 // One row of the policy in base 2: p_k = 2^(g'_k + s (e_k - e_max)) for the column pairs (p2) and
 // the unpaired last column (pt); returns 1 / sum_k p_k. A row whose sum leaves [2^-100, 2^100] is
-// recomputed with its exact maximum subtracted.
+// recomputed with its exact maximum subtracted, the maximum taken over the same packed exponents
+// (padding columns carry g' = -inf there), so the scalar potentials need not stay live.
 template <int NCB, bool EXACT>
 __device__ __forceinline__ float p2_row(float sv, const f2* e2, float et, const f2* g2, float gt,
                                         const float* eh, const float (&gk)[NCB], int nc, f2* p2,
@@ -125,10 +126,13 @@ __device__ __forceinline__ float p2_row(float sv, const f2* e2, float et, const 
     upk(S2, S0, S1);
     float S = S0 + S1 + pt;
     if (__builtin_expect(!(S >= 0x1p-100f && S <= 0x1p100f), 0)) {  // exact max shift for this row
-        float M = -INFINITY;
+        float M = TAIL ? fmaf(sv, et, gt) : -INFINITY;
 #pragma unroll
-        for (int k = 0; k < NCB; ++k)
-            if (EXACT || k < nc) M = fmaxf(M, fmaf(sv, eh[k], gk[k]));
+        for (int j = 0; j < NP; ++j) {
+            float a0, a1;
+            upk(fma2(sp, e2[j], g2[j]), a0, a1);
+            M = fmaxf(M, fmaxf(a0, a1));
+        }
         S2 = 0ull;
         const f2 M2 = pk(M, M);
 #pragma unroll

@@ -311,16 +311,17 @@ class FairRank:
 
 
 class FairRankBatch:
-    """Many independent FR_PARAM_ITEM markets advanced together (wraps an fr_batch).
+    """Many independent markets advanced together (wraps an fr_batch), all FR_PARAM_ITEM or all
+    FR_PARAM_FULL_C.
 
     sizes: sequence of (n_users, n_items, n_slots); overrides apply to every market's config."""
 
-    def __init__(self, sizes, **overrides):
+    def __init__(self, sizes, param=PARAM_ITEM, **overrides):
         L = lib()
         n = len(sizes)
         cfgs = (Config * n)()
         for j, (U, I, K) in enumerate(sizes):
-            L.fr_config_default(ct.byref(cfgs[j]), U, I, K, PARAM_ITEM)
+            L.fr_config_default(ct.byref(cfgs[j]), U, I, K, param)
             for k, v in overrides.items():
                 if not hasattr(cfgs[j], k):
                     raise KeyError(k)

@@ -137,3 +137,72 @@ def test_batch_rejections():
     assert ex.value.status == 6
     with pytest.raises(fr.FairRankError):
         b.set_exposure(2, synth.dcg_exposure(5))
+
+
+# ---- free-cost markets (the paper's Problem (8)) -----------------------------------------------
+# (U, I, K): 21-column tile sweep (two markets sharing a stride-512 bucket), 11 columns in registers
+# and in the stride-1024 tile, padded 8 / 16 / 32 buckets, |I| == K, the exact 50-column kernel,
+# a single consumer
+SIZES_P1 = [(13, 300, 20), (21, 310, 20), (40, 129, 10), (30, 1000, 10), (7, 77, 5), (5, 200, 12),
+            (4, 20, 20), (6, 40, 30), (4, 50, 49), (1, 64, 5)]
+
+
+def single_p1(U, I, K, r, **kw):
+    g = fr.FairRank(U, I, K, param=fr.PARAM_FULL_C, **kw)
+    g.set_relevance(r)
+    g.set_exposure(synth.dcg_exposure(K))
+    return g
+
+
+@pytest.mark.parametrize("opt", [fr.ADAM, fr.SGD])
+def test_free_cost_batch_matches_single_contexts_and_oracle(opt):
+    """Every free-cost market of one batch (kernel variants on concurrent launches, chunked
+    consumers with their own partial rows, one graph chunk of 8 steps plus direct steps) against its
+    own single-market context on the GPU and, where the oracle is quick, the FP64 oracle: F after
+    every step; with SGD also the policies and impacts (Adam renormalises every cell's step by its
+    own gradient scale, so the two paths' different FP32 summation orders reach the policy of
+    near-stationary cells almost undamped; F is the contract there)."""
+    L, steps = 20, 11
+    kw = dict(sinkhorn_iters=L, optimizer=opt, lr=0.1 if opt == fr.ADAM else 0.5)
+    rs = [relevance(j, U, I) for j, (U, I, K) in enumerate(SIZES_P1)]
+    b = make_batch(SIZES_P1, rs, param=fr.PARAM_FULL_C, **kw)
+    F = b.step(steps)
+    assert F.shape == (steps, len(SIZES_P1))
+    for j, ((U, I, K), r) in enumerate(zip(SIZES_P1, rs)):
+        g = single_p1(U, I, K, r, **kw)
+        Fs = g.step(steps)
+        np.testing.assert_allclose(F[:, j], Fs, rtol=PAIR_RTOL)
+        if opt == fr.SGD:
+            np.testing.assert_allclose(b.policy(j), g.policy(), atol=X_ATOL)
+            imp_b, _, F_b = b.impacts(j)
+            imp_s, _, F_s = g.impacts()
+            np.testing.assert_allclose(imp_b, imp_s, rtol=PAIR_RTOL)
+        # |U| = 1: the uniform policy is optimal and the gradient is at rounding level, which Adam
+        # turns into lr-sized steps in either precision, so FP32 and FP64 walk apart there
+        if U * I <= 20000 and (U > 1 or opt == fr.SGD):
+            o = oracle.Oracle(U, I, K, param=oracle.PARAM_FULL_C, iters=L, optimizer=opt,
+                              lr=kw["lr"])
+            o.set_relevance(r.astype(np.float64))
+            o.set_exposure(synth.dcg_exposure(K))
+            Fo, _ = o.step(steps)
+            np.testing.assert_allclose(F[:, j], Fo, rtol=NSW_RTOL)
+            if opt == fr.SGD:
+                np.testing.assert_allclose(b.policy(j), o.policy(), atol=X_ATOL)
+        g.close()
+    with pytest.raises(fr.FairRankError):
+        b.theta(0)
+    b.close()
+
+
+def test_free_cost_batch_autotune_and_reset():
+    sizes = [(60, 300, 10), (45, 900, 10), (30, 200, 20)]
+    rs = [relevance(10 + j, U, I) for j, (U, I, K) in enumerate(sizes)]
+    b = make_batch(sizes, rs, param=fr.PARAM_FULL_C, sinkhorn_iters=15)
+    b.autotune()
+    for row in b.tuning():
+        assert row["consumers_per_chunk"] in (4, 16)
+    F1 = b.step(9)
+    b.reset()
+    F2 = b.step(9)
+    np.testing.assert_array_equal(F1, F2)  # deterministic, and reset restores C = 0
+    b.close()

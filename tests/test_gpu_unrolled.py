@@ -174,8 +174,8 @@ def test_autograd_rejects_stale_backward():
 
 
 def test_unrolled_config_rejections():
-    with pytest.raises(fr.FairRankError) as ex:
-        fr.FairRank(4, 30, 5, param=fr.PARAM_FULL_C, grad_mode=fr.GRAD_UNROLLED)
+    with pytest.raises(fr.FairRankError) as ex:  # beyond the free-cost adjoint's 1024 items
+        fr.FairRank(4, 1100, 5, param=fr.PARAM_FULL_C, grad_mode=fr.GRAD_UNROLLED)
     assert ex.value.status == 7
     with pytest.raises(fr.FairRankError) as ex:
         fr.FairRank(4, 30, 5, param=fr.PARAM_ITEM, grad_mode=fr.GRAD_UNROLLED, ckpt_every=0)
@@ -220,3 +220,79 @@ def test_differentiation_workload_full_size():
     gs.set_exposure(e)
     gs.set_state(param=th)
     assert l2rel(gs.grad(omega=om), oth) <= GRAD_RTOL
+
+
+# ---- free costs (the paper's Problem (8)): dL/dc for every cell ---------------------------------
+def pair_unrolled_p1(U, I, K, r, L, ce, warm=True, **kw):
+    e = synth.dcg_exposure(K)
+    g = fr.FairRank(U, I, K, param=fr.PARAM_FULL_C, sinkhorn_iters=L, grad_mode=fr.GRAD_UNROLLED,
+                    ckpt_every=ce, warm_start=int(warm), **kw)
+    g.set_relevance(np.ascontiguousarray(r, dtype=np.float32))
+    g.set_exposure(e)
+    okw = {k: v for k, v in kw.items() if k in ("optimizer", "lr", "epsilon")}
+    o = oracle.Oracle(U, I, K, param=oracle.PARAM_FULL_C, iters=L, warm_start=warm,
+                      grad_mode=oracle.GRAD_UNROLLED, **okw)
+    o.set_relevance(np.asarray(r, dtype=np.float32).astype(np.float64))
+    o.set_exposure(e)
+    return g, o
+
+
+@pytest.mark.parametrize("U,I,K,L,ce", [
+    (6, 40, 10, 20, 5),      # 11 columns
+    (5, 1000, 10, 12, 5),    # 11 columns, 256 threads, ragged last segment
+    (4, 300, 20, 15, 4),     # 21 columns
+    (3, 500, 20, 6, 2),      # 21 columns at the row limit (2 rows per thread)
+    (4, 30, 5, 17, 6),       # padded 8-column bucket
+    (3, 100, 13, 9, 3),      # padded 16-column bucket
+    (3, 60, 25, 8, 8),       # padded 32-column bucket
+    (3, 24, 24, 10, 4),      # |I| == K (no dummy column)
+    (4, 50, 5, 1, 10),       # L = 1: the output layer only
+    (4, 50, 5, 7, 1),        # a checkpoint at every iteration
+])
+def test_free_cost_unrolled_grad_matches_oracle(U, I, K, L, ce):
+    """dL/dC of every cell and dL/dr from the adjoint kernel against the oracle's reverse sweep of
+    the same L iterations from the same warm start, for F and for an explicit omega."""
+    from gpu_util import seeded_state
+    r = synth.relevance_lowrank(U, I, seed=I + K + L)
+    g, o = pair_unrolled_p1(U, I, K, r, L, ce)
+    C, _, _, gg = seeded_state(U, I, K, seed=I + L, scale=0.6)
+    g.set_state(param=C, g=gg)
+    o.set_state(param=C.astype(np.float64), g=gg.astype(np.float64))
+    _, _, F = g.impacts()
+    _, _, oF = o.impacts()
+    assert rel(F, oF) < NSW_RTOL
+    dC, dr = g.grad(want_dr=True)
+    oC, odr = o.grad(want_dr=True)
+    assert l2rel(dC, oC) <= GRAD_RTOL
+    assert l2rel(dr, odr) <= GRAD_RTOL
+    om = (0.5 + synth.uniform(I, 78, I)).astype(np.float32)
+    dC2 = g.grad(omega=om)
+    oC2 = o.grad(omega=om.astype(np.float64))
+    assert l2rel(dC2, oC2) <= GRAD_RTOL
+    # gauge invariance of the L-iteration map: every row of dL/dC_u sums to zero
+    assert np.abs(dC.sum(axis=2)).max() <= 1e-5 * np.abs(dC).max()
+    g.close()
+
+
+@pytest.mark.parametrize("opt", [fr.ADAM, fr.SGD])
+def test_free_cost_unrolled_trajectory_matches_oracle(opt):
+    """Ascent steps driven by the adjoint (optimiser applied in the adjoint kernel, then the
+    Sinkhorn kernel on the new costs): F after every step against the oracle's trajectory."""
+    U, I, K, L, ce = 8, 60, 10, 20, 6
+    r = synth.relevance_lowrank(U, I, seed=31)
+    lr = 0.1 if opt == fr.ADAM else 0.5
+    g, o = pair_unrolled_p1(U, I, K, r, L, ce, optimizer=opt, lr=lr)
+    F = g.step(12)
+    Fo, _ = o.step(12)
+    np.testing.assert_allclose(F, Fo, rtol=NSW_RTOL)
+    np.testing.assert_allclose(g.policy(), o.policy(), atol=X_ATOL)
+    done, Fs = g.solve(0.0, 3)  # the device-side loop with the adjoint in its body
+    ds, Fso = o.solve(0.0, 3)
+    assert done == ds == 3 and rel(Fs, Fso) < NSW_RTOL
+    g.close()
+
+
+def test_free_cost_unrolled_limits():
+    with pytest.raises(fr.FairRankError) as ei:
+        fr.FairRank(4, 2000, 10, param=fr.PARAM_FULL_C, grad_mode=fr.GRAD_UNROLLED)
+    assert ei.value.status == 7 and "n_items" in str(ei.value)
