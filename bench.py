@@ -82,7 +82,7 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="profiling driver: set up the workload, run this many ascent steps, exit")
     ap.add_argument("--compare", choices=["batch", "unrolled", "bf16", "paper-shapes", "p1-scale",
-                                          "precision"],
+                                          "precision", "p1-batch"],
                     default=None,
                     help="compare a layered form against the plain FP32 method (one JSON line)")
     ap.add_argument("--profile-item", choices=["implicit", "unrolled", "bf16", "batch", "metrics"],
@@ -493,7 +493,81 @@ def compare_unrolled(args):
     out["grad_rel_l2_diff_at_theta0"] = float(np.linalg.norm(a - c) / np.linalg.norm(a))
     out["grad_cosine_at_theta0"] = float(a @ c / (np.linalg.norm(a) * np.linalg.norm(c)))
     out["unrolled_over_implicit_time"] = out["unrolled"]["s_per_run"] / out["implicit"]["s_per_run"]
+    # free costs (the paper's parametrisation) on the benchmark workload: dL/dc of every cell
+    U1, I1, K1, L1, S1 = 2000, 1000, 10, 50, max(args.steps, 1) * 20
+    r1 = synth.relevance_lowrank(U1, I1, seed=0).astype(np.float32)
+    fc, res1 = {"n_users": U1, "n_items": I1, "n_slots": K1, "sinkhorn_iters": L1, "ckpt_every": 10,
+                "ascent_steps": S1}, {}
+    for name, mode in (("implicit", fr.GRAD_IMPLICIT), ("unrolled", fr.GRAD_UNROLLED)):
+        g = fr.FairRank(U1, I1, K1, param=fr.PARAM_FULL_C, sinkhorn_iters=L1, grad_mode=mode,
+                        ckpt_every=10)
+        g.set_relevance(r1)
+        g.set_exposure(synth.dcg_exposure(K1))
+        g.step(2, trace=False)
+        g.reset()
+        F, t = _timed(lambda: g.step(S1))
+        kms = g.time_kernels(3)
+        g.reset()
+        g.step(3, trace=False)
+        res1[name] = g.grad()
+        fc[name] = {"s_per_run": t, "ms_per_step": t / S1 * 1e3, "F_final": float(F[-1]),
+                    "kernel_ms": list(kms)}
+        g.close()
+    a, c = res1["implicit"].astype(np.float64).ravel(), res1["unrolled"].astype(np.float64).ravel()
+    fc["rel_F_diff_final"] = abs(fc["unrolled"]["F_final"] - fc["implicit"]["F_final"]) / \
+        abs(fc["implicit"]["F_final"])
+    fc["grad_rel_l2_diff_after_3_steps"] = float(np.linalg.norm(a - c) / np.linalg.norm(a))
+    fc["grad_cosine_after_3_steps"] = float(a @ c / (np.linalg.norm(a) * np.linalg.norm(c)))
+    fc["unrolled_over_implicit_time"] = fc["unrolled"]["s_per_run"] / fc["implicit"]["s_per_run"]
+    out["free_costs"] = fc
     return out
+
+
+def compare_p1_batch(args):
+    """The batching workload's 256 markets (|U| ~ U[100, 4000], |I| ~ U[100, 2000], K in
+    {5, 10, 20}) under free costs: one batch (autotuned chunk lengths, one launch per kernel
+    variant per step on concurrent branches, graph-captured) against the 256 markets as single
+    contexts run one after another, the same S ascent steps from C = 0; F of every market
+    compared."""
+    from paper_2406_10262_gb300 import fairrank as fr
+    from paper_2406_10262_gb300 import synth
+    S, L = max(args.steps, 1) * 8, 50
+    ms = synth.markets(256, seed=0)
+    sizes = [(m.n_users, m.n_items, m.n_slots) for m in ms]
+    rs = [synth.relevance_lowrank_fast(m.n_users, m.n_items, seed=m.seed) for m in ms]
+    cells = sum(U * I * fr.num_cols(I, K) for U, I, K in sizes)
+    b = fr.FairRankBatch(sizes, param=fr.PARAM_FULL_C, sinkhorn_iters=L)
+    for j, ((U, I, K), r) in enumerate(zip(sizes, rs)):
+        b.set_relevance(j, r)
+        b.set_exposure(j, synth.dcg_exposure(K))
+    _, tune_s = _timed(b.autotune)
+    b.step(2, trace=False)  # warm-up (graph capture)
+    b.reset()
+    l0 = b.launch_count()
+    Fb, t_batch = _timed(lambda: b.step(S))
+    launches = b.launch_count() - l0
+    tuning = b.tuning()
+    b.close()
+    Fs, t_seq = [], 0.0
+    for (U, I, K), r in zip(sizes, rs):  # one context at a time (its state freed before the next)
+        g = fr.FairRank(U, I, K, param=fr.PARAM_FULL_C, sinkhorn_iters=L)
+        g.set_relevance(r)
+        g.set_exposure(synth.dcg_exposure(K))
+        g.step(S, trace=False)  # warm-up (graph capture)
+        g.reset()
+        F, t = _timed(lambda: g.step(S))
+        Fs.append(F)
+        t_seq += t
+        g.close()
+    Fs = np.array(Fs).T
+    cu = cells * L * (S + 1)
+    return {"compare": "p1-batch", "markets": len(sizes), "ascent_steps": S, "sinkhorn_iters": L,
+            "cells": cells, "state_bytes": 3 * 4 * sum(U * fr.num_cols(I, K) * ((I + 7) // 8 * 8)
+                                                        for U, I, K in sizes),
+            "batch_s": t_batch, "sequential_s": t_seq, "speedup": t_seq / t_batch,
+            "batch_cell_updates_per_s": cu / t_batch, "sequential_cell_updates_per_s": cu / t_seq,
+            "autotune_s": tune_s, "batch_launches": launches, "buckets": tuning,
+            "rel_F_diff_final_max": float(np.max(np.abs(Fb[-1] - Fs[-1]) / np.abs(Fs[-1])))}
 
 
 def compare_bf16(args):
@@ -757,7 +831,7 @@ def main():
         frbuild.build()
         fn = {"batch": compare_batch, "unrolled": compare_unrolled, "bf16": compare_bf16,
               "paper-shapes": compare_paper_shapes, "p1-scale": compare_p1_scale,
-              "precision": compare_precision}[args.compare]
+              "precision": compare_precision, "p1-batch": compare_p1_batch}[args.compare]
         print(json.dumps(fn(args)), flush=True)
         return
     w = workload(args.workload)
