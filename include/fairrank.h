@@ -163,8 +163,9 @@ FR_API fr_status fr_get_state(fr_ctx* ctx, float* param, float* m1, float* m2, f
    items whose impact is more than 10% above / below that of the uniform policy x_uik = b_k/|I|.
    Imp_i(X_j) = sum_u r(u,i) sum_{k<K} e_k x_ujk is formed on the tensor cores from three TF32
    products per term (hi*hi + hi*lo + lo*hi of each operand's TF32 split), accumulated in FP32: the
-   error is that of an FP32 contraction. Needs n_users x n_items x 4 bytes of scratch (allocated on
-   first use). FR_ETIMEOUT if a bounded device wait of the contraction expired. */
+   error is that of an FP32 contraction. Needs about n_users x n_items x 20 bytes of scratch (V and
+   the TF32 planes of R and V; allocated on first use). FR_ETIMEOUT if a bounded device wait of the
+   contraction expired. */
 FR_API fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* better_pct,
                      double* worse_pct);
 

@@ -927,13 +927,14 @@ fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* be
     fr_status st = ensure_fresh(ctx);
     if (st != FR_OK) return st;
     // scratch in tmp: V [U][ld] floats | rmax [tiles][ld] floats | diag [ld] floats | ru [ld]
-    // doubles | out [3] doubles | column-sum partials [colsum_chunks()][ld] doubles (16-byte
-    // aligned pieces)
+    // doubles | out [3] doubles | column-sum partials [colsum_chunks()][ld] doubles | the TF32
+    // planes of R and V for the tensor cores (256-byte aligned pieces)
     const size_t ld = ctx->ld, nt = envy_tc_tiles(ctx->I);
-    auto al = [](size_t b) { return (b + 15) / 16 * 16; };
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t oV = 0, oM = oV + al(4 * (size_t)ctx->U * ld), oD = oM + al(4 * nt * ld),
                  oR = oD + al(4 * ld), oO = oR + al(8 * ld), oP = oO + al(8 * 3),
-                 need = oP + al(8 * (size_t)colsum_chunks() * ld);
+                 oT = oP + al(8 * (size_t)colsum_chunks() * ld),
+                 need = oT + al(envy_tc_plane_bytes(ctx->U, ctx->I));
     if ((st = ensure_tmp(ctx, need)) != FR_OK) return st;
     unsigned char* base = reinterpret_cast<unsigned char*>(ctx->tmp);
     float* V = reinterpret_cast<float*>(base + oV);
@@ -946,8 +947,8 @@ fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* be
     CU(launch_envy(ctx->r, ctx->r_bf16, V, ctx->U, ctx->I, ctx->ld, ctx->imp, ctx->esum,
                    reinterpret_cast<float*>(base + oM), reinterpret_cast<float*>(base + oD),
                    reinterpret_cast<double*>(base + oR), reinterpret_cast<double*>(base + oP), out,
-                   ctx->flags, polls_of(ctx->cfg.max_wait_polls), ctx->s));
-    ctx->launches += 5;
+                   ctx->flags, polls_of(ctx->cfg.max_wait_polls), base + oT, ctx->s));
+    ctx->launches += 7;
     double h[3];
     int hf[4];
     CU(cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, ctx->s));

@@ -1,22 +1,30 @@
 // fr_envy_tc.cu -- the envy contraction E = R^T V of the Sec. 4.1 metrics on the 5th-generation
 // tensor cores (tcgen05), with FP32-level accuracy from three TF32 products.
 //
-// E_ij = sum_u r(u,i) v_uj. A CTA owns a 128 x 128 tile of E (items i x items j); the contraction
-// index u (consumers) is streamed 32 at a time. Every FP32 input x is split into two TF32 parts,
-// x = hi + lo with hi = tf32(x), lo = tf32(x - hi), and the tile accumulates
-//   hi_r hi_v + hi_r lo_v + lo_r hi_v
-// in FP32 in tensor memory (the dropped lo_r lo_v term is ~2^-22 relative): 12 MMAs of
-// M = 128, N = 128, K = 8 per 32 consumers, issued by one thread (tcgen05.mma.cta_group::1.
-// kind::tf32) and tracked by an mbarrier through tcgen05.commit. Operands live in shared memory in
-// the K-major, no-swizzle canonical layout: 8-row x 16-byte core matrices, core matrices adjacent
-// in K 128 bytes apart (leading byte offset), 8-row groups 1024 bytes apart (stride byte offset).
-// The CTA's 512 threads stage the next 32 consumers (two shared buffers, operands loaded into
-// registers two stages ahead) while the tensor cores work on the current ones. The epilogue reads the accumulator rows back from tensor memory (tcgen05.ld,
-// 32 lanes per warp) and keeps only the row maxima over the tile's valid columns and, on diagonal
-// tiles, E_ii: the |I|^2 matrix is never written.
+// E_ij = sum_u r(u,i) v_uj. Every FP32 input x is split into two TF32 parts, x = hi + lo with
+// hi = tf32(x), lo = tf32(x - hi), and a tile of E accumulates hi_r hi_v + hi_r lo_v + lo_r hi_v in
+// FP32 in tensor memory (the dropped lo_r lo_v term is ~2^-22 relative).
 //
-// Every wait is bounded; on expiry the kernel records an error flag, waits (bounded) for its own
-// MMAs, frees its tensor memory and returns.
+// Two kernels:
+//  - envy_split_kernel writes R and V once as TF32 hi / lo planes, already in the operand layout the
+//    tensor cores read from shared memory: one 16 KB block per (128-item tile, 32-consumer stage,
+//    part), K-major without swizzle (8-row x 16-byte core matrices, core matrices adjacent in K 128
+//    bytes apart, 8-row groups 1024 bytes apart). O(|U| |I|) work.
+//  - envy_tc_kernel: a CTA owns a 128 x 128 tile of E (items i x items j) and runs three roles.
+//    One producer thread bulk-copies each stage's four blocks (A hi / lo from R's planes of tile i,
+//    B hi / lo from V's planes of tile j; 64 KB) into a ring of NS shared buffers. One MMA thread
+//    waits for a stage, issues its 12 MMAs (M = N = 128, K = 8; tcgen05.mma.cta_group::1.kind::tf32)
+//    and commits them to the stage's "empty" mbarrier, which frees the buffer when they are done.
+//    Eight epilogue warps add each completed chunk of 256 consumers (8 stages) from one of two
+//    128-column tensor-memory regions to FP32 running sums in registers (tcgen05.ld) while the next
+//    chunk accumulates in the other region; restarting the accumulator every 256 consumers keeps the
+//    tensor cores' FP32 accumulation within FP32 rounding of an exact sum. The kernel keeps only the
+//    row maxima over the tile's valid columns and, on diagonal tiles, E_ii: the |I|^2 matrix is
+//    never written.
+//
+// Every wait is bounded (the context's poll limit). When one expires the CTA records an error
+// flag, the other roles give up at their next wait, the producer waits (default bound) for the
+// copies it issued and the MMA thread for its last commit, and only then is the tensor memory freed.
 #include <cuda_bf16.h>
 
 #include "fr_device.cuh"
@@ -34,13 +42,15 @@ constexpr int OPER_BYTES = TM * TK * 4;       // one operand part (hi or lo) of 
 constexpr int STAGE_BYTES = 4 * OPER_BYTES;   // A_hi, A_lo, B_hi, B_lo
 constexpr int LBO = 128;                      // bytes between K-adjacent core matrices
 constexpr int SBO = (TK / 4) * 128;           // bytes between 8-row groups
+constexpr int NS = 3;                         // shared stage buffers in the ring
 constexpr unsigned kTmemCols = 2 * TN;        // two FP32 accumulator regions of TN columns
 constexpr int CHUNK = 8;                      // stages (8 x 32 consumers) per accumulator chunk
-constexpr int NTHREADS = 512;                 // staging threads (warps 0-3 also run the epilogue)
-constexpr int KGROUPS = NTHREADS / TM;        // groups of 4 consumers per stage per thread row
+constexpr int NEPI = 8;                       // epilogue warps (warps 2 .. 9)
+constexpr int NTHREADS = 32 * (2 + NEPI);     // producer warp, MMA warp, epilogue warps
 
 static_assert(TM == 128 && TN % 16 == 0 && TN >= 16 && TN <= 256, "MMA shape");
 static_assert(TN == TM, "square tiles (diagonal capture)");
+static_assert(NEPI == 8 && TN == 128, "each epilogue warp: one lane quarter, 64 columns");
 
 __device__ __forceinline__ float rval_tc(const void* r, int bf16, size_t o) {
     return bf16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(r)[o])
@@ -87,70 +97,84 @@ __device__ __forceinline__ void mma_commit(unsigned long long* bar) {
         : "memory");
 }
 
-// One stage = 32 consumers of the tile: A[m][k] = r(u0 + k, i0 + m), B[n][k] = v(u0 + k, j0 + n).
-// Thread t owns row t % 128 of both operands and the groups of 4 consumers g0 + KGROUPS q,
-// g0 = t / 128. load_stage reads them into registers (issued two stages ahead, so the global-memory
-// latency overlaps the tensor cores' work); store_stage splits each value into TF32 hi and lo parts
-// and writes one 16-byte vector per group and part.
-constexpr int QG = TK / 4 / KGROUPS;  // groups per thread per stage
-
-struct StageRegs {
-    float r[QG][4], v[QG][4];
-};
-
-__device__ __forceinline__ void load_stage(StageRegs& R, const void* r, int r_bf16, const float* V,
-                                           int U, int ld, int i0, int j0, int u0) {
-    const int t = threadIdx.x % TM, g0 = threadIdx.x / TM;
-    const int i = i0 + t, j = j0 + t;
-#pragma unroll
-    for (int q2 = 0; q2 < QG; ++q2) {
-        const int k4 = 4 * (g0 + KGROUPS * q2);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int u = u0 + k4 + q;
-            R.r[q2][q] = (u < U && i < ld) ? rval_tc(r, r_bf16, (size_t)u * ld + i) : 0.f;
-            R.v[q2][q] = (u < U && j < ld) ? V[(size_t)u * ld + j] : 0.f;
-        }
-    }
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-__device__ __forceinline__ void store_stage(unsigned char* st, const StageRegs& R) {
-    const int t = threadIdx.x % TM, g0 = threadIdx.x / TM;
-#pragma unroll
-    for (int q2 = 0; q2 < QG; ++q2) {
-        const int k4 = 4 * (g0 + KGROUPS * q2);
-        uint4 rh, rl, vh, vl;
-        unsigned* prh = &rh.x; unsigned* prl = &rl.x; unsigned* pvh = &vh.x; unsigned* pvl = &vl.x;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            prh[q] = to_tf32(R.r[q2][q]);
-            prl[q] = to_tf32(R.r[q2][q] - __uint_as_float(prh[q]));
-            pvh[q] = to_tf32(R.v[q2][q]);
-            pvl[q] = to_tf32(R.v[q2][q] - __uint_as_float(pvh[q]));
-        }
-        const int o = oper_off(t, k4);
-        *reinterpret_cast<uint4*>(st + 0 * OPER_BYTES + o) = rh;
-        *reinterpret_cast<uint4*>(st + 1 * OPER_BYTES + o) = rl;
-        *reinterpret_cast<uint4*>(st + 2 * OPER_BYTES + o) = vh;
-        *reinterpret_cast<uint4*>(st + 3 * OPER_BYTES + o) = vl;
+// Bounded wait for phase `parity` of `bar` that also gives up once another role raised *abort.
+__device__ __forceinline__ bool wait_or_abort(unsigned long long* bar, unsigned parity,
+                                              unsigned max_polls, volatile int* abort) {
+    for (unsigned it = 0; it < max_polls; ++it) {
+        unsigned done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (*abort) return false;
     }
+    return false;
 }
 
-__global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const void* __restrict__ r, int r_bf16,
-                                                        const float* __restrict__ V, int U, int I,
-                                                        int ld, float* __restrict__ rmax,
+// TF32 planes of an |U| x |I| operand (x = r, or V): for tile t = 0 .. nt-1 (128 items), stage
+// s = 0 .. nk-1 (32 consumers) and part p (0 hi, 1 lo), the 16 KB block at ((t nk + s) 2 + p) * 4096
+// words holds element (item t 128 + m, consumer s 32 + k) at oper_off(m, k). Entries beyond the
+// items or the consumers are 0. One CTA per (t, s); thread (m, g) writes consumers 4g .. 4g+3 of
+// row m, one 16-byte vector per part.
+__global__ void __launch_bounds__(1024) envy_split_kernel(const void* __restrict__ x, int x_bf16,
+                                                          int U, int I, int ld, int nk,
+                                                          unsigned* __restrict__ planes) {
+    const int t = blockIdx.y, s = blockIdx.x;
+    const int m = threadIdx.x % TM, g = threadIdx.x / TM;
+    const int i = t * TM + m;
+    uint4 hi, lo;
+    unsigned* ph = &hi.x;
+    unsigned* pl = &lo.x;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int u = s * TK + 4 * g + q;
+        const float v = (u < U && i < I) ? rval_tc(x, x_bf16, (size_t)u * ld + i) : 0.f;
+        ph[q] = to_tf32(v);
+        pl[q] = to_tf32(v - __uint_as_float(ph[q]));
+    }
+    unsigned char* blk = reinterpret_cast<unsigned char*>(planes + (size_t)(t * nk + s) * 2 * (OPER_BYTES / 4));
+    const int o = oper_off(m, 4 * g);
+    *reinterpret_cast<uint4*>(blk + o) = hi;
+    *reinterpret_cast<uint4*>(blk + OPER_BYTES + o) = lo;
+}
+
+// Shared memory: NS stage buffers, then the mbarriers (full / empty per stage, chunk-done / region-
+// free per accumulator region), the tensor-memory address and the abort flag.
+constexpr int SMEM_BARS = NS * STAGE_BYTES;
+constexpr int SMEM_BYTES = SMEM_BARS + (2 * NS + 4) * 8 + 16;
+
+__global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const unsigned* __restrict__ Rp,
+                                                        const unsigned* __restrict__ Vp, int I,
+                                                        int ld, int nk, float* __restrict__ rmax,
                                                         float* __restrict__ diag, int* err,
                                                         unsigned max_polls) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* stages = smem_raw;                                    // 2 x STAGE_BYTES
-    unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + 2 * STAGE_BYTES);
-    unsigned* tmem_slot = reinterpret_cast<unsigned*>(bar + 2);
+    unsigned char* stages = smem_raw;
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(smem_raw + SMEM_BARS);
+    unsigned long long* empty = full + NS;
+    unsigned long long* accf = empty + NS;  // chunk accumulated in region r
+    unsigned long long* acce = accf + 2;    // region r read by every epilogue warp
+    unsigned* tmem_slot = reinterpret_cast<unsigned*>(acce + 2);
+    volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
 
     if (tid == 0) {
-        mbar_init(bar, 1);
-        mbar_init(bar + 1, 1);
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(full + s, 1);
+            mbar_init(empty + s, 1);
+        }
+        for (int r = 0; r < 2; ++r) {
+            mbar_init(accf + r, 1);
+            mbar_init(acce + r, NEPI);
+        }
+        *abort = 0;
         fence_mbar_init();
     }
     if (warp == 0) {
@@ -164,108 +188,133 @@ __global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const void* __rest
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned tmem = *tmem_slot;
-
-    // Running sums of the tile in registers: warp w holds the tile rows of its tensor-memory lane
-    // quarter, 32 (w % 4) + lane, and the 32 columns 32 (w / 4) .. + 31.
-    const int q4 = warp & 3, cslice = warp >> 2;
-    float sum[32];
-#pragma unroll
-    for (int q = 0; q < 32; ++q) sum[q] = 0.f;
-    auto read_chunk = [&](int c) {  // adds chunk c's accumulator (region c & 1) to the sums
-        unsigned v[32];
-        const unsigned taddr = tmem + ((unsigned)(q4 * 32) << 16) + (unsigned)((c & 1) * TN + cslice * 32);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
-            "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, "
-            "%26, %27, %28, %29, %30, %31}, [%32];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-              "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-              "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
-              "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-              "=r"(v[30]), "=r"(v[31])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int q = 0; q < 32; ++q) sum[q] += __uint_as_float(v[q]);
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    };
-
-    const int nk = (U + TK - 1) / TK;
     const int nch = (nk + CHUNK - 1) / CHUNK;
-    bool ok = true;
-    int issued = -1;  // last stage whose MMAs were committed
-    int nread = 0;    // chunks added to the running sums (in order)
-    StageRegs regs;
-    load_stage(regs, r, r_bf16, V, U, ld, i0, j0, 0);
-    for (int kc = 0; kc < nk; ++kc) {
-        const int st = kc & 1;
-        unsigned char* sbuf = stages + st * STAGE_BYTES;
-        if (kc >= 2 && ok) {  // the MMAs that read this buffer two stages ago are done
-            if (!mbar_wait(bar + st, ((kc - 2) >> 1) & 1u, max_polls)) ok = false;
-        }
-        if (!__syncthreads_and(ok)) {
-            ok = false;
-            break;
-        }
-        // the chunk that ended with stage kc - 2 is complete (waited for just above): add it
-        // before chunk kc / CHUNK + 1 reuses its region
-        if (kc % CHUNK == 1 && kc > CHUNK) read_chunk(nread++);
-        store_stage(sbuf, regs);
-        if (kc + 1 < nk) load_stage(regs, r, r_bf16, V, U, ld, i0, j0, (kc + 1) * TK);
-        fence_proxy_async_smem();  // generic-proxy stores -> the tensor cores' (async proxy) reads
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const unsigned base = smem_u32(sbuf);
-            const unsigned dst = tmem + (unsigned)(((kc / CHUNK) & 1) * TN);
-            const bool first = kc % CHUNK == 0;
+
+    // Epilogue warps' running sums: warp w holds the tile rows of its tensor-memory lane quarter,
+    // 32 (w % 4) + lane, and the 64 columns 64 ((w - 2) / 4) .. + 63.
+    const int q4 = warp & 3, half = (warp - 2) >> 2;
+    float sum[64];
 #pragma unroll
-            for (int ks = 0; ks < TK / KSTEP; ++ks) {
-                const unsigned koff = (unsigned)(ks * 2 * LBO);  // two core matrices per K step
-                const unsigned long long ah = smem_desc(base + 0 * OPER_BYTES + koff);
-                const unsigned long long al = smem_desc(base + 1 * OPER_BYTES + koff);
-                const unsigned long long bh = smem_desc(base + 2 * OPER_BYTES + koff);
-                const unsigned long long bl = smem_desc(base + 3 * OPER_BYTES + koff);
-                mma_tf32(dst, ah, bh, (first && ks == 0) ? 0u : 1u);
-                mma_tf32(dst, ah, bl, 1u);
-                mma_tf32(dst, al, bh, 1u);
+    for (int q = 0; q < 64; ++q) sum[q] = 0.f;
+
+    if (warp == 0) {
+        if (lane == 0) {  // producer: the stage's four 16 KB blocks into the ring
+            const unsigned char* ra =
+                reinterpret_cast<const unsigned char*>(Rp + (size_t)blockIdx.y * nk * 2 * (OPER_BYTES / 4));
+            const unsigned char* vb =
+                reinterpret_cast<const unsigned char*>(Vp + (size_t)blockIdx.x * nk * 2 * (OPER_BYTES / 4));
+            int last = -1;
+            for (int kc = 0; kc < nk; ++kc) {
+                const int s = kc % NS;
+                if (kc >= NS && !wait_or_abort(empty + s, ((kc / NS) - 1) & 1u, max_polls, abort)) {
+                    *abort = 1;
+                    break;
+                }
+                unsigned char* st = stages + s * STAGE_BYTES;
+                const size_t kb = (size_t)kc * 2 * OPER_BYTES;
+                mbar_arrive_expect_tx(full + s, STAGE_BYTES);
+                bulk_g2s(st + 0 * OPER_BYTES, ra + kb, OPER_BYTES, full + s);
+                bulk_g2s(st + 1 * OPER_BYTES, ra + kb + OPER_BYTES, OPER_BYTES, full + s);
+                bulk_g2s(st + 2 * OPER_BYTES, vb + kb, OPER_BYTES, full + s);
+                bulk_g2s(st + 3 * OPER_BYTES, vb + kb + OPER_BYTES, OPER_BYTES, full + s);
+                last = kc;
             }
-            mma_commit(bar + st);
+            // every copy issued here has landed before the CTA can leave (the last fill of each
+            // buffer; earlier ones were consumed before the buffer was refilled)
+            for (int kc = last - NS + 1 > 0 ? last - NS + 1 : 0; kc <= last; ++kc)
+                mbar_wait(full + kc % NS, (kc / NS) & 1u, kDefaultPolls);
         }
-        issued = kc;
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            int last = -1;
+            for (int kc = 0; kc < nk; ++kc) {
+                const int s = kc % NS, c = kc / CHUNK;
+                if (kc % CHUNK == 0 && c >= 2 &&
+                    !wait_or_abort(acce + (c & 1), ((c >> 1) - 1) & 1u, max_polls, abort)) {
+                    *abort = 1;
+                    break;
+                }
+                if (!wait_or_abort(full + s, (kc / NS) & 1u, max_polls, abort)) {
+                    *abort = 1;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const unsigned base = smem_u32(stages + s * STAGE_BYTES);
+                const unsigned dst = tmem + (unsigned)((c & 1) * TN);
+                const bool first = kc % CHUNK == 0;
+#pragma unroll
+                for (int ks = 0; ks < TK / KSTEP; ++ks) {
+                    const unsigned koff = (unsigned)(ks * 2 * LBO);  // two core matrices per K step
+                    const unsigned long long ah = smem_desc(base + 0 * OPER_BYTES + koff);
+                    const unsigned long long al = smem_desc(base + 1 * OPER_BYTES + koff);
+                    const unsigned long long bh = smem_desc(base + 2 * OPER_BYTES + koff);
+                    const unsigned long long bl = smem_desc(base + 3 * OPER_BYTES + koff);
+                    mma_tf32(dst, ah, bh, (first && ks == 0) ? 0u : 1u);
+                    mma_tf32(dst, ah, bl, 1u);
+                    mma_tf32(dst, al, bh, 1u);
+                }
+                mma_commit(empty + s);  // the buffer is free once these MMAs are done
+                if (kc % CHUNK == CHUNK - 1 || kc == nk - 1) mma_commit(accf + (c & 1));
+                last = kc;
+            }
+            // no MMA of this CTA is still running when it frees the tensor memory
+            if (last >= 0) mbar_wait(empty + last % NS, (last / NS) & 1u, kDefaultPolls);
+        }
+    } else {  // epilogue: chunk c of region c & 1 into the running sums, then free the region
+        for (int c = 0; c < nch; ++c) {
+            const bool w = wait_or_abort(accf + (c & 1), (c >> 1) & 1u, max_polls, abort);
+            if (!__all_sync(FULL, w)) {
+                *abort = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                unsigned v[32];
+                const unsigned taddr = tmem + ((unsigned)(q4 * 32) << 16) +
+                                       (unsigned)((c & 1) * TN + half * 64 + h * 32);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+                    "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, "
+                    "%26, %27, %28, %29, %30, %31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                      "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                      "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
+                      "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+                      "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+                      "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 32; ++q) sum[h * 32 + q] += __uint_as_float(v[q]);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce + (c & 1));
+        }
     }
-    // all MMAs complete: the last commit tracks every earlier one of the issuing thread. If this
-    // wait (or an earlier one) expired, the CTA still waits, with the default bound, for its own
-    // MMAs before it frees the tensor memory and leaves.
-    if (issued >= 0 && !mbar_wait(bar + (issued & 1), (issued >> 1) & 1u, ok ? max_polls : 0u))
-        ok = false;
-    if (issued >= 0 && !__syncthreads_and(ok))
-        mbar_wait(bar + (issued & 1), (issued >> 1) & 1u, kDefaultPolls);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (!__syncthreads_and(ok)) {
+
+    __syncthreads();  // every role is done (or gave up) and drained its own asynchronous work
+    const bool good = *abort == 0;
+    float* red = reinterpret_cast<float*>(stages);  // the stage buffers are idle now
+    if (!good) {
         if (tid == 0) atomicOr(err, 4);
-    } else {
-        while (nread < nch) read_chunk(nread++);  // the last one or two chunks
-        // row maxima over the tile's valid columns: each warp over its 32 columns, then the four
-        // column slices of a row combined through shared memory (the stage buffers are idle now)
+    } else if (warp >= 2) {
+        // row maxima over the tile's valid columns (this warp's 64), and E_ii on diagonal tiles
         const int row = q4 * 32 + lane, i = i0 + row;
         float m = -INFINITY, d = 0.f;
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-            if (j0 + cslice * 32 + q < I) m = fmaxf(m, sum[q]);
-            if (q == lane) d = sum[q];
+        for (int q = 0; q < 64; ++q) {
+            if (j0 + half * 64 + q < I) m = fmaxf(m, sum[q]);
+            if (half * 64 + q == row) d = sum[q];
         }
-        if (i0 == j0 && cslice == q4 && i < I) diag[i] = d;  // column j = i sits in this slice
-        float* red = reinterpret_cast<float*>(stages);
-        red[cslice * TM + row] = m;
-        __syncthreads();
-        if (warp < TM / 32 && i < I) {
-            float mm = red[row];
-#pragma unroll
-            for (int sl = 1; sl < TN / 32; ++sl) mm = fmaxf(mm, red[sl * TM + row]);
-            rmax[(size_t)blockIdx.x * ld + i] = mm;
-        }
+        if (i0 == j0 && (row >> 6) == half && i < I) diag[i] = d;
+        red[half * TM + row] = m;
+    }
+    __syncthreads();
+    if (good && warp >= 2 && half == 0) {
+        const int row = q4 * 32 + lane, i = i0 + row;
+        if (i < I) rmax[(size_t)blockIdx.x * ld + i] = fmaxf(red[row], red[TM + row]);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -278,16 +327,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const void* __rest
 }  // namespace
 
 int envy_tc_tiles(int I) { return (I + TM - 1) / TM; }
-size_t envy_tc_smem() { return 2 * STAGE_BYTES + 64; }
+size_t envy_tc_smem() { return SMEM_BYTES; }
+size_t envy_tc_plane_bytes(int U, int I) {
+    const size_t nt = (size_t)envy_tc_tiles(I), nk = (size_t)(U + TK - 1) / TK;
+    return 2 * nt * nk * 2 * OPER_BYTES;  // R and V, hi and lo
+}
 
 cudaError_t launch_envy_tc(const void* r, int r_bf16, const float* V, int U, int I, int ld,
-                           float* rmax, float* diag, int* err, unsigned max_polls,
+                           float* rmax, float* diag, int* err, unsigned max_polls, void* planes,
                            cudaStream_t s) {
-    const int nt = envy_tc_tiles(I);
-    cudaError_t e = raise_smem_limit((const void*)envy_tc_kernel, envy_tc_smem());
+    const int nt = envy_tc_tiles(I), nk = (U + TK - 1) / TK;
+    unsigned* Rp = static_cast<unsigned*>(planes);
+    unsigned* Vp = Rp + (size_t)nt * nk * 2 * (OPER_BYTES / 4);
+    envy_split_kernel<<<dim3(nk, nt), 1024, 0, s>>>(r, r_bf16, U, I, ld, nk, Rp);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    envy_tc_kernel<<<dim3(nt, nt), NTHREADS, envy_tc_smem(), s>>>(r, r_bf16, V, U, I, ld, rmax, diag,
-                                                                 err, max_polls);
+    envy_split_kernel<<<dim3(nk, nt), 1024, 0, s>>>(V, 0, U, I, ld, nk, Vp);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = raise_smem_limit((const void*)envy_tc_kernel, envy_tc_smem())) != cudaSuccess) return e;
+    envy_tc_kernel<<<dim3(nt, nt), NTHREADS, envy_tc_smem(), s>>>(Rp, Vp, I, ld, nk, rmax, diag, err,
+                                                                 max_polls);
     return cudaGetLastError();
 }
 

@@ -260,13 +260,16 @@ cudaError_t launch_solve_cond(const DevState* st, int* ctl, cudaGraphConditional
 // an expired bounded wait sets bit 4 of *err); rmax holds envy_tc_tiles(I) rows.
 int envy_tc_tiles(int I);
 size_t envy_tc_smem();
+// scratch of the TF32 planes of R and V (16-byte aligned), written by launch_envy_tc
+size_t envy_tc_plane_bytes(int U, int I);
 cudaError_t launch_v_p1(const P1Args& a, float* V, cudaStream_t s);
 cudaError_t launch_v_p2(const P2Args& a, float* V, cudaStream_t s);
 cudaError_t launch_envy_tc(const void* r, int r_bf16, const float* V, int U, int I, int ld,
-                           float* rmax, float* diag, int* err, unsigned max_polls, cudaStream_t s);
+                           float* rmax, float* diag, int* err, unsigned max_polls, void* planes,
+                           cudaStream_t s);
 cudaError_t launch_envy(const void* r, int r_bf16, const float* V, int U, int I, int ld,
                         const double* imp, double esum, float* rmax, float* diag, double* ru,
-                        double* ru_part, double* out, int* err, unsigned max_polls,
+                        double* ru_part, double* out, int* err, unsigned max_polls, void* planes,
                         cudaStream_t s);
 int colsum_chunks();  // FP64 partials [colsum_chunks()][ld] of the column sums of r (ru_part)
 // Frank-Wolfe certificate (fr_metrics.cu): one of a1 / a2 non-null (the policy's form); G CTAs

@@ -190,10 +190,10 @@ int colsum_chunks() { return COLSUM_CHUNKS; }
 
 cudaError_t launch_envy(const void* r, int r_bf16, const float* V, int U, int I, int ld,
                         const double* imp, double esum, float* rmax, float* diag, double* ru,
-                        double* ru_part, double* out, int* err, unsigned max_polls,
+                        double* ru_part, double* out, int* err, unsigned max_polls, void* planes,
                         cudaStream_t s) {
     const int nt = envy_tc_tiles(I);
-    cudaError_t e = launch_envy_tc(r, r_bf16, V, U, I, ld, rmax, diag, err, max_polls, s);
+    cudaError_t e = launch_envy_tc(r, r_bf16, V, U, I, ld, rmax, diag, err, max_polls, planes, s);
     if (e != cudaSuccess) return e;
     colsum_kernel<<<dim3((I + 255) / 256, COLSUM_CHUNKS), 256, 0, s>>>(r, r_bf16, U, I, ld, ru_part);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
