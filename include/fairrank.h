@@ -169,6 +169,11 @@ FR_API fr_status fr_get_state(fr_ctx* ctx, float* param, float* m1, float* m2, f
 FR_API fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* better_pct,
                      double* worse_pct);
 
+/* Per-item envy of Sec. 4.1 at the current policy: envy[i] = max_j (Imp_i(X_j) - Imp_i(X_i)) for
+   every item, host doubles [n_items] (non-NULL, else FR_EINVAL). The same contraction and error as
+   fr_metrics, whose mean envy is the mean of this vector; same scratch and FR_ETIMEOUT. */
+FR_API fr_status fr_item_envy(fr_ctx* ctx, double* envy);
+
 /* Optimality certificate of the current policy (host doubles, each nullable). F is concave in X
    and each X_u ranges over the polytope of Eqs. (1)-(3), so F* - F(X) <= max_Y <grad F(X), Y - X>;
    with e non-increasing the maximising Y_u ranks the items by r(u,i)/Imp_i (rearrangement), giving

@@ -920,25 +920,25 @@ fr_status fr_get_state(fr_ctx* ctx, float* param, float* m1, float* m2, float* g
     return FR_OK;
 }
 
-fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* better_pct,
-                     double* worse_pct) {
-    if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
-    Join j(ctx);
+// One evaluation of the Sec. 4.1 metrics; h receives mean envy, better %, worse %; env_host, when
+// set, the per-item envy max_j (E_ij - E_ii) [I].
+static fr_status metrics_run(fr_ctx* ctx, double h[3], double* env_host) {
     fr_status st = ensure_fresh(ctx);
     if (st != FR_OK) return st;
     // scratch in tmp: V [U][ld] floats | rmax [tiles][ld] floats | diag [ld] floats | ru [ld]
-    // doubles | out [3] doubles | column-sum partials [colsum_chunks()][ld] doubles | the TF32
-    // planes of R and V for the tensor cores (256-byte aligned pieces)
+    // doubles | out [3] doubles | column-sum partials [colsum_chunks()][ld] doubles | per-item envy
+    // [ld] doubles | the TF32 planes of R and V for the tensor cores (256-byte aligned pieces)
     const size_t ld = ctx->ld, nt = envy_tc_tiles(ctx->I);
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t oV = 0, oM = oV + al(4 * (size_t)ctx->U * ld), oD = oM + al(4 * nt * ld),
                  oR = oD + al(4 * ld), oO = oR + al(8 * ld), oP = oO + al(8 * 3),
-                 oT = oP + al(8 * (size_t)colsum_chunks() * ld),
+                 oE = oP + al(8 * (size_t)colsum_chunks() * ld), oT = oE + al(8 * ld),
                  need = oT + al(envy_tc_plane_bytes(ctx->U, ctx->I));
     if ((st = ensure_tmp(ctx, need)) != FR_OK) return st;
     unsigned char* base = reinterpret_cast<unsigned char*>(ctx->tmp);
     float* V = reinterpret_cast<float*>(base + oV);
     double* out = reinterpret_cast<double*>(base + oO);
+    double* env = env_host ? reinterpret_cast<double*>(base + oE) : nullptr;
     if (ctx->p2)
         CU(launch_v_p2(p2_args(ctx, ctx->part), V, ctx->s));
     else
@@ -947,19 +947,37 @@ fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* be
     CU(launch_envy(ctx->r, ctx->r_bf16, V, ctx->U, ctx->I, ctx->ld, ctx->imp, ctx->esum,
                    reinterpret_cast<float*>(base + oM), reinterpret_cast<float*>(base + oD),
                    reinterpret_cast<double*>(base + oR), reinterpret_cast<double*>(base + oP), out,
-                   ctx->flags, polls_of(ctx->cfg.max_wait_polls), base + oT, ctx->s));
+                   env, ctx->flags, polls_of(ctx->cfg.max_wait_polls), base + oT, ctx->s));
     ctx->launches += 7;
-    double h[3];
     int hf[4];
-    CU(cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, ctx->s));
+    CU(cudaMemcpyAsync(h, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->s));
+    if (env) CU(cudaMemcpyAsync(env_host, env, sizeof(double) * ctx->I, cudaMemcpyDeviceToHost, ctx->s));
     CU(cudaMemcpyAsync(hf, ctx->flags, sizeof hf, cudaMemcpyDeviceToHost, ctx->s));
     if ((st = read_state(ctx)) != FR_OK) return st;
     if (hf[0] & 4) return fail(ctx, FR_ETIMEOUT, "a bounded wait of the envy contraction expired");
+    return FR_OK;
+}
+
+fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* better_pct,
+                     double* worse_pct) {
+    if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
+    Join j(ctx);
+    double h[3];
+    fr_status st = metrics_run(ctx, h, nullptr);
+    if (st != FR_OK) return st;
     if (utility) *utility = ctx->st_host->utility;
     if (mean_envy) *mean_envy = h[0];
     if (better_pct) *better_pct = h[1];
     if (worse_pct) *worse_pct = h[2];
     return FR_OK;
+}
+
+fr_status fr_item_envy(fr_ctx* ctx, double* envy) {
+    if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
+    if (!envy) return fail(ctx, FR_EINVAL, "envy is NULL");
+    Join j(ctx);
+    double h[3];
+    return metrics_run(ctx, h, envy);
 }
 
 fr_status fr_certificate(fr_ctx* ctx, double* gap, double* col_residual) {

@@ -10,17 +10,19 @@
 //    tensor cores read from shared memory: one 16 KB block per (128-item tile, 32-consumer stage,
 //    part), K-major without swizzle (8-row x 16-byte core matrices, core matrices adjacent in K 128
 //    bytes apart, 8-row groups 1024 bytes apart). O(|U| |I|) work.
-//  - envy_tc_kernel: a CTA owns a 128 x 128 tile of E (items i x items j) and runs three roles.
-//    One producer thread bulk-copies each stage's four blocks (A hi / lo from R's planes of tile i,
-//    B hi / lo from V's planes of tile j; 64 KB) into a ring of NS shared buffers. One MMA thread
-//    waits for a stage, issues its 12 MMAs (M = N = 128, K = 8; tcgen05.mma.cta_group::1.kind::tf32)
-//    and commits them to the stage's "empty" mbarrier, which frees the buffer when they are done.
-//    Eight epilogue warps add each completed chunk of 256 consumers (8 stages) from one of two
-//    128-column tensor-memory regions to FP32 running sums in registers (tcgen05.ld) while the next
-//    chunk accumulates in the other region; restarting the accumulator every 256 consumers keeps the
+//  - envy_tc_kernel: a CTA owns a 128 x 256 tile of E (items i x items j) and runs three roles.
+//    One producer thread bulk-copies each stage's six blocks (A hi / lo from R's planes of tile i,
+//    B hi / lo from V's planes of the two 128-item tiles of j, which land as one 256-row operand;
+//    96 KB) into a ring of NS shared buffers. One MMA thread waits for a stage, issues its 12 MMAs
+//    (M = 128, N = 256, K = 8; tcgen05.mma.cta_group::1.kind::tf32) and commits them to the stage's
+//    "empty" mbarrier, which frees the buffer when they are done. Eight epilogue warps add each
+//    completed chunk of 256 consumers (8 stages) from one of two 256-column tensor-memory regions
+//    (all 512 columns) to FP32 running sums in registers (tcgen05.ld) while the next chunk
+//    accumulates in the other region; restarting the accumulator every 256 consumers keeps the
 //    tensor cores' FP32 accumulation within FP32 rounding of an exact sum. The kernel keeps only the
-//    row maxima over the tile's valid columns and, on diagonal tiles, E_ii: the |I|^2 matrix is
-//    never written.
+//    row maxima over the tile's valid columns and E_ii where the tile crosses the diagonal: the
+//    |I|^2 matrix is never written. The 256-wide tile reads 3/4 of the operand bytes per product
+//    of a 128 x 128 tile, from L2 and from shared memory alike.
 //
 // Every wait is bounded (the context's poll limit). When one expires the CTA records an error
 // flag, the other roles give up at their next wait, the producer waits (default bound) for the
@@ -35,22 +37,28 @@ namespace fr {
 namespace {
 
 constexpr int TM = 128;                       // tile rows (items i), MMA M
-constexpr int TN = 128;                       // tile columns (items j), MMA N
+constexpr int TN = 256;                       // tile columns (items j), MMA N
+constexpr int TP = 128;                       // items per plane tile (A: one, B: TN / TP of them)
 constexpr int TK = 32;                        // consumers per stage
 constexpr int KSTEP = 8;                      // K of one tf32 MMA (32 bytes per row)
-constexpr int OPER_BYTES = TM * TK * 4;       // one operand part (hi or lo) of one stage: 16 KB
-constexpr int STAGE_BYTES = 4 * OPER_BYTES;   // A_hi, A_lo, B_hi, B_lo
+constexpr int OPER_BYTES = TP * TK * 4;       // one plane block (128 items, hi or lo): 16 KB
+constexpr int A_BYTES = OPER_BYTES;           // A part of a stage (128 rows)
+constexpr int B_BYTES = (TN / TP) * OPER_BYTES;  // B part of a stage (256 rows)
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // A_hi, A_lo, B_hi, B_lo: 96 KB
 constexpr int LBO = 128;                      // bytes between K-adjacent core matrices
 constexpr int SBO = (TK / 4) * 128;           // bytes between 8-row groups
-constexpr int NS = 3;                         // shared stage buffers in the ring
-constexpr unsigned kTmemCols = 2 * TN;        // two FP32 accumulator regions of TN columns
+constexpr int NS = 2;                         // shared stage buffers in the ring
+constexpr unsigned kTmemCols = 2 * TN;        // two FP32 accumulator regions of TN columns: 512
 constexpr int CHUNK = 8;                      // stages (8 x 32 consumers) per accumulator chunk
 constexpr int NEPI = 8;                       // epilogue warps (warps 2 .. 9)
 constexpr int NTHREADS = 32 * (2 + NEPI);     // producer warp, MMA warp, epilogue warps
+constexpr int ECOLS = TN / 2;                 // columns per epilogue warp
+constexpr int kGroupM = 16;                   // row tiles per group of the CTA order
 
 static_assert(TM == 128 && TN % 16 == 0 && TN >= 16 && TN <= 256, "MMA shape");
-static_assert(TN == TM, "square tiles (diagonal capture)");
-static_assert(NEPI == 8 && TN == 128, "each epilogue warp: one lane quarter, 64 columns");
+static_assert(TN % TP == 0 && TM == TP, "operands assembled from 128-item plane blocks");
+static_assert(NEPI == 8, "each epilogue warp: one lane quarter, half of the columns");
+static_assert(kTmemCols <= 512, "tensor memory columns");
 
 __device__ __forceinline__ float rval_tc(const void* r, int bf16, size_t o) {
     return bf16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(r)[o])
@@ -64,7 +72,7 @@ __device__ __forceinline__ unsigned to_tf32(float x) {
     return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
 }
 
-// Byte offset of element (row m, k) of a 128 x 32 K-major operand part.
+// Byte offset of element (row m, k) of a K-major operand part of 32 columns (any number of rows).
 __host__ __device__ constexpr int oper_off(int m, int k) {
     return (m / 8) * SBO + (k / 4) * LBO + (m % 8) * 16 + (k % 4) * 4;
 }
@@ -126,8 +134,8 @@ __global__ void __launch_bounds__(1024) envy_split_kernel(const void* __restrict
                                                           int U, int I, int ld, int nk,
                                                           unsigned* __restrict__ planes) {
     const int t = blockIdx.y, s = blockIdx.x;
-    const int m = threadIdx.x % TM, g = threadIdx.x / TM;
-    const int i = t * TM + m;
+    const int m = threadIdx.x % TP, g = threadIdx.x / TP;
+    const int i = t * TP + m;
     uint4 hi, lo;
     unsigned* ph = &hi.x;
     unsigned* pl = &lo.x;
@@ -151,7 +159,8 @@ constexpr int SMEM_BYTES = SMEM_BARS + (2 * NS + 4) * 8 + 16;
 
 __global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const unsigned* __restrict__ Rp,
                                                         const unsigned* __restrict__ Vp, int I,
-                                                        int ld, int nk, float* __restrict__ rmax,
+                                                        int ld, int nk, int nt, int ntj,
+                                                        float* __restrict__ rmax,
                                                         float* __restrict__ diag, int* err,
                                                         unsigned max_polls) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -163,7 +172,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const unsigned* __
     unsigned* tmem_slot = reinterpret_cast<unsigned*>(acce + 2);
     volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
+    // CTA b -> tile (ti, tj): groups of kGroupM row tiles, column tiles in order within a group and
+    // row tiles fastest, so the CTAs resident at one time cover a compact block of tiles and reuse
+    // each other's operand tiles from L2 instead of streaming all of V once per row of tiles
+    const int per_group = kGroupM * ntj, grp = blockIdx.x / per_group, first = grp * kGroupM;
+    const int gm = min(nt - first, kGroupM), rem = blockIdx.x - grp * per_group;
+    const int ti = first + rem % gm, tj = rem / gm;
+    const int i0 = ti * TM, j0 = tj * TN;
 
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
@@ -191,18 +206,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const unsigned* __
     const int nch = (nk + CHUNK - 1) / CHUNK;
 
     // Epilogue warps' running sums: warp w holds the tile rows of its tensor-memory lane quarter,
-    // 32 (w % 4) + lane, and the 64 columns 64 ((w - 2) / 4) .. + 63.
+    // 32 (w % 4) + lane, and the 128 columns 128 ((w - 2) / 4) .. + 127.
     const int q4 = warp & 3, half = (warp - 2) >> 2;
-    float sum[64];
+    float sum[ECOLS];
 #pragma unroll
-    for (int q = 0; q < 64; ++q) sum[q] = 0.f;
+    for (int q = 0; q < ECOLS; ++q) sum[q] = 0.f;
 
     if (warp == 0) {
-        if (lane == 0) {  // producer: the stage's four 16 KB blocks into the ring
-            const unsigned char* ra =
-                reinterpret_cast<const unsigned char*>(Rp + (size_t)blockIdx.y * nk * 2 * (OPER_BYTES / 4));
+        if (lane == 0) {  // producer: the stage's six 16 KB blocks into the ring
+            const size_t tile_bytes = (size_t)nk * 2 * OPER_BYTES;  // one plane tile, all stages
+            const unsigned char* ra = reinterpret_cast<const unsigned char*>(Rp) + (size_t)ti * tile_bytes;
             const unsigned char* vb =
-                reinterpret_cast<const unsigned char*>(Vp + (size_t)blockIdx.x * nk * 2 * (OPER_BYTES / 4));
+                reinterpret_cast<const unsigned char*>(Vp) + (size_t)tj * (TN / TP) * tile_bytes;
             int last = -1;
             for (int kc = 0; kc < nk; ++kc) {
                 const int s = kc % NS;
@@ -213,10 +228,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const unsigned* __
                 unsigned char* st = stages + s * STAGE_BYTES;
                 const size_t kb = (size_t)kc * 2 * OPER_BYTES;
                 mbar_arrive_expect_tx(full + s, STAGE_BYTES);
-                bulk_g2s(st + 0 * OPER_BYTES, ra + kb, OPER_BYTES, full + s);
-                bulk_g2s(st + 1 * OPER_BYTES, ra + kb + OPER_BYTES, OPER_BYTES, full + s);
-                bulk_g2s(st + 2 * OPER_BYTES, vb + kb, OPER_BYTES, full + s);
-                bulk_g2s(st + 3 * OPER_BYTES, vb + kb + OPER_BYTES, OPER_BYTES, full + s);
+                bulk_g2s(st, ra + kb, OPER_BYTES, full + s);                       // A hi
+                bulk_g2s(st + A_BYTES, ra + kb + OPER_BYTES, OPER_BYTES, full + s);  // A lo
+#pragma unroll
+                for (int h = 0; h < TN / TP; ++h) {  // B hi, B lo: rows h 128 .. of the operand
+                    const unsigned char* vt = vb + h * tile_bytes + kb;
+                    bulk_g2s(st + 2 * A_BYTES + h * OPER_BYTES, vt, OPER_BYTES, full + s);
+                    bulk_g2s(st + 2 * A_BYTES + B_BYTES + h * OPER_BYTES, vt + OPER_BYTES, OPER_BYTES,
+                             full + s);
+                }
                 last = kc;
             }
             // every copy issued here has landed before the CTA can leave (the last fill of each
@@ -245,10 +265,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const unsigned* __
 #pragma unroll
                 for (int ks = 0; ks < TK / KSTEP; ++ks) {
                     const unsigned koff = (unsigned)(ks * 2 * LBO);  // two core matrices per K step
-                    const unsigned long long ah = smem_desc(base + 0 * OPER_BYTES + koff);
-                    const unsigned long long al = smem_desc(base + 1 * OPER_BYTES + koff);
-                    const unsigned long long bh = smem_desc(base + 2 * OPER_BYTES + koff);
-                    const unsigned long long bl = smem_desc(base + 3 * OPER_BYTES + koff);
+                    const unsigned long long ah = smem_desc(base + koff);
+                    const unsigned long long al = smem_desc(base + A_BYTES + koff);
+                    const unsigned long long bh = smem_desc(base + 2 * A_BYTES + koff);
+                    const unsigned long long bl = smem_desc(base + 2 * A_BYTES + B_BYTES + koff);
                     mma_tf32(dst, ah, bh, (first && ks == 0) ? 0u : 1u);
                     mma_tf32(dst, ah, bl, 1u);
                     mma_tf32(dst, al, bh, 1u);
@@ -269,10 +289,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const unsigned* __
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < ECOLS / 32; ++h) {
                 unsigned v[32];
                 const unsigned taddr = tmem + ((unsigned)(q4 * 32) << 16) +
-                                       (unsigned)((c & 1) * TN + half * 64 + h * 32);
+                                       (unsigned)((c & 1) * TN + half * ECOLS + h * 32);
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
                     "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, "
@@ -300,21 +320,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const unsigned* __
     if (!good) {
         if (tid == 0) atomicOr(err, 4);
     } else if (warp >= 2) {
-        // row maxima over the tile's valid columns (this warp's 64), and E_ii on diagonal tiles
-        const int row = q4 * 32 + lane, i = i0 + row;
+        // row maxima over the tile's valid columns (this warp's 128), and E_ii where column j = i
+        // lies among them
+        const int row = q4 * 32 + lane, i = i0 + row, jw = j0 + half * ECOLS;
         float m = -INFINITY, d = 0.f;
 #pragma unroll
-        for (int q = 0; q < 64; ++q) {
-            if (j0 + half * 64 + q < I) m = fmaxf(m, sum[q]);
-            if (half * 64 + q == row) d = sum[q];
+        for (int q = 0; q < ECOLS; ++q) {
+            if (jw + q < I) m = fmaxf(m, sum[q]);
+            if (jw + q == i) d = sum[q];
         }
-        if (i0 == j0 && (row >> 6) == half && i < I) diag[i] = d;
+        if (i >= jw && i < jw + ECOLS && i < I) diag[i] = d;
         red[half * TM + row] = m;
     }
     __syncthreads();
     if (good && warp >= 2 && half == 0) {
         const int row = q4 * 32 + lane, i = i0 + row;
-        if (i < I) rmax[(size_t)blockIdx.x * ld + i] = fmaxf(red[row], red[TM + row]);
+        if (i < I) rmax[(size_t)tj * ld + i] = fmaxf(red[row], red[TM + row]);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -327,26 +348,29 @@ __global__ void __launch_bounds__(NTHREADS, 1) envy_tc_kernel(const unsigned* __
 }  // namespace
 
 int envy_tc_tiles(int I) { return (I + TM - 1) / TM; }
+int envy_tc_col_tiles(int I) { return (I + TN - 1) / TN; }
 size_t envy_tc_smem() { return SMEM_BYTES; }
 size_t envy_tc_plane_bytes(int U, int I) {
-    const size_t nt = (size_t)envy_tc_tiles(I), nk = (size_t)(U + TK - 1) / TK;
-    return 2 * nt * nk * 2 * OPER_BYTES;  // R and V, hi and lo
+    // R: one plane tile per 128 items; V: TN / TP per 256-item column tile (zero past the items)
+    const size_t nt = (size_t)envy_tc_tiles(I), ntv = (size_t)envy_tc_col_tiles(I) * (TN / TP);
+    const size_t nk = (size_t)(U + TK - 1) / TK;
+    return (nt + ntv) * nk * 2 * OPER_BYTES;  // hi and lo
 }
 
 cudaError_t launch_envy_tc(const void* r, int r_bf16, const float* V, int U, int I, int ld,
                            float* rmax, float* diag, int* err, unsigned max_polls, void* planes,
                            cudaStream_t s) {
-    const int nt = envy_tc_tiles(I), nk = (U + TK - 1) / TK;
+    const int nt = envy_tc_tiles(I), ntj = envy_tc_col_tiles(I), nk = (U + TK - 1) / TK;
     unsigned* Rp = static_cast<unsigned*>(planes);
     unsigned* Vp = Rp + (size_t)nt * nk * 2 * (OPER_BYTES / 4);
     envy_split_kernel<<<dim3(nk, nt), 1024, 0, s>>>(r, r_bf16, U, I, ld, nk, Rp);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    envy_split_kernel<<<dim3(nk, nt), 1024, 0, s>>>(V, 0, U, I, ld, nk, Vp);
+    envy_split_kernel<<<dim3(nk, ntj * (TN / TP)), 1024, 0, s>>>(V, 0, U, I, ld, nk, Vp);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = raise_smem_limit((const void*)envy_tc_kernel, envy_tc_smem())) != cudaSuccess) return e;
-    envy_tc_kernel<<<dim3(nt, nt), NTHREADS, envy_tc_smem(), s>>>(Rp, Vp, I, ld, nk, rmax, diag, err,
-                                                                 max_polls);
+    envy_tc_kernel<<<nt * ntj, NTHREADS, envy_tc_smem(), s>>>(Rp, Vp, I, ld, nk, nt, ntj, rmax,
+                                                             diag, err, max_polls);
     return cudaGetLastError();
 }
 

@@ -256,9 +256,11 @@ cudaError_t launch_solve_cond(const DevState* st, int* ctl, cudaGraphConditional
 // contraction E = R^T V with its row-max epilogue, column sums of r and the ratio tests. out[3]:
 // mean max envy, % better off, % worse off. Scratch: rmax [envy_tc_tiles(I)][ld] floats, diag [ld]
 // floats, ru [ld] doubles, ru_part [colsum_chunks()][ld] doubles.
-// The contraction runs on the tensor cores (fr_envy_tc.cu: 128-item tiles, three TF32 products;
-// an expired bounded wait sets bit 4 of *err); rmax holds envy_tc_tiles(I) rows.
-int envy_tc_tiles(int I);
+// The contraction runs on the tensor cores (fr_envy_tc.cu: 128 x 256-item tiles, three TF32
+// products; an expired bounded wait sets bit 4 of *err); rmax holds envy_tc_col_tiles(I) rows, at
+// most envy_tc_tiles(I).
+int envy_tc_tiles(int I);      // 128-item row tiles
+int envy_tc_col_tiles(int I);  // 256-item column tiles
 size_t envy_tc_smem();
 // scratch of the TF32 planes of R and V (16-byte aligned), written by launch_envy_tc
 size_t envy_tc_plane_bytes(int U, int I);
@@ -269,8 +271,8 @@ cudaError_t launch_envy_tc(const void* r, int r_bf16, const float* V, int U, int
                            cudaStream_t s);
 cudaError_t launch_envy(const void* r, int r_bf16, const float* V, int U, int I, int ld,
                         const double* imp, double esum, float* rmax, float* diag, double* ru,
-                        double* ru_part, double* out, int* err, unsigned max_polls, void* planes,
-                        cudaStream_t s);
+                        double* ru_part, double* out, double* env_item /* nullable, [I] */,
+                        int* err, unsigned max_polls, void* planes, cudaStream_t s);
 int colsum_chunks();  // FP64 partials [colsum_chunks()][ld] of the column sums of r (ru_part)
 // Frank-Wolfe certificate (fr_metrics.cu): one of a1 / a2 non-null (the policy's form); G CTAs
 // (cert_grid), per-CTA partials gap_part [G] doubles and res_part [G] floats; out[0] = gap,

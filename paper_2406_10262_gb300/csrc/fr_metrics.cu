@@ -123,7 +123,8 @@ __global__ void __launch_bounds__(1024) envy_final_kernel(const float* __restric
                                                           const float* __restrict__ diag,
                                                           const double* __restrict__ ru, int I,
                                                           int ld, const double* __restrict__ imp,
-                                                          double esum, double* __restrict__ out) {
+                                                          double esum, double* __restrict__ out,
+                                                          double* __restrict__ env_item) {
     __shared__ double s_env[32];
     __shared__ int s_cnt[2][32];
     double env = 0.0;
@@ -131,7 +132,9 @@ __global__ void __launch_bounds__(1024) envy_final_kernel(const float* __restric
     for (int i = threadIdx.x; i < I; i += blockDim.x) {
         float m = -INFINITY;
         for (int t = 0; t < ntj; ++t) m = fmaxf(m, rmax[(size_t)t * ld + i]);
-        env += (double)m - (double)diag[i];
+        const double env_i = (double)m - (double)diag[i];
+        env += env_i;
+        if (env_item) env_item[i] = env_i;
         const double unif = ru[i] * esum / I;
         if (imp[i] > 1.1 * unif) ++nb;
         if (imp[i] < 0.9 * unif) ++nw;
@@ -190,16 +193,16 @@ int colsum_chunks() { return COLSUM_CHUNKS; }
 
 cudaError_t launch_envy(const void* r, int r_bf16, const float* V, int U, int I, int ld,
                         const double* imp, double esum, float* rmax, float* diag, double* ru,
-                        double* ru_part, double* out, int* err, unsigned max_polls, void* planes,
-                        cudaStream_t s) {
-    const int nt = envy_tc_tiles(I);
+                        double* ru_part, double* out, double* env_item, int* err,
+                        unsigned max_polls, void* planes, cudaStream_t s) {
+    const int nt = envy_tc_col_tiles(I);  // rows of rmax written by the contraction
     cudaError_t e = launch_envy_tc(r, r_bf16, V, U, I, ld, rmax, diag, err, max_polls, planes, s);
     if (e != cudaSuccess) return e;
     colsum_kernel<<<dim3((I + 255) / 256, COLSUM_CHUNKS), 256, 0, s>>>(r, r_bf16, U, I, ld, ru_part);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     colsum_final_kernel<<<(I + 255) / 256, 256, 0, s>>>(ru_part, I, ld, ru);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    envy_final_kernel<<<1, 1024, 0, s>>>(rmax, nt, diag, ru, I, ld, imp, esum, out);
+    envy_final_kernel<<<1, 1024, 0, s>>>(rmax, nt, diag, ru, I, ld, imp, esum, out, env_item);
     return cudaGetLastError();
 }
 

@@ -92,8 +92,13 @@ __device__ __forceinline__ void adj_bcast(const float (&gm)[GPL], int nc, float 
     gt = NCB % 2 == 1 ? gk[NCB - 1] : 0.f;
 }
 
+// Two CTAs of 256 threads per SM (at most 128 registers) where the live set fits without spills
+// (8 rows per thread, up to 21 columns); one otherwise.
+template <int NCB, int R>
+constexpr int adj_min_blocks() { return (R <= 8 && NCB <= 21) ? 2 : 1; }
+
 template <int NCB, int R, bool EXACT>
-__global__ void __launch_bounds__(256) p2_adj_kernel(const P2Args a) {
+__global__ void __launch_bounds__(256, adj_min_blocks<NCB, R>()) p2_adj_kernel(const P2Args a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int GPL = (NCB + 31) / 32;
     constexpr int NP = NCB / 2;
@@ -282,42 +287,52 @@ __global__ void __launch_bounds__(256) p2_adj_kernel(const P2Args a) {
                         s.drt[i] = om * (v * inv);
                     }
                 } else {
+                    // gc shifted by the gauge column's value c (the dummy's, which holds most of
+                    // every row's mass): a_i - c stays small, and with d_k = eh_k (gc_k - c)
+                    //   sum_k eh_k p_k (gc_k - a_i) = sum_k p_k d_k - (a_i - c) sum_k p_k eh_k
+                    // takes three packed dot products per row instead of the centred form's five
+                    // packed operations (the identity sum_k P_ik (gc_k - a_i) = 0 holds for any c)
                     float gck[NCB];
                     bcast_g<NCB, GPL>(gcm, gck);
-                    f2 gc2[NPA];
+                    const float gcc = __shfl_sync(FULL, gcm[ref / 32], ref % 32);
+                    f2 gc2[NPA], d2[NPA];
 #pragma unroll
-                    for (int j = 0; j < NP; ++j) gc2[j] = pk(gck[2 * j], gck[2 * j + 1]);
-                    const float gct = TAIL ? gck[NCB - 1] : 0.f;
+                    for (int j = 0; j < NP; ++j) {
+                        gc2[j] = pk(gck[2 * j] - gcc, gck[2 * j + 1] - gcc);
+                        d2[j] = mul2(e2[j], gc2[j]);
+                    }
+                    const float gct = TAIL ? gck[NCB - 1] - gcc : 0.f;
+                    const float dt = et * gct;
 #pragma unroll
                     for (int r = 0; r < R; ++r) {
                         if (!vr[r]) continue;
                         f2 p2[NPA];
                         float pt;
                         const float inv = p2_row<NCB, EXACT>(sv[r], e2, et, g2, gt, s.eh, gk, nc, p2, pt);
-                        f2 ag2 = 0ull;
-#pragma unroll
-                        for (int j = 0; j < NP; ++j) ag2 = fma2(p2[j], gc2[j], ag2);
-                        float ag0, ag1;
-                        upk(ag2, ag0, ag1);
-                        const float ai = (ag0 + ag1 + (TAIL ? pt * gct : 0.f)) * inv;
-                        const f2 ai2 = pk(ai, ai);
-                        const float iai = inv * ai;
-                        const f2 iai2 = pk(iai, iai);
-                        f2 rs2 = 0ull;
+                        f2 A2 = 0ull, B2 = 0ull, C2 = 0ull;
 #pragma unroll
                         for (int j = 0; j < NP; ++j) {
-                            const f2 y = fma2(p2[j], sub2(gc2[j], ai2), 0ull);  // p_k (gc_k - a_i)
-                            rs2 = fma2(e2[j], y, rs2);
-                            acc2[j] = fma2(p2[j], iai2, acc2[j]);
+                            A2 = fma2(p2[j], gc2[j], A2);
+                            B2 = fma2(p2[j], d2[j], B2);
+                            C2 = fma2(p2[j], e2[j], C2);
                         }
-                        float rs0, rs1;
-                        upk(rs2, rs0, rs1);
-                        float rs = rs0 + rs1;
+                        float A0, A1, B0, B1, C0, C1;
+                        upk(A2, A0, A1);
+                        upk(B2, B0, B1);
+                        upk(C2, C0, C1);
+                        float A = A0 + A1, B = B0 + B1, C = C0 + C1;
                         if (TAIL) {
-                            rs = fmaf(et, pt * (gct - ai), rs);
-                            acct = fmaf(pt, iai, acct);
+                            A = fmaf(pt, gct, A);
+                            B = fmaf(pt, dt, B);
+                            C = fmaf(pt, et, C);
                         }
-                        rho[r] = fmaf(rs, inv, rho[r]);
+                        const float ai = A * inv;                 // a_i - c
+                        rho[r] = fmaf(fmaf(-ai, C, B), inv, rho[r]);
+                        const float iai = inv * (ai + gcc);       // P_ik a_i = p_ik iai
+                        const f2 iai2 = pk(iai, iai);
+#pragma unroll
+                        for (int j = 0; j < NP; ++j) acc2[j] = fma2(p2[j], iai2, acc2[j]);
+                        if (TAIL) acct = fmaf(pt, iai, acct);
                     }
                 }
                 if (l > 1) {  // gbar^(l-1); the warm start g^(0) is a constant

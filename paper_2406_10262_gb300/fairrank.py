@@ -69,6 +69,7 @@ def lib():
             "fr_set_state": (i32, [_vp, _vp, _vp, _vp, _vp, i64, i32]),
             "fr_get_state": (i32, [_vp, _vp, _vp, _vp, _vp, ct.POINTER(i64), i32]),
             "fr_metrics": (i32, [_vp, _dp, _dp, _dp, _dp]),
+            "fr_item_envy": (i32, [_vp, _dp]),
             "fr_certificate": (i32, [_vp, _dp, _dp]),
             "fr_last_error": (ct.c_char_p, [_vp]),
             "fr_launch_count": (i64, [_vp]),
@@ -281,6 +282,12 @@ class FairRank:
         vals = [ct.c_double() for _ in range(4)]
         self._check(lib().fr_metrics(self.h, *[ct.byref(v) for v in vals]))
         return dict(zip(["utility", "mean_envy", "better_pct", "worse_pct"], [v.value for v in vals]))
+
+    def item_envy(self):
+        """Per-item envy max_j (Imp_i(X_j) - Imp_i(X_i)) at the current policy, [n_items] doubles."""
+        out = np.zeros(self.I)
+        self._check(lib().fr_item_envy(self.h, out.ctypes.data_as(_dp)))
+        return out
 
     def certificate(self):
         """(gap, column residual): Frank-Wolfe bound on F* - F at the current policy."""
