@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="plain2000x1000")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the short measurements of the layered forms in the JSON line")
     ap.add_argument("--full-oracle", action="store_true",
                     help="with --compare precision: also one FP64 oracle forward over all consumers")
     ap.add_argument("--profile-steps", type=int, default=0,
@@ -406,10 +408,68 @@ def run_ours(args, w):
         info["single_thread"] = {"value": rate1, "unit": UNIT, "cores": 1,
                                  "sample": info1["sample"]}
         line["cpu_baseline"] = info
+    if rank == 0 and world == 1 and not args.no_forms:
+        g.close()  # frees the headline context's device state before the other workloads
+        line["forms"] = measure_forms()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def measure_forms():
+    """Short measurements of the layered forms, recorded beside the headline (each in its own
+    try block, so a failure is reported instead of losing the line):
+    per_item: |U| = 20000, |I| = 2000, K = 20, L = 100 -- Sinkhorn sweep, implicit gradient and
+    unrolled adjoint (checkpoints every 10) kernel times; batch: the 256-market workload, 8 ascent
+    steps batched against 256 contexts run one after another; metrics: fr_metrics (the envy
+    contraction) at 20000 consumers x 10^4 items."""
+    import torch
+    from paper_2406_10262_gb300 import fairrank as fr
+    from paper_2406_10262_gb300 import synth
+    out = {}
+    try:
+        U, I, K, L = 20000, 2000, 20, 100
+        r = synth.relevance_lowrank_fast(U, I, seed=7)
+        res = {"n_users": U, "n_items": I, "n_slots": K, "sinkhorn_iters": L, "ckpt_every": 10}
+        cu = U * I * fr.num_cols(I, K) * L
+        for name, mode in (("implicit", fr.GRAD_IMPLICIT), ("unrolled", fr.GRAD_UNROLLED)):
+            g = fr.FairRank(U, I, K, param=fr.PARAM_ITEM, sinkhorn_iters=L, grad_mode=mode,
+                            ckpt_every=10)
+            g.set_relevance(r)
+            g.set_exposure(synth.dcg_exposure(K))
+            g.step(2, trace=False)
+            ms = g.time_kernels(3)
+            res[name] = {"sweep_ms": ms[0], "grad_ms": ms[2]}
+            g.close()
+        res["sweep_cell_updates_per_s"] = cu / (res["implicit"]["sweep_ms"] * 1e-3)
+        res["adjoint_over_sweep"] = res["unrolled"]["grad_ms"] / res["unrolled"]["sweep_ms"]
+        out["per_item"] = res
+    except Exception as ex:  # noqa: BLE001 -- reported in the line
+        out["per_item"] = {"error": repr(ex)}
+    try:
+        c = compare_batch(argparse.Namespace(steps=1))
+        out["batch"] = {k: c[k] for k in ("markets", "ascent_steps", "sinkhorn_iters", "cells",
+                                          "batched_s", "sequential_s", "speedup",
+                                          "batched_cell_updates_per_s", "max_rel_F_diff_final",
+                                          "launches_per_run")}
+    except Exception as ex:  # noqa: BLE001
+        out["batch"] = {"error": repr(ex)}
+    try:
+        U, I, K = 20000, 10000, 20
+        g = fr.FairRank(U, I, K, param=fr.PARAM_ITEM, sinkhorn_iters=20)
+        g.set_relevance(synth.relevance_lowrank_fast(U, I, seed=3))
+        g.set_exposure(synth.dcg_exposure(K))
+        g.step(1, trace=False)
+        g.metrics()
+        ts = [_timed(g.metrics)[1] * 1e3 for _ in range(3)]
+        out["metrics"] = {"n_users": U, "n_items": I, "n_slots": K, "fr_metrics_ms": statistics.median(ts),
+                          "envy_tf32_products": 3 * U * I * I}
+        g.close()
+    except Exception as ex:  # noqa: BLE001
+        out["metrics"] = {"error": repr(ex)}
+    torch.cuda.synchronize()
+    return out
 
 
 # ---- layered forms against the plain FP32 method ---------------------------------------------

@@ -291,6 +291,14 @@ FR_API fr_status fr_measure_ex2_rate(double* ex2_per_second);
    measured denominators of the rooflines the benchmark reports. 1 <= n <= 6, else FR_EINVAL. */
 FR_API fr_status fr_measure_peaks(double* out, int32_t n);
 
+/* Self-check of the logarithm in the Sinkhorn column updates: log2_near1(y) evaluates log2 for
+   |y - 1| < 2^-5 as the Taylor series of ln(1 + t) / ln 2 (t = y - 1, coefficients +-1/(n ln 2)
+   through t^6) and calls log2f elsewhere. Evaluates it on the device for every float y in that
+   range and writes out[0] its largest relative error against log2 in double precision, out[1] the
+   same for log2f(y), out[2] the number of values at y = 1 that were not exactly 0. FR_EINVAL if
+   out is NULL. */
+FR_API fr_status fr_check_log2_near1(double* out);
+
 /* ---- allocation-free evaluation --------------------------------------------------------- */
 
 /* For callers that cannot allocate device memory. The paper has no counterpart to this entry

@@ -1176,6 +1176,28 @@ fr_status fr_sweep_stats(fr_ctx* ctx, int64_t* log_form_solves) {
     return FR_OK;
 }
 
+fr_status fr_check_log2_near1(double* out) {
+    fr_ctx* ctx = nullptr;
+    if (!out) return fail(nullptr, FR_EINVAL, "output is NULL");
+    int dev = 0, sms = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    unsigned* d = nullptr;
+    CU(cudaMalloc(&d, sizeof(unsigned) * 3));
+    unsigned h[3] = {0u, 0u, 0u};
+    cudaError_t e = cudaMemset(d, 0, sizeof h);
+    if (e == cudaSuccess) e = launch_log2_check(d, sms * 4, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof h, cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    CU(e);
+    float f[2];
+    std::memcpy(f, h, sizeof f);
+    out[0] = f[0];
+    out[1] = f[1];
+    out[2] = (double)h[2];
+    return FR_OK;
+}
+
 fr_status fr_measure_ex2_rate(double* ex2_per_second) {
     fr_ctx* ctx = nullptr;
     if (!ex2_per_second) return fail(nullptr, FR_EINVAL, "output is NULL");

@@ -1,6 +1,8 @@
 // fr_common.cu -- the cross-consumer impact reduction and the support kernels of libfairrank.
 #include <cuda_bf16.h>
 
+#include <cstring>
+
 #include <mutex>
 
 #include "fr_device.cuh"
@@ -421,6 +423,42 @@ cudaError_t launch_solve_cond(const DevState* st, int* ctl, cudaGraphConditional
 
 cudaError_t launch_ex2_bench(float* sink, int blocks, int threads, int iters, cudaStream_t s) {
     ex2_bench_kernel<<<blocks, threads, 0, s>>>(sink, iters);
+    return cudaGetLastError();
+}
+
+// ---- self-check of the column update's log2 (fr_check_log2_near1) -------------------------------
+// Every float y with |y - 1| < 2^-5 (the range of the short path), as consecutive bit patterns from
+// start: the relative error of log2_near1(y) and of log2f(y) against log2 in double precision,
+// maxima kept as the bit patterns of non-negative floats (which order like the floats); y = 1 must
+// give exactly 0 (counted in bad).
+__global__ void log2_check_kernel(unsigned start, unsigned count, unsigned* out) {
+    unsigned m_near = 0u, m_lib = 0u, bad = 0u;
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+        const float y = __uint_as_float(start + k);
+        const float a = log2_near1(y), b = log2f(y);
+        const double ex = log2((double)y);
+        if (ex == 0.0) {
+            bad += a != 0.f;
+            continue;
+        }
+        m_near = max(m_near, __float_as_uint((float)fabs(((double)a - ex) / ex)));
+        m_lib = max(m_lib, __float_as_uint((float)fabs(((double)b - ex) / ex)));
+    }
+    atomicMax(out, m_near);
+    atomicMax(out + 1, m_lib);
+    if (bad) atomicAdd(out + 2, bad);
+}
+
+static unsigned host_bits(float x) {
+    unsigned u;
+    std::memcpy(&u, &x, sizeof u);
+    return u;
+}
+
+cudaError_t launch_log2_check(unsigned* out, int blocks, cudaStream_t s) {
+    const unsigned lo = host_bits(1.f - 0x1p-5f) + 1u;  // first float above 1 - 2^-5
+    const unsigned hi = host_bits(1.f + 0x1p-5f) - 1u;  // last float below 1 + 2^-5
+    log2_check_kernel<<<blocks, 256, 0, s>>>(lo, hi - lo + 1u, out);
     return cudaGetLastError();
 }
 

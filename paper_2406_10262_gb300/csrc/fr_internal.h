@@ -245,6 +245,9 @@ cudaError_t launch_policy(const P1Args& a, int u0, int n_u, float* x_out, cudaSt
 cudaError_t launch_ex2_bench(float* sink, int blocks, int threads, int iters, cudaStream_t s);
 // kind 0 / 1: shared-memory loads of 8 / 16 bytes; 2 / 3: scalar / packed FP32 FMA. clk[0..1]: SM
 // cycles and nanoseconds of block 0's loop.
+// self-check of log2_near1 over every float of its short path (fr_common.cu): out[3] unsigned,
+// zeroed by the caller: max relative errors of log2_near1 and log2f as float bits, misses at y = 1
+cudaError_t launch_log2_check(unsigned* out, int blocks, cudaStream_t s);
 cudaError_t launch_peak_bench(int kind, float* sink, int blocks, int threads, int iters,
                               unsigned long long* clk, cudaStream_t s);
 // Body end of fr_solve's device-side while loop: ctl[0] counts body iterations, ctl[1] caps them;

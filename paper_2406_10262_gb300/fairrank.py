@@ -79,6 +79,7 @@ def lib():
             "fr_sweep_stats": (i32, [_vp, ct.POINTER(i64)]),
             "fr_set_wait_limit": (i32, [_vp, i32]),
             "fr_measure_peaks": (i32, [_dp, i32]),
+            "fr_check_log2_near1": (i32, [_dp]),
             "fr_batch_create": (i32, [ct.POINTER(Config), i32, _vp, ct.POINTER(_vp)]),
             "fr_batch_destroy": (i32, [_vp]),
             "fr_batch_reset": (i32, [_vp]),
@@ -150,6 +151,16 @@ def measure_peaks() -> dict:
     keys = ["ex2_per_s", "smem_bytes_per_s_8B", "smem_bytes_per_s_16B", "ffma_per_s",
             "ffma2_fmas_per_s", "sm_mhz"]
     return dict(zip(keys, list(out)))
+
+
+def check_log2_near1() -> dict:
+    """Self-check of the column updates' log2 near 1 over every float of its short path
+    (fr_check_log2_near1)."""
+    out = (ct.c_double * 3)()
+    st = lib().fr_check_log2_near1(out)
+    if st:
+        raise FairRankError(st, lib().fr_last_error(None).decode())
+    return {"max_rel_err": out[0], "log2f_max_rel_err": out[1], "nonzero_at_one": int(out[2])}
 
 
 class FairRank:
