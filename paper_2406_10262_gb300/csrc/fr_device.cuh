@@ -326,7 +326,10 @@ __device__ inline void warp_cholesky_solve(double* A, double* rhs, int n, int la
 // transposed copy of L in shared memory (Lt, n*n floats). Pivots below `floor` are raised to it.
 // Each pivot costs one reciprocal square root (rsqrt.approx) and the divisions by L_jj become
 // multiplications by it: the n pivots form a sequential chain, and IEEE square root and division
-// are long software sequences. Writes beta[0..n).
+// are long software sequences. The pivot and substitution loops stay rolled (the pivot's row entry
+// picked from the registers by a select chain): the solve runs once per consumer between long
+// sweeps, and its fully unrolled straight-line form cost 2 % more of the fused step for the same
+// arithmetic. Writes beta[0..n).
 template <int NM>
 __device__ inline void warp_cholesky_solve_f32(const float* A, const float* rhs, int n, float* Lt,
                                                float* beta, int lane) {
@@ -334,32 +337,35 @@ __device__ inline void warp_cholesky_solve_f32(const float* A, const float* rhs,
 #pragma unroll
     for (int k = 0; k < NM; ++k) row[k] = (lane < n && k < n) ? A[lane * n + k] : 0.f;
     float dmax = 0.f;
-#pragma unroll
-    for (int j = 0; j < NM; ++j)
-        if (j < n) dmax = fmaxf(dmax, __shfl_sync(FULL, row[j], j));
+#pragma unroll 1
+    for (int j = 0; j < n; ++j) dmax = fmaxf(dmax, A[j * n + j]);
     const float floor_ = 1e-12f * fmaxf(dmax, 1e-30f);
     float rinv = 0.f;  // lane j: 1 / L_jj
+#pragma unroll 1
+    for (int j = 0; j < n; ++j) {
+        float rj = row[0];  // row[j]
 #pragma unroll
-    for (int j = 0; j < NM; ++j) {
-        if (j >= n) break;
-        const float d = fmaxf(__shfl_sync(FULL, row[j], j), floor_);
+        for (int k = 1; k < NM; ++k) rj = k == j ? row[k] : rj;
+        const float d = fmaxf(__shfl_sync(FULL, rj, j), floor_);
         const float ri = rsqrtf(d);
-        const float lij = lane > j ? row[j] * ri : (lane == j ? d * ri : 0.f);
+        const float lij = lane > j ? rj * ri : (lane == j ? d * ri : 0.f);
         if (lane == j) rinv = ri;
-        row[j] = lij;
 #pragma unroll
-        for (int k = j + 1; k < NM; ++k) {
+        for (int k = 0; k < NM; ++k) {
+            if (k == j) row[k] = lij;
             const float lkj = __shfl_sync(FULL, lij, k);
-            if (lane > j) row[k] = fmaf(-lij, lkj, row[k]);
+            if (k > j && lane > j) row[k] = fmaf(-lij, lkj, row[k]);
         }
     }
     float y = lane < n ? rhs[lane] : 0.f;  // L y = rhs: lane i holds y_i
+#pragma unroll 1
+    for (int j = 0; j < n; ++j) {
+        float lj = row[0];  // L[lane][j]
 #pragma unroll
-    for (int j = 0; j < NM; ++j) {
-        if (j >= n) break;
+        for (int k = 1; k < NM; ++k) lj = k == j ? row[k] : lj;
         const float yj = __shfl_sync(FULL, y * rinv, j);
         if (lane == j) y = yj;
-        if (lane > j) y = fmaf(-row[j], yj, y);
+        if (lane > j) y = fmaf(-lj, yj, y);
     }
     if (lane < n) {  // Lt[k][i] = L[i][k]
 #pragma unroll

@@ -106,8 +106,8 @@ def test_batch_bf16_matches_single_bf16():
 
 def test_batching_workload_size_sample():
     """24 markets drawn from the batching workload's size distribution, 2 steps, every market
-    against its single-market context; the two smallest and the median one also against the
-    oracle."""
+    against its single-market context; the two smallest, the median and the largest one also
+    against the oracle."""
     ms = synth.markets(24, seed=3)
     sizes = [(m.n_users, m.n_items, m.n_slots) for m in ms]
     rs = [synth.relevance_lowrank_fast(m.n_users, m.n_items, seed=m.seed) for m in ms]
@@ -116,7 +116,8 @@ def test_batching_workload_size_sample():
     for j, ((U, I, K), r) in enumerate(zip(sizes, rs)):
         np.testing.assert_allclose(F[:, j], single(U, I, K, r).step(2), rtol=PAIR_RTOL)
     order = np.argsort([U * I for U, I, K in sizes])
-    for j in list(order[:2]) + [order[len(order) // 2]]:  # the two smallest and the median market
+    # the two smallest, the median and the largest market
+    for j in list(order[:2]) + [order[len(order) // 2], order[-1]]:
         U, I, K = sizes[j]
         o = oracle.Oracle(U, I, K, param=oracle.PARAM_ITEM, iters=50)
         o.set_relevance(rs[j].astype(np.float64))
