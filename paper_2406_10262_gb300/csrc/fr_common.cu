@@ -14,57 +14,75 @@ namespace {
 
 constexpr int RED_ITEMS = 32;  // items per CTA (one per lane)
 constexpr int RED_WARPS = 32;  // warps splitting the per-CTA partials
+constexpr int RED_BATCH = 20;  // partial-row loads in flight per lane
 
 // Eq. (4) across consumers and Eq. (5): Imp_i = sum over the sweep CTAs' partials (fixed order,
-// FP64), omega_i = 1/Imp_i for the next gradient, F = sum_i log Imp_i in FP64. The last CTA to
+// compensated FP32 arithmetic carrying FP64-level precision, delivered as a double),
+// omega_i = 1/Imp_i for the next gradient, F = sum_i log Imp_i in FP64. The last CTA to
 // finish (atomic ticket) combines the per-CTA partial sums of log Imp_i, of Imp_i (utility,
 // Sec. 4.1) and of the squared gradient norm in a fixed order, updates the step state and, for
 // fr_solve, raises the stop flag once the step's gradient norm is <= the threshold.
 // bid / nb: this CTA's index among the nb CTAs that reduce one problem.
 __device__ __forceinline__ void reduce_body(const ReduceArgs& a, int bid, int nb) {
-    __shared__ double s_sum[RED_WARPS][RED_ITEMS];
+    __shared__ float2 s_sum[RED_WARPS][RED_ITEMS];  // per warp and item: compensated sum (s, c)
     __shared__ int s_last;
     if (a.st->stop) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int item = bid * RED_ITEMS + lane;
-    // partials g = warp, warp + RED_WARPS, ... in two interleaved compensated FP32 sums (Knuth's
-    // TwoSum: the rounding error of every addition is carried exactly in c), so each warp's total
-    // s + c is accurate to double-level precision without FP64 arithmetic per partial (the FP64
-    // pipe is a small fraction of the FP32 one on this part); the fixed order keeps it
+    // Knuth's TwoSum: t = s + x and the rounding error of that addition, carried exactly in c
+    auto two_sum = [](float& s, float& c, float x) {
+        const float t = __fadd_rn(s, x);
+        const float bp = __fsub_rn(t, s);
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
+        s = t;
+    };
+    // partials g = warp, warp + RED_WARPS, ... in two interleaved compensated FP32 sums, so each
+    // warp's total s + c is accurate to double-level precision without FP64 arithmetic per partial
+    // (the FP64 pipe is a small fraction of the FP32 one on this part); the fixed order keeps it
     // deterministic
     float sa[2] = {0.f, 0.f}, ca[2] = {0.f, 0.f};
     if (item < a.I) {
         const float* p = a.part + item;
         const size_t step = (size_t)RED_WARPS * a.ld;
         int g = warp;
-        auto two_sum = [](float& s, float& c, float x) {
-            const float t = __fadd_rn(s, x);
-            const float bp = __fsub_rn(t, s);
-            c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(x, bp)));
-            s = t;
-        };
-        for (; g + 15 * RED_WARPS < a.G; g += 16 * RED_WARPS) {  // sixteen loads in flight
+        // RED_BATCH loads in flight per lane: up to 640 partial rows (a grid of 4 CTAs per SM) take
+        // one round trip to L2; RED_BATCH is even, so every row keeps its accumulator (j & 1)
+        for (; g + (RED_BATCH - 1) * RED_WARPS < a.G; g += RED_BATCH * RED_WARPS) {
             const float* q = p + (size_t)g * a.ld;
-            float x[16];
+            float x[RED_BATCH];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) x[j] = __ldcg(q + j * step);
+            for (int j = 0; j < RED_BATCH; ++j) x[j] = __ldcg(q + j * step);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) two_sum(sa[j & 1], ca[j & 1], x[j]);
+            for (int j = 0; j < RED_BATCH; ++j) two_sum(sa[j & 1], ca[j & 1], x[j]);
         }
-        {  // the remaining fewer than sixteen, all loads first (zeros add exactly)
-            float x[16];
+        {  // the remaining fewer than RED_BATCH, all loads first (zeros add exactly)
+            float x[RED_BATCH];
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
+            for (int j = 0; j < RED_BATCH; ++j)
                 x[j] = g + j * RED_WARPS < a.G ? __ldcg(p + (size_t)(g + j * RED_WARPS) * a.ld) : 0.f;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) two_sum(sa[j & 1], ca[j & 1], x[j]);
+            for (int j = 0; j < RED_BATCH; ++j) two_sum(sa[j & 1], ca[j & 1], x[j]);
         }
     }
-    s_sum[warp][lane] = ((double)sa[0] + (double)ca[0]) + ((double)sa[1] + (double)ca[1]);
-    __syncthreads();
+    // the two accumulators and then the warps combined as double-float pairs (s, c): s absorbs the
+    // other's s by TwoSum, the rounding error and both c's go to c; warps pairwise in a fixed tree
+    two_sum(sa[0], ca[0], sa[1]);
+    ca[0] = __fadd_rn(ca[0], ca[1]);
+    s_sum[warp][lane] = make_float2(sa[0], ca[0]);
+#pragma unroll
+    for (int h = RED_WARPS / 2; h > 0; h >>= 1) {
+        __syncthreads();
+        if (warp < h) {
+            const float2 o = s_sum[warp + h][lane];
+            float ss = s_sum[warp][lane].x, cc = s_sum[warp][lane].y;
+            two_sum(ss, cc, o.x);
+            cc = __fadd_rn(cc, o.y);
+            s_sum[warp][lane] = make_float2(ss, cc);
+        }
+    }
     if (warp == 0) {
-        double tot = 0.0;
-        for (int w = 0; w < RED_WARPS; ++w) tot += s_sum[w][lane];
+        const float2 t2 = s_sum[0][lane];
+        const double tot = (double)t2.x + (double)t2.y;
         double lg = 0.0, im = 0.0;
         if (item < a.I) {
             a.imp[item] = tot;
@@ -94,8 +112,19 @@ __device__ __forceinline__ void reduce_body(const ReduceArgs& a, int bid, int nb
         F += __ldcg(a.blk + 2 * b);
         S += __ldcg(a.blk + 2 * b + 1);
     }
-    if (a.after_update)
-        for (int g = lane; g < a.Ggn; g += 32) g2 += __ldcg(a.gn2_part + g);
+    if (a.after_update) {  // partials lane, lane + 32, ... in that order, RED_BATCH loads in flight
+        for (int g0 = 0; g0 < a.Ggn; g0 += 32 * RED_BATCH) {
+            double y[RED_BATCH];
+#pragma unroll
+            for (int j = 0; j < RED_BATCH; ++j) {
+                const int g = g0 + lane + 32 * j;
+                y[j] = g < a.Ggn ? __ldcg(a.gn2_part + g) : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < RED_BATCH; ++j)
+                if (g0 + lane + 32 * j < a.Ggn) g2 += y[j];
+        }
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         F += __shfl_xor_sync(FULL, F, o);
