@@ -326,13 +326,16 @@ __device__ inline void warp_cholesky_solve(double* A, double* rhs, int n, int la
 // transposed copy of L in shared memory (Lt, n*n floats). Pivots below `floor` are raised to it.
 // Each pivot costs one reciprocal square root (rsqrt.approx) and the divisions by L_jj become
 // multiplications by it: the n pivots form a sequential chain, and IEEE square root and division
-// are long software sequences. The pivot and substitution loops stay rolled (the pivot's row entry
-// picked from the registers by a select chain): the solve runs once per consumer between long
-// sweeps, and its fully unrolled straight-line form cost 2 % more of the fused step for the same
-// arithmetic. Writes beta[0..n).
+// are long software sequences. Two forms with the same arithmetic (bit-identical results): up to 12
+// unknowns the pivot and substitution loops stay rolled (the pivot's row entry picked from the
+// registers by a select chain) -- the solve runs once per consumer between long sweeps, and the
+// fully unrolled straight-line form cost 2 % more of the fused 11-column step; for wider systems
+// the select chains and full-width shuffles of the rolled form grow with n, and the unrolled form
+// (shuffles only for the trailing columns) is 3 % faster in the 21-column per-item gradient.
+// Writes beta[0..n).
 template <int NM>
-__device__ inline void warp_cholesky_solve_f32(const float* A, const float* rhs, int n, float* Lt,
-                                               float* beta, int lane) {
+__device__ inline void warp_cholesky_solve_f32_rolled(const float* A, const float* rhs, int n,
+                                                      float* Lt, float* beta, int lane) {
     float row[NM];
 #pragma unroll
     for (int k = 0; k < NM; ++k) row[k] = (lane < n && k < n) ? A[lane * n + k] : 0.f;
@@ -380,6 +383,64 @@ __device__ inline void warp_cholesky_solve_f32(const float* A, const float* rhs,
         if (lane < j) z = fmaf(-Lt[lane * n + j], zj, z);  // (L^T)[i][j] = L[j][i]
     }
     if (lane < n) beta[lane] = z;
+}
+
+template <int NM>
+__device__ inline void warp_cholesky_solve_f32_unrolled(const float* A, const float* rhs, int n,
+                                                        float* Lt, float* beta, int lane) {
+    float row[NM];
+#pragma unroll
+    for (int k = 0; k < NM; ++k) row[k] = (lane < n && k < n) ? A[lane * n + k] : 0.f;
+    float dmax = 0.f;
+#pragma unroll
+    for (int j = 0; j < NM; ++j)
+        if (j < n) dmax = fmaxf(dmax, __shfl_sync(FULL, row[j], j));
+    const float floor_ = 1e-12f * fmaxf(dmax, 1e-30f);
+    float rinv = 0.f;  // lane j: 1 / L_jj
+#pragma unroll
+    for (int j = 0; j < NM; ++j) {
+        if (j >= n) break;
+        const float d = fmaxf(__shfl_sync(FULL, row[j], j), floor_);
+        const float ri = rsqrtf(d);
+        const float lij = lane > j ? row[j] * ri : (lane == j ? d * ri : 0.f);
+        if (lane == j) rinv = ri;
+        row[j] = lij;
+#pragma unroll
+        for (int k = j + 1; k < NM; ++k) {
+            const float lkj = __shfl_sync(FULL, lij, k);
+            if (lane > j) row[k] = fmaf(-lij, lkj, row[k]);
+        }
+    }
+    float y = lane < n ? rhs[lane] : 0.f;  // L y = rhs: lane i holds y_i
+#pragma unroll
+    for (int j = 0; j < NM; ++j) {
+        if (j >= n) break;
+        const float yj = __shfl_sync(FULL, y * rinv, j);
+        if (lane == j) y = yj;
+        if (lane > j) y = fmaf(-row[j], yj, y);
+    }
+    if (lane < n) {  // Lt[k][i] = L[i][k]
+#pragma unroll
+        for (int k = 0; k < NM; ++k)
+            if (k < n) Lt[k * n + lane] = row[k];
+    }
+    __syncwarp();
+    float z = y;  // L^T z = y
+    for (int j = n - 1; j >= 0; --j) {
+        const float zj = __shfl_sync(FULL, z * rinv, j);
+        if (lane == j) z = zj;
+        if (lane < j) z = fmaf(-Lt[lane * n + j], zj, z);  // (L^T)[i][j] = L[j][i]
+    }
+    if (lane < n) beta[lane] = z;
+}
+
+template <int NM>
+__device__ inline void warp_cholesky_solve_f32(const float* A, const float* rhs, int n, float* Lt,
+                                               float* beta, int lane) {
+    if constexpr (NM <= 12)
+        warp_cholesky_solve_f32_rolled<NM>(A, rhs, n, Lt, beta, lane);
+    else
+        warp_cholesky_solve_f32_unrolled<NM>(A, rhs, n, Lt, beta, lane);
 }
 
 // Broadcast of the column potentials held by lane k % 32 (slot k / 32) to every lane.
