@@ -130,6 +130,25 @@ def _ptr(x, dtype=None):
     raise TypeError(f"unsupported buffer type {type(x)}")
 
 
+def _rows(x):
+    """(pointer, on_device, keepalive, ld) of a 2-D row-major numpy array or torch tensor whose
+    rows may be padded (unit stride within a row, ld >= n_cols elements between rows): views such
+    as wide[:, :n] pass without a copy; other layouts are copied to a dense array first."""
+    if isinstance(x, np.ndarray):
+        if (x.ndim == 2 and x.strides[1] == x.itemsize and x.strides[0] % x.itemsize == 0
+                and x.strides[0] >= x.shape[1] * x.itemsize):
+            return ct.c_void_p(x.ctypes.data), 0, x, x.strides[0] // x.itemsize
+        c = np.ascontiguousarray(x)
+        return ct.c_void_p(c.ctypes.data), 0, c, c.shape[1]
+    import torch
+    if isinstance(x, torch.Tensor):
+        if x.dim() == 2 and x.stride(1) == 1 and x.stride(0) >= x.shape[1]:
+            return ct.c_void_p(x.data_ptr()), int(x.is_cuda), x, x.stride(0)
+        c = x.contiguous()
+        return ct.c_void_p(c.data_ptr()), int(c.is_cuda), c, c.shape[1]
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
 def num_cols(n_items: int, n_slots: int) -> int:
     return lib().fr_num_cols(n_items, n_slots)
 
@@ -205,7 +224,8 @@ class FairRank:
 
     # ---- inputs ---------------------------------------------------------------------------
     def set_relevance(self, r, dtype=None):
-        """r: (U, I) numpy float32/float64, uint16 bfloat16 bits, or a torch tensor."""
+        """r: (U, I) numpy float32/float64, uint16 bfloat16 bits, or a torch tensor (host or CUDA);
+        rows may be padded (a view of a wider array), which passes as the C ABI's ld."""
         import_dtype = dtype
         if import_dtype is None:
             kind = str(getattr(r, "dtype", ""))
@@ -213,8 +233,7 @@ class FairRank:
                             "uint16": BF16, "torch.bfloat16": BF16}.get(kind)
             if import_dtype is None:
                 raise TypeError(f"unsupported relevance dtype {kind}")
-        p, dev, keep = _ptr(r)
-        ld = r.shape[1]
+        p, dev, keep, ld = _rows(r)
         self._check(lib().fr_set_relevance(self.h, p, import_dtype, ld, dev))
 
     def set_exposure(self, e):
@@ -373,8 +392,8 @@ class FairRankBatch:
               "torch.float64": F64, "torch.bfloat16": BF16}.get(kind)
         if dt is None:
             raise TypeError(f"unsupported relevance dtype {kind}")
-        p, dev, keep = _ptr(r)
-        self._check(lib().fr_batch_set_relevance(self.h, market, p, dt, r.shape[1], dev))
+        p, dev, keep, ld = _rows(r)
+        self._check(lib().fr_batch_set_relevance(self.h, market, p, dt, ld, dev))
 
     def set_exposure(self, market, e):
         e = np.ascontiguousarray(e, dtype=np.float64)
