@@ -222,21 +222,30 @@ __global__ void relevance_import_kernel(const void* __restrict__ src, int dtype,
     }
 }
 
-// flags[0] |= 1 for a negative or non-finite value; flags[1] counts items without positive r
-__global__ void relevance_check_kernel(const void* __restrict__ r, int r_bf16, int U, int I,
-                                       int ld, int* flags) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= I) return;
+// flags[0] |= 1 for a negative or non-finite value; flags[1] counts items without positive r.
+// Block b checks items 32 b .. 32 b + 31 (one per lane, 128-byte row segments); its warps split the
+// consumers, and a shared flag per item collects whether any consumer's relevance is positive.
+__global__ void __launch_bounds__(1024) relevance_check_kernel(const void* __restrict__ r, int r_bf16,
+                                                               int U, int I, int ld, int* flags) {
+    __shared__ int s_pos[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    if (threadIdx.x < 32) s_pos[threadIdx.x] = 0;
+    __syncthreads();
     bool bad = false, pos = false;
-    for (int u = 0; u < U; ++u) {
-        const size_t o = (size_t)u * ld + i;
-        const float v = r_bf16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(r)[o])
-                               : static_cast<const float*>(r)[o];
-        bad |= !(v >= 0.f) || !isfinite(v);
-        pos |= v > 0.f;
+    if (i < I) {
+        for (int u = warp; u < U; u += W) {
+            const size_t o = (size_t)u * ld + i;
+            const float v = r_bf16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(r)[o])
+                                   : static_cast<const float*>(r)[o];
+            bad |= !(v >= 0.f) || !isfinite(v);
+            pos |= v > 0.f;
+        }
     }
-    if (bad) atomicOr(flags, 1);
-    if (!pos) atomicAdd(flags + 1, 1);
+    if (pos) atomicOr(&s_pos[lane], 1);
+    if (__any_sync(FULL, bad) && lane == 0) atomicOr(flags, 1);
+    __syncthreads();
+    if (warp == 0 && i < I && !s_pos[lane]) atomicAdd(flags + 1, 1);
 }
 
 // Policy of consumers u0.. (one CTA each): x_ik = softmax_k(g^(L-1)'_k - c'_ik) in base 2, the
@@ -434,7 +443,7 @@ cudaError_t launch_relevance_import(const void* src, int dtype, long long ld_src
 
 cudaError_t launch_relevance_check(const void* r, int r_bf16, int U, int I, int ld, int* flags,
                                    cudaStream_t s) {
-    relevance_check_kernel<<<(I + 127) / 128, 128, 0, s>>>(r, r_bf16, U, I, ld, flags);
+    relevance_check_kernel<<<(I + 31) / 32, 1024, 0, s>>>(r, r_bf16, U, I, ld, flags);
     return cudaGetLastError();
 }
 
