@@ -49,7 +49,7 @@ def build(force: bool = False, extra: list[str] | None = None, verbose: bool = F
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
     extra = list(extra or [])
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), _sources()))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
