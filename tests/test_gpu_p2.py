@@ -150,3 +150,41 @@ def test_two_live_contexts_sharing_a_kernel():
     b.step(1)
     Fa = a.step(2)
     np.testing.assert_allclose(Fa, oa.step(2)[0], rtol=NSW_RTOL)
+
+
+def test_precision_workload_full_size_sampled_parity():
+    """The precision workload at its full size: |U| = 200000, |I| = 10^4, K = 20, L = 50, BF16
+    relevance (rank-32 sigmoid, 5% boosted items), two ascent steps from theta = 0 in the launch
+    configuration the benchmark's comparison uses. The oracle then solves a seeded sample of 64
+    consumers at the GPU's final theta from the GPU's warm start of the last solve, on the same
+    BF16-rounded relevance: the sampled policies (max-abs 1e-5), the sample's impacts formed from
+    the GPU policies (1e-5 relative) and the sample's NSW (1e-6 relative)."""
+    U, I, K, L, blk, n_sample = 200000, 10000, 20, 50, 20000, 64
+    rb = np.empty((U, I), dtype=np.uint16)
+    for u0 in range(0, U, blk):
+        rb[u0:u0 + blk] = synth.to_bf16_bits(
+            synth.relevance_lowrank_fast(U, I, seed=0, boost_frac=0.05, row0=u0, rows=blk))
+    e = synth.dcg_exposure(K)
+    g = fr.FairRank(U, I, K, param=fr.PARAM_ITEM, sinkhorn_iters=L, rel_dtype=fr.BF16)
+    g.set_relevance(rb)
+    g.set_exposure(e)
+    g.step(1, trace=False)
+    _, _, _, g0, _ = g.get_state()  # warm start of the last solve
+    F = g.step(1)
+    theta = g.get_state()[0]
+    assert np.isfinite(F).all()
+    sample = np.sort(np.random.default_rng(7).choice(U, n_sample, replace=False))
+    X = np.stack([g.policy(int(u), 1)[0] for u in sample]).astype(np.float64)
+    g.close()
+    r_s = synth.bf16_bits_to_f64(rb[sample])
+    del rb
+    o = oracle.Oracle(n_sample, I, K, param=oracle.PARAM_ITEM, iters=L, warm_start=True)
+    o.set_relevance(r_s)
+    o.set_exposure(e)
+    o.set_state(param=theta.astype(np.float64), g=g0[sample].astype(np.float64))
+    imp_o, _, F_o = o.impacts()
+    assert np.max(np.abs(X - o.policy())) <= X_ATOL
+    e_pad = np.r_[e, np.zeros(fr.num_cols(I, K) - K)]
+    imp_g = (r_s * (X @ e_pad)).sum(axis=0)
+    assert np.max(np.abs(imp_g - imp_o) / imp_o) <= 1e-5
+    assert rel(float(np.sum(np.log(imp_g))), F_o) <= NSW_RTOL
