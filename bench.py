@@ -421,9 +421,9 @@ def measure_forms():
     """Short measurements of the layered forms, recorded beside the headline (each in its own
     try block, so a failure is reported instead of losing the line):
     per_item: |U| = 20000, |I| = 2000, K = 20, L = 100 -- Sinkhorn sweep, implicit gradient and
-    unrolled adjoint (checkpoints every 10) kernel times; batch: the 256-market workload, 8 ascent
-    steps batched against 256 contexts run one after another; metrics: fr_metrics (the envy
-    contraction) at 20000 consumers x 10^4 items."""
+    unrolled adjoint (checkpoints every 10, and every iteration) kernel times; batch: the
+    256-market workload, 8 ascent steps batched against 256 contexts run one after another;
+    metrics: fr_metrics (the envy contraction) at 20000 consumers x 10^4 items."""
     import torch
     from paper_2406_10262_gb300 import fairrank as fr
     from paper_2406_10262_gb300 import synth
@@ -442,8 +442,19 @@ def measure_forms():
             ms = g.time_kernels(3)
             res[name] = {"sweep_ms": ms[0], "grad_ms": ms[2]}
             g.close()
+        # a checkpoint every iteration: the sweep also keeps the column sums, no forward re-runs
+        g = fr.FairRank(U, I, K, param=fr.PARAM_ITEM, sinkhorn_iters=L, grad_mode=fr.GRAD_UNROLLED,
+                        ckpt_every=1)
+        g.set_relevance(r)
+        g.set_exposure(synth.dcg_exposure(K))
+        g.step(2, trace=False)
+        ms = g.time_kernels(3)
+        res["unrolled_ckpt_every_1"] = {"sweep_ms": ms[0], "grad_ms": ms[2]}
+        g.close()
         res["sweep_cell_updates_per_s"] = cu / (res["implicit"]["sweep_ms"] * 1e-3)
         res["adjoint_over_sweep"] = res["unrolled"]["grad_ms"] / res["unrolled"]["sweep_ms"]
+        res["adjoint_over_sweep_ckpt_every_1"] = (res["unrolled_ckpt_every_1"]["grad_ms"] /
+                                                  res["unrolled_ckpt_every_1"]["sweep_ms"])
         out["per_item"] = res
     except Exception as ex:  # noqa: BLE001 -- reported in the line
         out["per_item"] = {"error": repr(ex)}

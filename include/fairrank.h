@@ -71,7 +71,9 @@ typedef struct fr_config {
                                n_items <= 1024 (n_cols <= 16) or 512, else FR_EUNSUPPORTED */
     int32_t ckpt_every;     /* FR_GRAD_UNROLLED: every ckpt_every-th iterate of the column
                                potentials is stored per consumer (ceil(L / ckpt_every) n_cols
-                               floats); the rest are recomputed. >= 1 */
+                               floats); the rest are recomputed. With 1 and FR_PARAM_ITEM each
+                               iteration's column sums are kept too (L n_cols more floats per
+                               consumer) and the adjoint does no forward re-runs. >= 1 */
     int32_t optimizer;      /* FR_ADAM (PyTorch Adam, maximize) | FR_SGD */
     double  lr, beta1, beta2, adam_eps;
     int32_t rel_dtype;      /* storage of r on the device: FR_F32 | FR_BF16 */

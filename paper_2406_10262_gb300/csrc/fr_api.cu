@@ -46,6 +46,7 @@ struct fr_ctx {
     // and the grid of the adjoint kernel (its dL/dtheta partials fill gpart[Gg][ld])
     bool unrolled = false;
     float* ck = nullptr;
+    float* csk = nullptr;  // with ce == 1: the column sums of every iteration [U][L][nc]
     int ce = 0, nck = 0, Gg = 0;
     double *ad_blk = nullptr, *gn2_one = nullptr;
     float *gL = nullptr, *gP = nullptr, *e = nullptr, *invb = nullptr, *omega = nullptr,
@@ -132,7 +133,7 @@ P2Args p2_args(fr_ctx* c, float* part) {
     a.inv_eps_ln2 = (float)(1.0 / (c->cfg.epsilon * std::log(2.0)));
     a.inv_eps = (float)(1.0 / c->cfg.epsilon);
     a.warm = c->cfg.warm_start ? 1 : 0;
-    a.ck = c->ck; a.ce = c->ce; a.nck = c->nck;
+    a.ck = c->ck; a.ce = c->ce; a.nck = c->nck; a.csk = c->csk;
     a.max_polls = polls_of(c->cfg.max_wait_polls);
     return a;
 }
@@ -363,7 +364,7 @@ void free_all(fr_ctx* c) {
     if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
     cudaFree(c->solve_ctl);
     float* fs[] = {c->C, c->m1, c->m2, c->theta, c->tm1, c->tm2, c->w, c->gpart, c->gL, c->gP,
-                   c->e, c->invb, c->omega, c->part, c->tmp, c->ck, c->g0};
+                   c->e, c->invb, c->omega, c->part, c->tmp, c->ck, c->csk, c->g0};
     for (float* p : fs) cudaFree(p);
     double* ds[] = {c->gn2_part, c->imp, c->blk, c->F_hist, c->gn_hist, c->ad_blk, c->gn2_one};
     for (double* p : ds) cudaFree(p);
@@ -600,6 +601,11 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
             const size_t nck = (size_t)ctx->U * ctx->nck * nc;
             CUC(cudaMalloc(&ctx->ck, sizeof(float) * nck));
             CUC(cudaMemset(ctx->ck, 0, sizeof(float) * nck));
+            if (ctx->ce == 1) {  // state of the same size per iteration: the column sums too
+                const size_t ncs = (size_t)ctx->U * ctx->cfg.sinkhorn_iters * nc;
+                CUC(cudaMalloc(&ctx->csk, sizeof(float) * ncs));
+                CUC(cudaMemset(ctx->csk, 0, sizeof(float) * ncs));
+            }
         }
         CUC(cudaMalloc(&ctx->ad_blk, sizeof(double) * p2_adam_blocks(ctx->I)));
         CUC(cudaMalloc(&ctx->gn2_one, sizeof(double)));

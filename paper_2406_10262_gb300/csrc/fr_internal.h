@@ -102,6 +102,9 @@ struct P2Args {
     int warm;
     float* ck;            // unrolled gradient: column-potential checkpoints [U][nck][nc] (nullable)
     int ce, nck;          // checkpoint interval (iterations) and count ceil(L / ce)
+    float* csk;           // with a checkpoint every iteration: the column sums cs^(l+1) of every
+                          // iteration l [U][L][nc], so the adjoint skips its forward re-runs
+                          // (nullable)
     unsigned max_polls;   // bounded waits: polls before a wait gives up (0: expires at once)
 };
 

@@ -242,8 +242,19 @@ __device__ __forceinline__ void sweep_iter(const P2Args& a, const SweepSmem& s, 
 #pragma unroll
     for (int j = 0; j < NP; ++j) upk(cs2[j], cs[2 * j], cs[2 * j + 1]);
     if (TAIL) cs[NCB - 1] = cst;
-    column_update<NCB, GPL>(cs, gm, nc, s.red, s.ib, par, lane, warp, W);
+    // column sums (the reduction of column_update, written out here so that they can be kept
+    // for the adjoint), then g'_k -= log2(cs_k / b_k)
+    float csum[GPL];
+    column_sum<NCB, GPL>(cs, csum, nc, s.red, par, lane, warp, W);
     par ^= 1;
+#pragma unroll
+    for (int j = 0; j < GPL; ++j) {
+        const int col = j * 32 + lane;
+        if (col < nc) {
+            gm[j] -= log2_near1(fmaxf(csum[j] * s.ib[col], 1e-37f));
+            if (a.csk && warp == 0) a.csk[((size_t)u * a.L + l) * nc + col] = csum[j];
+        }
+    }
     // re-reference the potentials to the last column (x is invariant to a common shift)
     const float gref = __shfl_sync(FULL, gm[ref / 32], ref % 32);
 #pragma unroll

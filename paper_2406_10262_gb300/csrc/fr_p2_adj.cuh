@@ -25,6 +25,9 @@
 // j ce + 1 .. min((j+1) ce, L)) is recomputed from its checkpoint with the same arithmetic as the
 // sweep, keeping g^(l-1) and cs^(l) of the segment in shared memory (2 ce m floats), then reversed.
 // Work: L forward plus L reverse iterations per consumer; memory: ceil(L/ce) m floats per consumer.
+// With a checkpoint every iteration (ce = 1) the sweep also keeps each iteration's column sums
+// (P2Args::csk, L m more floats per consumer), and the re-runs reduce to loading them: L reverse
+// iterations per consumer.
 #pragma once
 #include "fr_p2.cuh"
 
@@ -180,37 +183,45 @@ __global__ void __launch_bounds__(256, adj_min_blocks<NCB, R>()) p2_adj_kernel(c
                         if (j * 32 + lane < nc) s.gs[q * np_ + j * 32 + lane] = gm[j];
                 }
                 if (l == L) break;  // the output layer needs g^(L-1) only
-                float gk[NCB];
-                f2 g2[NPA];
-                float gt;
-                adj_bcast<NCB, GPL, EXACT>(gm, nc, gk, g2, gt);
-                f2 cs2[NPA];
-#pragma unroll
-                for (int j = 0; j < NP; ++j) cs2[j] = 0ull;
-                float cst = 0.f;
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    if (!vr[r]) continue;
-                    f2 p2[NPA];
-                    float pt;
-                    const float inv = p2_row<NCB, EXACT>(sv[r], e2, et, g2, gt, s.eh, gk, nc, p2, pt);
-                    const f2 inv2 = pk(inv, inv);
-#pragma unroll
-                    for (int j = 0; j < NP; ++j) cs2[j] = fma2(p2[j], inv2, cs2[j]);
-                    cst = fmaf(pt, inv, cst);
-                }
-                float csv[NCB];
-#pragma unroll
-                for (int j = 0; j < NP; ++j) upk(cs2[j], csv[2 * j], csv[2 * j + 1]);
-                if (TAIL) csv[NCB - 1] = cst;
                 float csum[GPL];
-                column_sum<NCB, GPL>(csv, csum, nc, s.red, par, lane, warp, W);
-                par ^= 1;
+                if (a.csk) {  // the sweep kept this iteration's column sums: no row work
+#pragma unroll
+                    for (int j = 0; j < GPL; ++j) {
+                        const int col = j * 32 + lane;
+                        csum[j] = col < nc ? a.csk[((size_t)u * L + (l - 1)) * nc + col] : 0.f;
+                    }
+                } else {
+                    float gk[NCB];
+                    f2 g2[NPA];
+                    float gt;
+                    adj_bcast<NCB, GPL, EXACT>(gm, nc, gk, g2, gt);
+                    f2 cs2[NPA];
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) cs2[j] = 0ull;
+                    float cst = 0.f;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        if (!vr[r]) continue;
+                        f2 p2[NPA];
+                        float pt;
+                        const float inv = p2_row<NCB, EXACT>(sv[r], e2, et, g2, gt, s.eh, gk, nc, p2, pt);
+                        const f2 inv2 = pk(inv, inv);
+#pragma unroll
+                        for (int j = 0; j < NP; ++j) cs2[j] = fma2(p2[j], inv2, cs2[j]);
+                        cst = fmaf(pt, inv, cst);
+                    }
+                    float csv[NCB];
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) upk(cs2[j], csv[2 * j], csv[2 * j + 1]);
+                    if (TAIL) csv[NCB - 1] = cst;
+                    column_sum<NCB, GPL>(csv, csum, nc, s.red, par, lane, warp, W);
+                    par ^= 1;
+                }
 #pragma unroll
                 for (int j = 0; j < GPL; ++j) {
                     const int col = j * 32 + lane;
                     if (col < nc) {
-                        gm[j] -= log2f(fmaxf(csum[j] * s.ib[col], 1e-37f));  // as the sweep
+                        gm[j] -= log2_near1(fmaxf(csum[j] * s.ib[col], 1e-37f));  // as the sweep
                         if (warp == 0) s.cs[q * np_ + col] = csum[j];
                     }
                 }
