@@ -36,6 +36,7 @@ struct fr_ctx {
     P2Variant var2{};
     P1AdjVariant var1a{};  // free costs, unrolled gradient
     float* g0 = nullptr;   // free costs, unrolled gradient: [U][nc] starting potentials of the last solve
+    float *gall = nullptr, *csall = nullptr;  // free costs, ce == 1: [U][L][nc] g' and cs per iteration
     int r_bf16 = 0;
     float emax = 0.f;
     double esum = 0.0;  // sum of the K real exposures (uniform-policy impacts of the metrics)
@@ -118,6 +119,8 @@ P1Args p1_args(fr_ctx* c) {
     a.warm = c->cfg.warm_start ? 1 : 0;
     a.max_polls = polls_of(c->cfg.max_wait_polls);
     a.g0 = c->g0;
+    a.gall = c->gall;
+    a.csall = c->csall;
     a.ce = c->ce;
     a.nck = c->nck;
     return a;
@@ -364,7 +367,8 @@ void free_all(fr_ctx* c) {
     if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
     cudaFree(c->solve_ctl);
     float* fs[] = {c->C, c->m1, c->m2, c->theta, c->tm1, c->tm2, c->w, c->gpart, c->gL, c->gP,
-                   c->e, c->invb, c->omega, c->part, c->tmp, c->ck, c->csk, c->g0};
+                   c->e, c->invb, c->omega, c->part, c->tmp, c->ck, c->csk, c->g0, c->gall,
+                   c->csall};
     for (float* p : fs) cudaFree(p);
     double* ds[] = {c->gn2_part, c->imp, c->blk, c->F_hist, c->gn_hist, c->ad_blk, c->gn2_one};
     for (double* p : ds) cudaFree(p);
@@ -570,6 +574,10 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
             fr_status st = set_smem(var.fn[m], p1_smem_bytes(var, m, nc, ctx->ld));
             if (st != FR_OK) return bail(st);
         }
+        if (var.fn_rec) {
+            fr_status st = set_smem(var.fn_rec, p1_smem_bytes(var, MODE_SWEEP, nc, ctx->ld));
+            if (st != FR_OK) return bail(st);
+        }
         CUC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &occ, var.fn[MODE_UPDATE_SWEEP], var.threads,
             p1_smem_bytes(var, MODE_UPDATE_SWEEP, nc, ctx->ld)));
@@ -614,6 +622,13 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
         if (ctx->unrolled) {
             CUC(cudaMalloc(&ctx->g0, sizeof(float) * (size_t)ctx->U * nc));
             CUC(cudaMemset(ctx->g0, 0, sizeof(float) * (size_t)ctx->U * nc));
+            if (ctx->ce == 1) {  // the sweeps record every iteration; the adjoint only reverses
+                const size_t n = (size_t)ctx->U * ctx->cfg.sinkhorn_iters * nc;
+                CUC(cudaMalloc(&ctx->gall, sizeof(float) * n));
+                CUC(cudaMalloc(&ctx->csall, sizeof(float) * n));
+                CUC(cudaMemset(ctx->gall, 0, sizeof(float) * n));
+                CUC(cudaMemset(ctx->csall, 0, sizeof(float) * n));
+            }
         }
         CUC(cudaMalloc(&ctx->C, sizeof(float) * cells));
         CUC(cudaMalloc(&ctx->m1, sizeof(float) * cells));

@@ -469,11 +469,13 @@ __device__ __forceinline__ float log2_near1(float y) {
 }
 
 // Column update after the row sums: warp reduce-scatter of cs, one barrier, then every warp sums
-// the per-warp partials of its lanes' columns and updates its copy of g'.
-template <int NCB, int GPL>
+// the per-warp partials of its lanes' columns and updates its copy of g'. With REC, rec_g / rec_cs
+// (nc floats each) receive the iteration's g' before the update and its column sums.
+template <int NCB, int GPL, bool REC = false>
 __device__ __forceinline__ void column_update(float (&cs)[NCB], float (&gm)[GPL], int nc,
                                               float* s_red, const float* s_ib, int par, int lane,
-                                              int warp, int W) {
+                                              int warp, int W, float* rec_g = nullptr,
+                                              float* rec_cs = nullptr) {
     constexpr int P = pow2ceil(NCB);
     constexpr int PER = P >= 32 ? P / 32 : 1;
     float w[P];
@@ -494,6 +496,10 @@ __device__ __forceinline__ void column_update(float (&cs)[NCB], float (&gm)[GPL]
         if (col < nc) {
             float sum = 0.f;
             for (int ww = 0; ww < W; ++ww) sum += buf[ww * P + col];
+            if (REC && warp == 0) {
+                rec_g[col] = gm[j];
+                rec_cs[col] = sum;
+            }
             // log2 b - log2 cs = -log2(cs / b): the argument is near 1, so the log2 and the one
             // rounding of cs / b are accurate to ~1e-7 absolute (two logs of ~log2 |I| each would
             // carry ~5e-7 of rounding into every iteration's potentials)

@@ -65,6 +65,9 @@ struct P1Args {
     float* g0;            // unrolled gradient: [U][nc] log2-unit potentials each solve started
                           // from, stored by the sweeps when non-null
     int ce, nck;          // unrolled gradient: checkpoint interval and count ceil(L / ce)
+    float* gall;          // with a checkpoint every iteration: g' at the start of every iteration
+    float* csall;         // and its column sums, [U][L][nc] each, stored by the sweeps (nullable;
+                          // the unrolled gradient then does no forward re-runs)
 };
 
 struct ReduceArgs {
@@ -198,6 +201,8 @@ struct P1Variant {
     int threads;          // CTA size
     size_t smem;          // dynamic shared memory (bytes) of the largest mode
     const void* fn[3];    // kernels by Mode
+    const void* fn_rec;   // MODE_SWEEP that also records g' and the column sums of every iteration
+                          // (P1Args::gall / csall), for the unrolled gradient
     const void* fb[2];    // batched-market kernels (argument: P1Batch) for MODE_SWEEP and
                           // MODE_UPDATE_SWEEP; set by p1_select_batch only
 };

@@ -16,7 +16,9 @@ bool p1_select(int nc, int I, P1Variant* out) {
 cudaError_t p1_launch(const P1Variant& v, int mode, const P1Args& a, cudaStream_t s) {
     const size_t smem = p1_smem_bytes(v, mode, a.nc, a.ld);
     void* args[] = {const_cast<P1Args*>(&a)};
-    return cudaLaunchKernel(v.fn[mode], dim3(a.G), dim3(v.threads), args, smem, s);
+    // the unrolled gradient's solves record every iteration (its own compiled kernel)
+    const void* fn = (mode == MODE_SWEEP && a.gall) ? v.fn_rec : v.fn[mode];
+    return cudaLaunchKernel(fn, dim3(a.G), dim3(v.threads), args, smem, s);
 }
 
 }  // namespace fr

@@ -296,7 +296,7 @@ constexpr float TS_DRIFT = 30.f;
 //   TS_DRIFT the CTA rebuilds its rows in this form from the costs in global memory (at the
 //   current g') and finishes the solve in it; every warp holds the same g', so all decide alike.
 // Each thread rewrites only its own rows, which only it reads during the solve.
-template <int NCB, int R, int BR, int LDS, bool EXACT, int MODE>
+template <int NCB, int R, int BR, int LDS, bool EXACT, int MODE, bool REC = false>
 __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u, int nc,
                                            float (&gm)[(NCB + 31) / 32], int& par,
                                            float* part_row, bool first_row, const P1Args& na,
@@ -598,7 +598,9 @@ __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u
                 cs[k] = lo + hi;
             }
         }
-        column_update<NCB, GPL>(cs, gm, nc, s.red, s.ib, par, lane, warp, W);
+        column_update<NCB, GPL, REC>(cs, gm, nc, s.red, s.ib, par, lane, warp, W,
+                                     REC ? a.gall + ((size_t)u * a.L + l) * nc : nullptr,
+                                     REC ? a.csall + ((size_t)u * a.L + l) * nc : nullptr);
         par ^= 1;
         // the next consumer's tile and relevance row into L2 eight iterations before the end of
         // this solve: early enough to hide the HBM latency, late enough that four CTAs per SM
@@ -618,7 +620,7 @@ __device__ __forceinline__ void tile_sweep(const P1Args& a, const Smem& s, int u
 // row's first consumer, first_row) or are added to acc_imp (the register sweep; the caller writes
 // them out); the squared gradient is added to gn2. Returns false if a bounded wait expired (the CTA
 // then stops). The per-market shared arrays (e, 1/b, omega, the Adam coefficients) must hold a's.
-template <int NCB, int R, bool EXACT, int MODE, int TS>
+template <int NCB, int R, bool EXACT, int MODE, int TS, bool REC = false>
 __device__ __forceinline__ bool p1_consumer(const P1Args& a, const Smem& s, int u, const P1Args& na,
                                             int nu, float* part_row, bool first_row,
                                             float (&acc_imp)[R], double& gn2, int& par,
@@ -885,7 +887,7 @@ __device__ __forceinline__ bool p1_consumer(const P1Args& a, const Smem& s, int 
 
             // ---------------- Sinkhorn solve on the consumer's (new) costs ----------------------------
             if constexpr (TS != 0) {
-                tile_sweep<NCB, R, 2, TS, EXACT, MODE>(a, s, u, nc, gm, par, part_row, first_row, na, nu);
+                tile_sweep<NCB, R, 2, TS, EXACT, MODE, REC>(a, s, u, nc, gm, par, part_row, first_row, na, nu);
             } else {
             float rr[R];
             bool vr[R];
@@ -1098,7 +1100,9 @@ __device__ __forceinline__ bool p1_consumer(const P1Args& a, const Smem& s, int 
                         upk(cs2[k], lo, hi);
                         cs[k] = lo + hi;
                     }
-                    column_update<NCB, GPL>(cs, gm, nc, s.red, s.ib, par, lane, warp, W);
+                    column_update<NCB, GPL, REC>(cs, gm, nc, s.red, s.ib, par, lane, warp, W,
+                                                 REC ? a.gall + ((size_t)u * a.L + l) * nc : nullptr,
+                                                 REC ? a.csall + ((size_t)u * a.L + l) * nc : nullptr);
                     par ^= 1;
                     if (l == 0 && tid == 0)
                         stage_consumer(na, nu, ncn, na.ld, s, MODE == MODE_UPDATE_SWEEP && a.optimizer == 0, false);
@@ -1156,7 +1160,9 @@ __device__ __forceinline__ bool p1_consumer(const P1Args& a, const Smem& s, int 
                             acc_imp[r] += rr[r] * (v * inv);
                         }
                     }
-                    column_update<NCB, GPL>(cs, gm, nc, s.red, s.ib, par, lane, warp, W);
+                    column_update<NCB, GPL, REC>(cs, gm, nc, s.red, s.ib, par, lane, warp, W,
+                                                 REC ? a.gall + ((size_t)u * a.L + l) * nc : nullptr,
+                                                 REC ? a.csall + ((size_t)u * a.L + l) * nc : nullptr);
                     par ^= 1;
                     if (l == 0 && tid == 0)
                         stage_consumer(na, nu, ncn, na.ld, s, MODE == MODE_UPDATE_SWEEP && a.optimizer == 0, false);
@@ -1209,7 +1215,7 @@ __device__ __forceinline__ void p1_market_setup(const P1Args& a, const Smem& s) 
 
 // Launch bound: 512 threads, except the tile sweep of more than 16 columns, which serves at most
 // 2048 items (256 threads) and may then use up to 255 registers per thread.
-template <int NCB, int R, bool EXACT, int MODE, int TS>
+template <int NCB, int R, bool EXACT, int MODE, int TS, bool REC = false>
 __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(const P1Args a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nc = EXACT ? NCB : a.nc;
@@ -1261,7 +1267,7 @@ __global__ void __launch_bounds__((TS != 0 && NCB > 16) ? 256 : 512) p1_kernel(c
 
     for (int u = blockIdx.x; u < a.U; u += gridDim.x) {
         const int nu = u + (int)gridDim.x < a.U ? u + (int)gridDim.x : -1;
-        if (!p1_consumer<NCB, R, EXACT, MODE, TS>(a, s, u, a, nu, a.part + (size_t)blockIdx.x * ld,
+        if (!p1_consumer<NCB, R, EXACT, MODE, TS, REC>(a, s, u, a, nu, a.part + (size_t)blockIdx.x * ld,
                                                   u == (int)blockIdx.x, acc_imp, gn2, par, phase))
             break;
     }
@@ -1399,6 +1405,7 @@ P1Variant make_variant(int threads) {
     v.fn[MODE_SWEEP] = (const void*)p1_kernel<NCB, R, EXACT, MODE_SWEEP, TS>;
     v.fn[MODE_UPDATE_SWEEP] = (const void*)p1_kernel<NCB, R, EXACT, MODE_UPDATE_SWEEP, TS>;
     v.fn[MODE_GRAD] = (const void*)p1_kernel<NCB, R, EXACT, MODE_GRAD, TS>;
+    v.fn_rec = (const void*)p1_kernel<NCB, R, EXACT, MODE_SWEEP, TS, true>;
     return v;
 }
 

@@ -19,7 +19,9 @@
 // g^(0) (P1Args::g0). The kernel re-runs the forward from g^(0), keeping g^(j ce) for
 // j = 0 .. ceil(L/ce)-1 in shared memory, then walks the segments backwards, recomputing each
 // segment's g^(l-1) and cs^(l) (2 ce m floats of shared memory) before reversing it. The forward
-// iterations use the log form with an exact row-max shift (one exp2 per cell).
+// iterations use the log form with an exact row-max shift (one exp2 per cell). With a checkpoint
+// every iteration (ce = 1) the sweep records g^(l-1) and cs^(l) of every iteration
+// (P1Args::gall / csall, 2 L m floats per consumer) and the kernel only runs the reverse.
 //
 // Modes: ADJ_GRAD writes dL/dC in the public layout [u][i][k] and dL/dr = omega_i v_i (C does not
 // depend on r); ADJ_STEP applies the optimiser to the consumer's costs with dF/dC (omega = 1/Imp)
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(256) p1_adj_kernel(const P1Args a) {
             const int col = j * 32 + lane;
             gm[j] = col < nc ? a.g0[(size_t)u * nc + col] : 0.f;
         }
-        for (int l = 0;; ++l) {  // gm = g'^(l)
+        for (int l = 0; !a.gall; ++l) {  // gm = g'^(l); none with the sweep's records
             if (l % ce == 0 && warp == 0) {
 #pragma unroll
                 for (int j = 0; j < GPL; ++j)
@@ -229,7 +231,21 @@ __global__ void __launch_bounds__(256) p1_adj_kernel(const P1Args a) {
                 const int col = j * 32 + lane;
                 gm[j] = col < nc ? s.ck[seg * np + col] : 0.f;
             }
-            for (int l = l0 + 1; l <= l1; ++l) {  // recompute g'^(l-1) and cs^(l) of the segment
+            for (int l = l0 + 1; a.gall && l <= l1; ++l) {  // the sweep recorded them
+                const int q = l - l0 - 1;
+                if (warp == 0) {
+                    const size_t o = ((size_t)u * L + (l - 1)) * nc;
+#pragma unroll
+                    for (int j = 0; j < GPL; ++j) {
+                        const int col = j * 32 + lane;
+                        if (col < nc) {
+                            s.gs[q * np + col] = a.gall[o + col];
+                            if (l < L) s.cs[q * np + col] = a.csall[o + col];
+                        }
+                    }
+                }
+            }
+            for (int l = l0 + 1; !a.gall && l <= l1; ++l) {  // recompute g'^(l-1), cs^(l)
                 const int q = l - l0 - 1;
                 if (warp == 0) {
 #pragma unroll

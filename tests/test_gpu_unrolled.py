@@ -247,7 +247,9 @@ def pair_unrolled_p1(U, I, K, r, L, ce, warm=True, **kw):
     (3, 60, 25, 8, 8),       # padded 32-column bucket
     (3, 24, 24, 10, 4),      # |I| == K (no dummy column)
     (4, 50, 5, 1, 10),       # L = 1: the output layer only
-    (4, 50, 5, 7, 1),        # a checkpoint at every iteration
+    (4, 50, 5, 7, 1),        # a checkpoint at every iteration: the sweep's records, no re-runs
+    (5, 1000, 10, 12, 1),    # the same, recorded by the 11-column tile sweep
+    (4, 300, 20, 15, 1),     # the same, 21 columns
 ])
 def test_free_cost_unrolled_grad_matches_oracle(U, I, K, L, ce):
     """dL/dC of every cell and dL/dr from the adjoint kernel against the oracle's reverse sweep of
@@ -274,11 +276,12 @@ def test_free_cost_unrolled_grad_matches_oracle(U, I, K, L, ce):
     g.close()
 
 
-@pytest.mark.parametrize("opt", [fr.ADAM, fr.SGD])
-def test_free_cost_unrolled_trajectory_matches_oracle(opt):
+@pytest.mark.parametrize("opt,ce", [(fr.ADAM, 6), (fr.SGD, 6), (fr.ADAM, 1)])
+def test_free_cost_unrolled_trajectory_matches_oracle(opt, ce):
     """Ascent steps driven by the adjoint (optimiser applied in the adjoint kernel, then the
-    Sinkhorn kernel on the new costs): F after every step against the oracle's trajectory."""
-    U, I, K, L, ce = 8, 60, 10, 20, 6
+    Sinkhorn kernel on the new costs): F after every step against the oracle's trajectory; with a
+    checkpoint every iteration the adjoint reverses the sweep's own records."""
+    U, I, K, L = 8, 60, 10, 20
     r = synth.relevance_lowrank(U, I, seed=31)
     lr = 0.1 if opt == fr.ADAM else 0.5
     g, o = pair_unrolled_p1(U, I, K, r, L, ce, optimizer=opt, lr=lr)
