@@ -421,8 +421,10 @@ def measure_forms():
     """Short measurements of the layered forms, recorded beside the headline (each in its own
     try block, so a failure is reported instead of losing the line):
     per_item: |U| = 20000, |I| = 2000, K = 20, L = 100 -- Sinkhorn sweep, implicit gradient and
-    unrolled adjoint (checkpoints every 10, and every iteration) kernel times; batch: the
-    256-market workload, 8 ascent steps batched against 256 contexts run one after another;
+    unrolled adjoint (checkpoints every 10, and every iteration) kernel times;
+    free_cost_gradients: 2000 x 1000 x 11, L = 50 -- the fused implicit step and the unrolled
+    gradient's kernels (checkpoints every 10, and every iteration); batch: the 256-market workload, 8 ascent steps batched against 256 contexts run one
+    after another;
     metrics: fr_metrics (the envy contraction) at 20000 consumers x 10^4 items."""
     import torch
     from paper_2406_10262_gb300 import fairrank as fr
@@ -458,6 +460,24 @@ def measure_forms():
         out["per_item"] = res
     except Exception as ex:  # noqa: BLE001 -- reported in the line
         out["per_item"] = {"error": repr(ex)}
+    try:
+        U, I, K, L = 2000, 1000, 10, 50
+        r = synth.workload_relevance("plain2000x1000").astype(np.float32)
+        res = {"n_users": U, "n_items": I, "n_slots": K, "sinkhorn_iters": L}
+        for name, mode, ce in (("implicit", fr.GRAD_IMPLICIT, 10), ("unrolled", fr.GRAD_UNROLLED, 10),
+                               ("unrolled_ckpt_every_1", fr.GRAD_UNROLLED, 1)):
+            g = fr.FairRank(U, I, K, sinkhorn_iters=L, grad_mode=mode, ckpt_every=ce)
+            g.set_relevance(r)
+            g.set_exposure(synth.dcg_exposure(K))
+            g.step(3, trace=False)
+            ms = g.time_kernels(5)
+            keys = (("fused_step_ms", "reduce_ms", "sweep_only_ms") if mode == fr.GRAD_IMPLICIT
+                    else ("sweep_ms", "reduce_ms", "adjoint_adam_ms"))
+            res[name] = dict(zip(keys, (float(x) for x in ms)))
+            g.close()
+        out["free_cost_gradients"] = res
+    except Exception as ex:  # noqa: BLE001
+        out["free_cost_gradients"] = {"error": repr(ex)}
     try:
         c = compare_batch(argparse.Namespace(steps=1))
         out["batch"] = {k: c[k] for k in ("markets", "ascent_steps", "sinkhorn_iters", "cells",
