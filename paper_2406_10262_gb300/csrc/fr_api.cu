@@ -83,12 +83,16 @@ fr_status fail(fr_ctx* c, fr_status st, const char* fmt, ...) {
     return st;
 }
 
+// A failing runtime call returns its status with the message; its (non-sticky) error is also
+// cleared from the runtime's last-error state, so that it cannot surface in a later call's checks.
 #define CU(call)                                                                             \
     do {                                                                                     \
         cudaError_t e_ = (call);                                                             \
-        if (e_ != cudaSuccess)                                                               \
+        if (e_ != cudaSuccess) {                                                             \
+            cudaGetLastError();                                                              \
             return fail(ctx, e_ == cudaErrorMemoryAllocation ? FR_ENOMEM : FR_ECUDA, "%s: %s", \
                         #call, cudaGetErrorString(e_));                                      \
+        }                                                                                    \
     } while (0)
 
 // Orders the library stream after the caller's stream (call entry) and back (call exit).
@@ -443,6 +447,7 @@ int32_t fr_num_cols(int32_t n_items, int32_t n_slots) {
 }
 
 fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
+    NvtxRange nvtx_range("fr_create");
     fr_ctx* ctx = nullptr;
     if (!out) return fail(nullptr, FR_EINVAL, "out is NULL");
     *out = nullptr;
@@ -523,6 +528,7 @@ fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out) {
         g_create_error = ctx->err;
         free_all(ctx);
         delete ctx;
+        cudaGetLastError();  // a failed allocation must not surface in the next call's checks
         return st;
     };
 #define CUC(call)                                                                             \
@@ -674,6 +680,7 @@ fr_status fr_reset(fr_ctx* ctx) {
 }
 
 fr_status fr_set_relevance(fr_ctx* ctx, const void* r, int32_t dtype, int64_t ld, int32_t on_device) {
+    NvtxRange nvtx_range("fr_set_relevance");
     if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
     if (!r) return fail(ctx, FR_EINVAL, "r is NULL");
     if (dtype != FR_F32 && dtype != FR_F64 && dtype != FR_BF16)
@@ -732,6 +739,7 @@ fr_status fr_set_exposure(fr_ctx* ctx, const double* e, int32_t K) {
 }
 
 fr_status fr_step(fr_ctx* ctx, int32_t n_steps, double* nsw_trace) {
+    NvtxRange nvtx_range("fr_step");
     if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
     if (n_steps < 0) return fail(ctx, FR_EINVAL, "n_steps < 0");
     Join j(ctx);
@@ -750,6 +758,7 @@ fr_status fr_step(fr_ctx* ctx, int32_t n_steps, double* nsw_trace) {
 }
 
 fr_status fr_solve(fr_ctx* ctx, double t, int32_t max_steps, int32_t* steps_done, double* nsw_out) {
+    NvtxRange nvtx_range("fr_solve");
     if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
     if (max_steps < 0 || !(t >= 0.0)) return fail(ctx, FR_EINVAL, "need max_steps >= 0 and t >= 0");
     Join j(ctx);
@@ -774,6 +783,7 @@ fr_status fr_solve(fr_ctx* ctx, double t, int32_t max_steps, int32_t* steps_done
 }
 
 fr_status fr_impacts(fr_ctx* ctx, double* imp_out, double* utility_out, double* nsw_out) {
+    NvtxRange nvtx_range("fr_impacts");
     if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
     Join j(ctx);
     fr_status st = ensure_fresh(ctx);
@@ -787,6 +797,7 @@ fr_status fr_impacts(fr_ctx* ctx, double* imp_out, double* utility_out, double* 
 }
 
 fr_status fr_policy(fr_ctx* ctx, int32_t u0, int32_t n_u, float* x_out, int32_t on_device) {
+    NvtxRange nvtx_range("fr_policy");
     if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
     if (u0 < 0 || n_u < 0 || (int64_t)u0 + n_u > ctx->U)
         return fail(ctx, FR_EINVAL, "consumer range [%d, %d) outside [0, %d)", u0, u0 + n_u, ctx->U);
@@ -811,6 +822,7 @@ fr_status fr_policy(fr_ctx* ctx, int32_t u0, int32_t n_u, float* x_out, int32_t 
 }
 
 fr_status fr_grad(fr_ctx* ctx, const float* omega, float* dparam, float* dr, int32_t on_device) {
+    NvtxRange nvtx_range("fr_grad");
     if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
     if (!dparam) return fail(ctx, FR_EINVAL, "dparam is NULL");
     Join j(ctx);
@@ -856,6 +868,7 @@ fr_status fr_grad(fr_ctx* ctx, const float* omega, float* dparam, float* dr, int
 
 fr_status fr_set_state(fr_ctx* ctx, const float* param, const float* m1, const float* m2,
                        const float* g, int64_t t, int32_t on_device) {
+    NvtxRange nvtx_range("fr_set_state");
     if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
     if (t < 0) return fail(ctx, FR_EINVAL, "t < 0");
     Join j(ctx);
@@ -906,6 +919,7 @@ fr_status fr_set_state(fr_ctx* ctx, const float* param, const float* m1, const f
 
 fr_status fr_get_state(fr_ctx* ctx, float* param, float* m1, float* m2, float* g, int64_t* t,
                        int32_t on_device) {
+    NvtxRange nvtx_range("fr_get_state");
     if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
     Join j(ctx);
     const size_t nP = nparam(ctx);
@@ -981,6 +995,7 @@ static fr_status metrics_run(fr_ctx* ctx, double h[3], double* env_host) {
 
 fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* better_pct,
                      double* worse_pct) {
+    NvtxRange nvtx_range("fr_metrics");
     if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
     Join j(ctx);
     double h[3];
@@ -994,6 +1009,7 @@ fr_status fr_metrics(fr_ctx* ctx, double* utility, double* mean_envy, double* be
 }
 
 fr_status fr_item_envy(fr_ctx* ctx, double* envy) {
+    NvtxRange nvtx_range("fr_item_envy");
     if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
     if (!envy) return fail(ctx, FR_EINVAL, "envy is NULL");
     Join j(ctx);
@@ -1002,6 +1018,7 @@ fr_status fr_item_envy(fr_ctx* ctx, double* envy) {
 }
 
 fr_status fr_certificate(fr_ctx* ctx, double* gap, double* col_residual) {
+    NvtxRange nvtx_range("fr_certificate");
     if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
     Join j(ctx);
     fr_status st = ensure_fresh(ctx);

@@ -122,9 +122,11 @@ fr_status bfail(fr_batch* b, fr_status st, const char* fmt, ...) {
 #define BCU(call)                                                                             \
     do {                                                                                      \
         cudaError_t e_ = (call);                                                              \
-        if (e_ != cudaSuccess)                                                                \
+        if (e_ != cudaSuccess) {                                                              \
+            cudaGetLastError(); /* no stale error in a later call's checks */                 \
             return bfail(b, e_ == cudaErrorMemoryAllocation ? FR_ENOMEM : FR_ECUDA, "%s: %s", \
                          #call, cudaGetErrorString(e_));                                      \
+        }                                                                                     \
     } while (0)
 
 struct BJoin {
@@ -676,6 +678,7 @@ fr_batch* checked(fr_batch* b, int32_t market, fr_status* st) {
 extern "C" {
 
 fr_status fr_batch_create(const fr_config* cfgs, int32_t n_markets, void* stream, fr_batch** out) {
+    NvtxRange nvtx_range("fr_batch_create");
     fr_batch* b = nullptr;
     if (!out) return bfail(nullptr, FR_EINVAL, "out is NULL");
     *out = nullptr;
@@ -900,6 +903,7 @@ fr_status fr_batch_reset(fr_batch* b) {
 
 fr_status fr_batch_set_relevance(fr_batch* b, int32_t market, const void* r, int32_t dtype, int64_t ld,
                                  int32_t on_device) {
+    NvtxRange nvtx_range("fr_batch_set_relevance");
     fr_status st = FR_OK;
     if (!checked(b, market, &st)) return st;
     BMarket& m = b->mk[market];
@@ -961,6 +965,7 @@ fr_status fr_batch_set_exposure(fr_batch* b, int32_t market, const double* e, in
 }
 
 fr_status fr_batch_autotune(fr_batch* b) {
+    NvtxRange nvtx_range("fr_batch_autotune");
     if (!b) return bfail(nullptr, FR_EINVAL, "batch is NULL");
     for (int i = 0; i < b->M; ++i)
         if (!b->mk[i].have_r || !b->mk[i].have_e)
@@ -970,6 +975,7 @@ fr_status fr_batch_autotune(fr_batch* b) {
 }
 
 fr_status fr_batch_step(fr_batch* b, int32_t n_steps, double* nsw_trace) {
+    NvtxRange nvtx_range("fr_batch_step");
     if (!b) return bfail(nullptr, FR_EINVAL, "batch is NULL");
     if (n_steps < 0) return bfail(b, FR_EINVAL, "n_steps < 0");
     BJoin j(b);
@@ -1001,6 +1007,7 @@ fr_status fr_batch_step(fr_batch* b, int32_t n_steps, double* nsw_trace) {
 
 fr_status fr_batch_impacts(fr_batch* b, int32_t market, double* imp_out, double* utility_out,
                            double* nsw_out) {
+    NvtxRange nvtx_range("fr_batch_impacts");
     fr_status st = FR_OK;
     if (!checked(b, market, &st)) return st;
     BJoin j(b);
@@ -1016,6 +1023,7 @@ fr_status fr_batch_impacts(fr_batch* b, int32_t market, double* imp_out, double*
 
 fr_status fr_batch_policy(fr_batch* b, int32_t market, int32_t u0, int32_t n_u, float* x_out,
                           int32_t on_device) {
+    NvtxRange nvtx_range("fr_batch_policy");
     fr_status st = FR_OK;
     if (!checked(b, market, &st)) return st;
     const BMarket& m = b->mk[market];

@@ -16,10 +16,21 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "fairrank.h"
 
 namespace fr {
+
+// NVTX range over a public entry point: names the call on a profiler's timeline (header-only NVTX
+// 3; without a tool attached the push / pop return at once).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 
 // Device-resident step state: read and written by the kernels so that captured CUDA graphs can
 // be replayed without changing kernel arguments.

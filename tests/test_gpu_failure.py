@@ -136,3 +136,20 @@ def test_impact_below_fp32_range_reports_numeric_error(torch, param):
     imp, _, F = o.impacts()
     assert imp[5] > 0 and np.isfinite(F)
     g.close()
+
+
+def test_allocation_failure_reports_enomem_and_frees_what_it_took(torch):
+    """A context larger than the GPU (free costs for 3 million consumers x 1024 items x 21 columns:
+    C and each Adam moment 258 GB) fails with FR_ENOMEM instead of faulting, gives back every block
+    it had allocated, and the device stays usable for the next context."""
+    torch.cuda.synchronize()
+    free0, total = torch.cuda.mem_get_info()
+    msg = expect_status(2, fr.FairRank, 3_000_000, 1024, 20)  # FR_ENOMEM
+    assert "cudaMalloc" in msg or "memory" in msg
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 >= free0 - (64 << 20)
+    g = make(8, 100, 10)
+    F = g.step(2)
+    assert np.isfinite(F).all()
+    g.close()
