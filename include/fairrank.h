@@ -136,6 +136,12 @@ FR_API fr_status fr_step(fr_ctx* ctx, int32_t n_steps, double* nsw_trace);
 FR_API fr_status fr_solve(fr_ctx* ctx, double t, int32_t max_steps, int32_t* steps_done,
                    double* nsw_out);
 
+/* Per-step record of the last fr_step or fr_solve call (host doubles, each nullable, the first
+   min(n, recorded) steps): nsw[k] = F after step k (FP64), grad_norm[k] = ||grad F||_2 of step k
+   (FP64, the norm Algorithm 1's stop test compares with t, taken at the policy before that step's
+   update). *n_steps (nullable) receives the number of steps recorded. FR_EINVAL if n < 0. */
+FR_API fr_status fr_trace(fr_ctx* ctx, int32_t n, double* nsw, double* grad_norm, int32_t* n_steps);
+
 /* Current impacts Imp_i (Eq. 4; host, n_items doubles, nullable), user utility sum_i Imp_i / |U|
    (Sec. 4.1, nullable) and F (Eq. 5, nullable) of the current policy; solves first if stale. */
 FR_API fr_status fr_impacts(fr_ctx* ctx, double* imp_out, double* utility_out, double* nsw_out);

@@ -57,6 +57,7 @@ struct fr_ctx {
     size_t tmp_bytes = 0;
     double *gn2_part = nullptr, *imp = nullptr, *blk = nullptr, *F_hist = nullptr, *gn_hist = nullptr;
     int hist_cap = 0;
+    int hist_n = 0;  // steps recorded in F_hist / gn_hist by the last fr_step or fr_solve
     DevState* st = nullptr;
     DevState* st_host = nullptr;  // pinned
     int* flags = nullptr;
@@ -745,10 +746,12 @@ fr_status fr_step(fr_ctx* ctx, int32_t n_steps, double* nsw_trace) {
     Join j(ctx);
     fr_status st = ensure_fresh(ctx);
     if (st != FR_OK) return st;
+    ctx->hist_n = 0;
     if ((st = ensure_hist(ctx, n_steps)) != FR_OK) return st;
     if ((st = set_run_state(ctx, -1.0)) != FR_OK) return st;
     if ((st = run_steps(ctx, n_steps)) != FR_OK) return st;
     if ((st = read_state(ctx)) != FR_OK) return st;
+    ctx->hist_n = n_steps;
     if (nsw_trace && n_steps > 0) {
         CU(cudaMemcpyAsync(nsw_trace, ctx->F_hist, sizeof(double) * n_steps, cudaMemcpyDeviceToHost,
                            ctx->s));
@@ -764,6 +767,7 @@ fr_status fr_solve(fr_ctx* ctx, double t, int32_t max_steps, int32_t* steps_done
     Join j(ctx);
     fr_status st = ensure_fresh(ctx);
     if (st != FR_OK) return st;
+    ctx->hist_n = 0;
     if ((st = ensure_hist(ctx, max_steps)) != FR_OK) return st;
     if ((st = set_run_state(ctx, t, max_steps)) != FR_OK) return st;
     if (max_steps > 0) {
@@ -777,9 +781,25 @@ fr_status fr_solve(fr_ctx* ctx, double t, int32_t max_steps, int32_t* steps_done
         ctx->launches += (int64_t)done_ctl[0] * (kernels_per_step(ctx) * kChunk + 1);
     }
     if ((st = read_state(ctx)) != FR_OK) return st;
+    ctx->hist_n = ctx->st_host->steps_done;
     if (steps_done) *steps_done = ctx->st_host->steps_done;
     if (nsw_out) *nsw_out = ctx->st_host->F;
     return set_run_state(ctx, -1.0);
+}
+
+fr_status fr_trace(fr_ctx* ctx, int32_t n, double* nsw, double* grad_norm, int32_t* n_steps) {
+    NvtxRange nvtx_range("fr_trace");
+    if (!ctx) return fail(nullptr, FR_EINVAL, "ctx is NULL");
+    if (n < 0) return fail(ctx, FR_EINVAL, "n < 0");
+    const int m = std::min(n, ctx->hist_n);
+    if (n_steps) *n_steps = ctx->hist_n;
+    if (m == 0) return FR_OK;
+    Join j(ctx);
+    if (nsw) CU(cudaMemcpyAsync(nsw, ctx->F_hist, sizeof(double) * m, cudaMemcpyDeviceToHost, ctx->s));
+    if (grad_norm)
+        CU(cudaMemcpyAsync(grad_norm, ctx->gn_hist, sizeof(double) * m, cudaMemcpyDeviceToHost, ctx->s));
+    CU(cudaStreamSynchronize(ctx->s));
+    return FR_OK;
 }
 
 fr_status fr_impacts(fr_ctx* ctx, double* imp_out, double* utility_out, double* nsw_out) {

@@ -70,6 +70,7 @@ def lib():
             "fr_get_state": (i32, [_vp, _vp, _vp, _vp, _vp, ct.POINTER(i64), i32]),
             "fr_metrics": (i32, [_vp, _dp, _dp, _dp, _dp]),
             "fr_item_envy": (i32, [_vp, _dp]),
+            "fr_trace": (i32, [_vp, i32, _dp, _dp, ct.POINTER(i32)]),
             "fr_certificate": (i32, [_vp, _dp, _dp]),
             "fr_last_error": (ct.c_char_p, [_vp]),
             "fr_launch_count": (i64, [_vp]),
@@ -312,6 +313,14 @@ class FairRank:
         vals = [ct.c_double() for _ in range(4)]
         self._check(lib().fr_metrics(self.h, *[ct.byref(v) for v in vals]))
         return dict(zip(["utility", "mean_envy", "better_pct", "worse_pct"], [v.value for v in vals]))
+
+    def trace(self):
+        """(F after each step, gradient norm of each step) of the last step() / solve() call."""
+        n = ct.c_int32()
+        self._check(lib().fr_trace(self.h, 0, None, None, ct.byref(n)))
+        F, gn = np.zeros(n.value), np.zeros(n.value)
+        self._check(lib().fr_trace(self.h, n.value, F.ctypes.data_as(_dp), gn.ctypes.data_as(_dp), None))
+        return F, gn
 
     def item_envy(self):
         """Per-item envy max_j (Imp_i(X_j) - Imp_i(X_i)) at the current policy, [n_items] doubles."""

@@ -26,7 +26,7 @@ def pair(U, I, K, r, seed_state=None, **kw):
     g = fr.FairRank(U, I, K, **kw)
     g.set_relevance(np.ascontiguousarray(r, dtype=np.float32))
     g.set_exposure(e)
-    okw = {k: v for k, v in kw.items() if k in ("epsilon", "warm_start", "optimizer", "lr", "beta1", "beta2", "adam_eps")}
+    okw = {k: v for k, v in kw.items() if k in ("epsilon", "warm_start", "optimizer", "lr", "beta1", "beta2", "adam_eps", "param")}
     if "sinkhorn_iters" in kw:
         okw["iters"] = kw["sinkhorn_iters"]
     o = oracle.Oracle(U, I, K, **okw)

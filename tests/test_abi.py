@@ -59,3 +59,4 @@ def test_create_rejects_invalid_config_before_touching_the_device(lib, field, va
 def test_null_context_is_rejected(lib):
     assert lib.fr_step(None, 1, None) == 1
     assert lib.fr_impacts(None, None, None, None) == 1
+    assert lib.fr_trace(None, 0, None, None, None) == 1

@@ -157,6 +157,30 @@ def test_solve_stops_like_the_oracle():
     assert rel(F_g, F_o) < NSW_RTOL
 
 
+@pytest.mark.parametrize("param", [fr.PARAM_FULL_C, fr.PARAM_ITEM])
+def test_trace_reports_each_steps_objective_and_gradient_norm(param):
+    """fr_trace after fr_step: F after each step equals the trace fr_step returned, and the FP64
+    gradient norm of each step (the quantity Algorithm 1's stop test compares with t) matches the
+    oracle's; after fr_solve the record covers exactly the steps the solve ran."""
+    U, I, K = 9, 40, 5
+    r = synth.relevance_lowrank(U, I, seed=4)
+    kw = {} if param == fr.PARAM_FULL_C else {"param": fr.PARAM_ITEM}
+    g, o = pair(U, I, K, r, **kw)
+    F = g.step(15)
+    Ft, gn = g.trace()
+    np.testing.assert_array_equal(Ft, F)
+    Fo, gno = o.step(15)
+    np.testing.assert_allclose(gn, gno, rtol=1e-5)
+    thr = float(gno[-1]) * 0.999
+    n, Fs = g.solve(thr, 4)
+    no, Fso = o.solve(thr, 4)
+    Ft2, gn2 = g.trace()
+    assert n == no and Ft2.size == n and gn2.size == n and Ft2[-1] == Fs
+    assert rel(Fs, Fso) < NSW_RTOL
+    assert np.all(gn2[:-1] > thr) and (n == 4 or gn2[-1] <= thr)
+    g.close()
+
+
 def test_error_statuses():
     with pytest.raises(fr.FairRankError) as ei:
         fr.FairRank(4, 5, 2, param=fr.PARAM_ITEM, grad_mode=7)
