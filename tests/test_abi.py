@@ -43,7 +43,7 @@ def test_config_defaults_and_columns(lib):
     assert fr.num_cols(20, 5) == 6 and fr.num_cols(5, 5) == 5
 
 
-@pytest.mark.parametrize("field,value", [("n_slots", 0), ("n_items", 3), ("epsilon", 0.0),
+@pytest.mark.parametrize("field,value", [("n_users", 0), ("n_slots", 0), ("n_items", 3), ("epsilon", 0.0),
                                          ("sinkhorn_iters", 0), ("lr", -1.0), ("optimizer", 7),
                                          ("max_wait_polls", -2)])
 def test_create_rejects_invalid_config_before_touching_the_device(lib, field, value):

@@ -53,6 +53,8 @@ def test_initial_sweep_is_the_uniform_policy():
     (3, 1000, 10, 1.0, 1, 1),     # 11 columns, tile sweep
     (2, 1030, 10, 0.9, 2, 1),     # 11 columns, tile sweep, 2048-float stride
     (2, 700, 20, 1.0, 1, 1),      # 21 columns, tile sweep
+    (1, 30, 5, 1.0, 50, 1),       # one consumer: one CTA, no cross-CTA partials
+    (4, 40, 1, 1.0, 30, 1),       # one slot: two columns (the slot and the dummy)
 ])
 def test_one_step_from_seeded_state(U, I, K, eps, L, warm):
     r = synth.relevance_lowrank(U, I, seed=U + I)
@@ -155,6 +157,51 @@ def test_solve_stops_like_the_oracle():
     n_g, F_g = g.solve(thr, 60)
     assert n_g == n_o
     assert rel(F_g, F_o) < NSW_RTOL
+
+
+def test_single_consumer_uniform_policy_is_optimal_and_solve_stops_at_once():
+    """|U| = 1 from C = 0: the uniform policy (x_ik = b_k / |I|) is optimal, so the gradient
+    vanishes up to rounding and Algorithm 1's stop test ends the solve after its first step, on the
+    GPU as in the oracle; SGD keeps the policy uniform and F at the closed form
+    sum_i log(r_i sum_k e_k / |I|)."""
+    U, I, K = 1, 30, 5
+    r = synth.relevance_lowrank(U, I, seed=12)
+    g, o = pair(U, I, K, r, optimizer=fr.SGD, lr=0.5)
+    e = synth.dcg_exposure(K)
+    r64 = np.asarray(r, dtype=np.float32).astype(np.float64)[0]
+    F_unif = float(np.sum(np.log(r64 * e.sum() / I)))
+    t = 1e-4
+    n_g, F_g = g.solve(t, 20)
+    n_o, F_o = o.solve(t, 20)
+    assert n_g == n_o == 1
+    _, gn = g.trace()
+    assert gn.size == 1 and gn[0] <= 1e-5
+    assert rel(F_g, F_unif) < 1e-7 and rel(F_o, F_unif) < 1e-12
+    b = np.r_[np.ones(K), I - K] / I
+    np.testing.assert_allclose(g.policy()[0], np.broadcast_to(b, (I, K + 1)), atol=1e-6)
+
+
+@pytest.mark.parametrize("param", [fr.PARAM_FULL_C, fr.PARAM_ITEM])
+def test_single_item_single_slot(param):
+    """|I| = K = 1: one column, no dummy, so every policy is x = 1 whatever the costs; F is
+    log(sum_u r_u e_1) at every step and the gradient is zero up to FP32 rounding."""
+    U, I, K = 3, 1, 1
+    r = np.array([[0.3], [0.9], [0.55]], dtype=np.float32)
+    kw = {} if param == fr.PARAM_FULL_C else {"param": fr.PARAM_ITEM}
+    g, o = pair(U, I, K, r, sinkhorn_iters=10, **kw)
+    F_exact = float(np.log(r.astype(np.float64).sum()))  # e_1 = 1 / log2(2) = 1
+    imp, _, F = g.impacts()
+    assert rel(F, F_exact) < 1e-7 and rel(o.impacts()[2], F_exact) < 1e-14
+    np.testing.assert_allclose(imp, [r.astype(np.float64).sum()], rtol=1e-7)
+    np.testing.assert_allclose(g.policy(), np.ones((U, 1, 1)), atol=1e-7)
+    dg = g.grad()
+    assert np.max(np.abs(dg)) <= 1e-6
+    Fs = g.step(3)
+    Fo, _ = o.step(3)
+    np.testing.assert_allclose(Fs, F_exact, rtol=1e-7)
+    np.testing.assert_allclose(Fo, F_exact, rtol=1e-14)
+    np.testing.assert_allclose(g.policy(), np.ones((U, 1, 1)), atol=1e-7)
+    g.close()
 
 
 @pytest.mark.parametrize("param", [fr.PARAM_FULL_C, fr.PARAM_ITEM])

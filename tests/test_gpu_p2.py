@@ -55,6 +55,8 @@ def seeded(U, I, K, seed):
     (4, 50, 3, 30, False),      # generic 8-column bucket
     (4, 200, 12, 30, False),    # generic 16-column bucket
     (3, 20, 20, 25, False),     # |I| == K: no dummy column, generic 32-column bucket
+    (1, 60, 5, 40, False),      # one consumer
+    (4, 40, 1, 30, False),      # one slot: two columns
 ])
 def test_item_param_one_step_from_seeded_state(U, I, K, L, bf16):
     r = synth.relevance_lowrank(U, I, seed=I + K)
