@@ -425,7 +425,10 @@ def measure_forms():
     free_cost_gradients: 2000 x 1000 x 11, L = 50 -- the fused implicit step and the unrolled
     gradient's kernels (checkpoints every 10, and every iteration); batch: the 256-market workload, 8 ascent steps batched against 256 contexts run one
     after another;
-    metrics: fr_metrics (the envy contraction) at 20000 consumers x 10^4 items."""
+    metrics: fr_metrics (the envy contraction) at 20000 consumers x 10^4 items;
+    precision: the precision workload (200000 x 10^4, K = 20, L = 50) with BF16 against FP32
+    relevance storage, one ascent step from theta = 0 each: Sinkhorn kernel times, bytes of
+    relevance and the relative difference of F."""
     import torch
     from paper_2406_10262_gb300 import fairrank as fr
     from paper_2406_10262_gb300 import synth
@@ -499,6 +502,16 @@ def measure_forms():
         g.close()
     except Exception as ex:  # noqa: BLE001
         out["metrics"] = {"error": repr(ex)}
+    try:
+        c = compare_bf16(argparse.Namespace(steps=1))
+        res = {k: c[k] for k in ("n_users", "n_items", "n_slots", "sinkhorn_iters", "ascent_steps",
+                                 "rel_F_diff_final", "sweep_speedup")}
+        for name in ("fp32", "bf16"):
+            res[name] = {k: c[name][k] for k in ("sweep_ms", "grad_ms", "sweep_cell_updates_per_s",
+                                                 "relevance_bytes", "F_final")}
+        out["precision"] = res
+    except Exception as ex:  # noqa: BLE001
+        out["precision"] = {"error": repr(ex)}
     torch.cuda.synchronize()
     return out
 
