@@ -100,7 +100,12 @@ FR_API int32_t fr_num_cols(int32_t n_items, int32_t n_slots);
 /* Creates a context on the current CUDA device. stream: a cudaStream_t (NULL = legacy default
    stream); every later call is ordered on it. Allocates the optimiser state (zero costs / theta =
    the uniform policy, Algorithm 1's unspecified initialisation). FR_EINVAL on a bad config,
-   FR_EUNSUPPORTED on a shape outside the compiled variants, FR_ENOMEM. *out is NULL on error. */
+   FR_EUNSUPPORTED on a shape outside the compiled variants, FR_ENOMEM. *out is NULL on error.
+   Largest n_items by n_cols (a CTA has at most 512 threads and 227 KB of shared memory):
+   FR_PARAM_FULL_C 4096 for 11 columns, 2048 for 2-16 and 21, 1024 for 17-24 (except 21), from
+   992 down to 776 for 25-32, 512 for 33-45, from 496 down to 320 for 46-64;
+   FR_PARAM_ITEM 12288 for 6, 11 or 21 columns with BF16 relevance (11400, 11352 and 11088 with
+   FP32), 4096 for the other counts up to 32. */
 FR_API fr_status fr_create(const fr_config* cfg, void* stream, fr_ctx** out);
 FR_API fr_status fr_destroy(fr_ctx* ctx);
 

@@ -28,7 +28,15 @@ __device__ __forceinline__ float lg2_approx(float x) {
     return y;
 }
 
-constexpr int pow2ceil(int n) { return n <= 1 ? 1 : 2 * pow2ceil((n + 1) / 2); }
+// Smallest power of two >= n (1 for n <= 1). A loop, not a recursion: called with a run-time
+// argument (the shared-memory layouts), a recursive device function stays an out-of-line call
+// whose frames the compiler's per-thread stack size does not include, so a kernel whose own frame
+// is close to the stack limit would overrun it.
+__host__ __device__ __forceinline__ constexpr int pow2ceil(int n) {
+    int p = 1;
+    while (p < n) p *= 2;
+    return p;
+}
 
 // Adam's bias correction 1 - beta^t (beta in [0.5, 1), t >= 1) in FP32 without cancellation, as
 // -expm1(t log1p(beta - 1)): beta - 1 is exact, and the result keeps a few-ulp relative accuracy

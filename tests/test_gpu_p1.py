@@ -57,6 +57,10 @@ def test_initial_sweep_is_the_uniform_policy():
     (4, 40, 1, 1.0, 30, 1),       # one slot: two columns (the slot and the dummy)
 ])
 def test_one_step_from_seeded_state(U, I, K, eps, L, warm):
+    one_step_parity(U, I, K, eps, L, warm)
+
+
+def one_step_parity(U, I, K, eps, L, warm):
     r = synth.relevance_lowrank(U, I, seed=U + I)
     g, o = pair(U, I, K, r, epsilon=eps, sinkhorn_iters=L, warm_start=warm)
     C, m1, m2, gg = seeded_state(U, I, K, seed=I)
@@ -81,6 +85,31 @@ def test_one_step_from_seeded_state(U, I, K, eps, L, warm):
     po, m1o, m2o, ggo, to = o.get_state()
     assert tg == to == 4
     np.testing.assert_allclose(pg.reshape(-1), po, atol=2e-5, rtol=1e-5)
+
+
+# The largest shape of each free-cost variant (threads: one per R items, at most 512 per CTA;
+# shared memory: at most 227 KB per CTA, which the 32- and 64-column buckets reach first, since
+# they also hold the policy in shared memory for the Gram block), and the first shape past it.
+@pytest.mark.parametrize("I,K", [
+    (4096, 10),   # 11 columns, tile sweep at a 4096-float stride, 512 threads
+    (2048, 20),   # 21 columns, tile sweep at a 2048-float stride, 256 threads
+    (2048, 5),    # 8-column bucket, 512 threads
+    (2048, 15),   # 16-column bucket, 512 threads
+    (1024, 19),   # 32-column bucket, 512 threads
+    (776, 31),    # 32 columns: 776 items fill the shared memory
+    (512, 40),    # 64-column bucket, 512 threads
+    (320, 63),    # 64 columns: 320 items fill the shared memory
+])
+def test_largest_shape_of_each_free_cost_variant(I, K):
+    one_step_parity(2, I, K, 1.0, 10, 1)
+
+
+@pytest.mark.parametrize("I,K", [(4097, 10), (2049, 20), (2049, 5), (1025, 19), (777, 31),
+                                 (513, 40), (321, 63)])
+def test_free_cost_shapes_past_the_limits_are_rejected(I, K):
+    with pytest.raises(fr.FairRankError) as ei:
+        fr.FairRank(2, I, K)
+    assert ei.value.status == 7  # FR_EUNSUPPORTED, with the limit in the message
 
 
 def test_parity50_trajectory_against_golden():

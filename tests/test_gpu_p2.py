@@ -84,6 +84,43 @@ def test_item_param_one_step_from_seeded_state(U, I, K, L, bf16):
     np.testing.assert_allclose(pg, po, atol=2e-6, rtol=1e-5)
 
 
+# The largest shape of each per-item variant: 24 rows per thread and 512 threads give 12288 items
+# for 6, 11 and 21 columns with BF16 relevance; with FP32 relevance the gradient kernel's shared
+# arrays (20 bytes per item) fill the 227 KB first; the generic buckets take 8 rows per thread.
+@pytest.mark.parametrize("I,K,bf16", [
+    (12288, 20, True), (12288, 10, True), (12288, 5, True),
+    (11088, 20, False), (11352, 10, False), (11400, 5, False),
+    (4096, 3, False), (4096, 30, False),
+])
+def test_largest_shape_of_each_per_item_variant(I, K, bf16):
+    U, L = 2, 10
+    r = synth.relevance_lowrank_fast(U, I, seed=I + K)
+    g, o = pair_item(U, I, K, r, bf16=bf16, sinkhorn_iters=L)
+    th = synth.random_state(I, I, 0.4).astype(np.float32)
+    g.set_state(param=th)
+    o.set_state(param=th.astype(np.float64))
+    imp, _, F = g.impacts()
+    oimp, _, oF = o.impacts()
+    assert rel(F, oF) < NSW_RTOL
+    np.testing.assert_allclose(imp, oimp, rtol=1e-6)
+    np.testing.assert_allclose(g.policy(), o.policy(), atol=X_ATOL)
+    dth = g.grad()
+    oth = o.grad()
+    assert np.linalg.norm(dth - oth) <= 1e-5 * np.linalg.norm(oth)
+    Fg = g.step(1)
+    Fo, _ = o.step(1)
+    assert rel(Fg[0], Fo[0]) < NSW_RTOL
+    g.close()
+
+
+@pytest.mark.parametrize("I,K,bf16", [(12289, 20, True), (11096, 20, False), (11360, 10, False),
+                                      (11408, 5, False), (4097, 3, False)])
+def test_per_item_shapes_past_the_limits_are_rejected(I, K, bf16):
+    with pytest.raises(fr.FairRankError) as ei:
+        fr.FairRank(2, I, K, param=fr.PARAM_ITEM, rel_dtype=fr.BF16 if bf16 else fr.F32)
+    assert ei.value.status == 7  # FR_EUNSUPPORTED
+
+
 def test_item_param_trajectory():
     U, I, K = 40, 500, 10
     r = synth.relevance_lowrank(U, I, seed=3)
