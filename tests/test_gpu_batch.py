@@ -125,6 +125,29 @@ def test_batching_workload_size_sample():
         np.testing.assert_allclose(F[:, j], o.step(2)[0], rtol=NSW_RTOL)
 
 
+@pytest.mark.parametrize("param,sizes", [
+    # per-item markets at the batched limit (8 rows per thread, 512 threads): 4096 items
+    (fr.PARAM_ITEM, [(2, 4096, 20), (2, 4096, 10), (2, 4096, 5), (2, 4096, 30)]),
+    # free-cost markets at their variants' limits
+    (fr.PARAM_FULL_C, [(2, 4096, 10), (2, 2048, 20), (2, 2048, 5)]),
+])
+def test_batch_largest_markets_match_single_contexts(param, sizes):
+    L, steps = 10, 3
+    rs = [relevance(40 + j, U, I) for j, (U, I, K) in enumerate(sizes)]
+    b = make_batch(sizes, rs, param=param, sinkhorn_iters=L)
+    F = b.step(steps)
+    for j, ((U, I, K), r) in enumerate(zip(sizes, rs)):
+        g = fr.FairRank(U, I, K, param=param, sinkhorn_iters=L)
+        g.set_relevance(r)
+        g.set_exposure(synth.dcg_exposure(K))
+        np.testing.assert_allclose(F[:, j], g.step(steps), rtol=PAIR_RTOL)
+        g.close()
+    b.close()
+    with pytest.raises(fr.FairRankError) as ex:
+        fr.FairRankBatch([(2, 4097, 20)])
+    assert ex.value.status == 7
+
+
 def test_batch_rejections():
     with pytest.raises(fr.FairRankError) as ex:
         fr.FairRankBatch([(3, 5000, 10)])

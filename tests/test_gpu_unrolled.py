@@ -58,6 +58,13 @@ def l2rel(a, b):
     (3, 20, 20, 25, 25, False),     # |I| == K (no dummy column), padded 32-column bucket
     (4, 60, 5, 1, 10, False),       # L = 1: the output layer only
     (4, 60, 5, 9, 1, False),        # a checkpoint at every iteration
+    # the largest shapes (at most 256 threads): 24 rows per thread for 6, 11 and 21 columns,
+    # 8 rows for the padded buckets
+    (2, 6144, 20, 10, 5, False),    # 21 columns
+    (2, 6144, 10, 8, 4, True),      # 11 columns, BF16 relevance
+    (2, 6144, 5, 8, 3, False),      # 6 columns
+    (2, 2048, 3, 10, 5, False),     # padded 8-column bucket
+    (2, 2048, 30, 6, 3, False),     # padded 32-column bucket
 ])
 def test_unrolled_grad_matches_oracle(U, I, K, L, ce, bf16):
     r = synth.relevance_lowrank(U, I, seed=I + K + L)
@@ -250,6 +257,12 @@ def pair_unrolled_p1(U, I, K, r, L, ce, warm=True, **kw):
     (4, 50, 5, 7, 1),        # a checkpoint at every iteration: the sweep's records, no re-runs
     (5, 1000, 10, 12, 1),    # the same, recorded by the 11-column tile sweep
     (4, 300, 20, 15, 1),     # the same, 21 columns
+    # the largest shapes (at most 256 threads): 4 rows per thread up to 16 columns, 2 above
+    (2, 1024, 10, 10, 5),    # 11 columns
+    (2, 1024, 7, 8, 4),      # padded 8-column bucket, 8 columns
+    (2, 1024, 15, 8, 4),     # padded 16-column bucket, 16 columns
+    (2, 512, 20, 8, 4),      # 21 columns
+    (2, 512, 31, 6, 3),      # padded 32-column bucket, 32 columns
 ])
 def test_free_cost_unrolled_grad_matches_oracle(U, I, K, L, ce):
     """dL/dC of every cell and dL/dr from the adjoint kernel against the oracle's reverse sweep of
@@ -299,3 +312,13 @@ def test_free_cost_unrolled_limits():
     with pytest.raises(fr.FairRankError) as ei:
         fr.FairRank(4, 2000, 10, param=fr.PARAM_FULL_C, grad_mode=fr.GRAD_UNROLLED)
     assert ei.value.status == 7 and "n_items" in str(ei.value)
+
+
+@pytest.mark.parametrize("I,K,param", [
+    (1025, 10, fr.PARAM_FULL_C), (513, 20, fr.PARAM_FULL_C), (1025, 15, fr.PARAM_FULL_C),
+    (513, 31, fr.PARAM_FULL_C), (6145, 20, fr.PARAM_ITEM), (2049, 3, fr.PARAM_ITEM),
+])
+def test_unrolled_shapes_past_the_limits_are_rejected(I, K, param):
+    with pytest.raises(fr.FairRankError) as ei:
+        fr.FairRank(2, I, K, param=param, grad_mode=fr.GRAD_UNROLLED, ckpt_every=5)
+    assert ei.value.status == 7  # FR_EUNSUPPORTED
