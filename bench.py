@@ -410,14 +410,20 @@ def run_ours(args, w):
         line["cpu_baseline"] = info
     if rank == 0 and world == 1 and not args.no_forms:
         g.close()  # frees the headline context's device state before the other workloads
-        line["forms"] = measure_forms()
+        line["forms"] = measure_forms(peaks["ex2_per_s"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
 
-def measure_forms():
+def mufu_frac(cell_updates, m, ms, ex2_per_s):
+    """Fraction of the log-form Sinkhorn bound ((1 + 2/m) MUFU operations per cell-update at the
+    measured ex2 rate) reached by a sweep of `cell_updates` that took `ms` milliseconds."""
+    return cell_updates * (1.0 + 2.0 / m) / ex2_per_s / (ms * 1e-3)
+
+
+def measure_forms(ex2_per_s):
     """Short measurements of the layered forms, recorded beside the headline (each in its own
     try block, so a failure is reported instead of losing the line):
     per_item: |U| = 20000, |I| = 2000, K = 20, L = 100 -- Sinkhorn sweep, implicit gradient and
@@ -428,7 +434,9 @@ def measure_forms():
     metrics: fr_metrics (the envy contraction) at 20000 consumers x 10^4 items;
     precision: the precision workload (200000 x 10^4, K = 20, L = 50) with BF16 against FP32
     relevance storage, one ascent step from theta = 0 each: Sinkhorn kernel times, bytes of
-    relevance and the relative difference of F."""
+    relevance and the relative difference of F.
+    Sinkhorn kernels carry "sweep_mufu_frac": the log-form bound of (1 + 2/m) MUFU operations per
+    cell-update at the measured ex2 rate over the kernel's time (the headline's method bound)."""
     import torch
     from paper_2406_10262_gb300 import fairrank as fr
     from paper_2406_10262_gb300 import synth
@@ -457,6 +465,7 @@ def measure_forms():
         res["unrolled_ckpt_every_1"] = {"sweep_ms": ms[0], "grad_ms": ms[2]}
         g.close()
         res["sweep_cell_updates_per_s"] = cu / (res["implicit"]["sweep_ms"] * 1e-3)
+        res["sweep_mufu_frac"] = mufu_frac(cu, fr.num_cols(I, K), res["implicit"]["sweep_ms"], ex2_per_s)
         res["adjoint_over_sweep"] = res["unrolled"]["grad_ms"] / res["unrolled"]["sweep_ms"]
         res["adjoint_over_sweep_ckpt_every_1"] = (res["unrolled_ckpt_every_1"]["grad_ms"] /
                                                   res["unrolled_ckpt_every_1"]["sweep_ms"])
@@ -506,9 +515,12 @@ def measure_forms():
         c = compare_bf16(argparse.Namespace(steps=1))
         res = {k: c[k] for k in ("n_users", "n_items", "n_slots", "sinkhorn_iters", "ascent_steps",
                                  "rel_F_diff_final", "sweep_speedup")}
+        cu = c["n_users"] * c["n_items"] * fr.num_cols(c["n_items"], c["n_slots"]) * c["sinkhorn_iters"]
         for name in ("fp32", "bf16"):
             res[name] = {k: c[name][k] for k in ("sweep_ms", "grad_ms", "sweep_cell_updates_per_s",
                                                  "relevance_bytes", "F_final")}
+            res[name]["sweep_mufu_frac"] = mufu_frac(
+                cu, fr.num_cols(c["n_items"], c["n_slots"]), c[name]["sweep_ms"], ex2_per_s)
         out["precision"] = res
     except Exception as ex:  # noqa: BLE001
         out["precision"] = {"error": repr(ex)}
