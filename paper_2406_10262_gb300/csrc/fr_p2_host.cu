@@ -116,13 +116,18 @@ __global__ void exp_theta_kernel(const float* __restrict__ theta, float* __restr
 
 int p2_adam_blocks(int I) { return (I + AD_ITEMS - 1) / AD_ITEMS; }
 
-// Rows per thread: 8 for up to 1024 items, 16 up to 8192, 24 up to 12288 (CTA <= 512 threads).
+// Rows per thread: 8 for up to 1024 items, 16 up to 8192, 24 up to 12288 (CTA <= 512 threads);
+// 21 columns take 20 up to 10240 items. Above 8192 items one CTA fills an SM (its per-item arrays),
+// so the CTA's own warps are all the latency hiding there is: at 10^4 items 20 rows give 512
+// threads (16 warps, 115 registers) against 448 for 24, and the Sinkhorn kernel ran 73.0 instead
+// of 85.9 ms (the gradient kernel 19.9 instead of 22.0 ms) for 40000 consumers, L = 50.
 bool p2_select(int nc, int I, P2Variant* out) {
     auto threads_for = [&](int R) {
         const int t = (I + R - 1) / R;
         return (t + 31) / 32 * 32;
     };
     int R = I <= 1024 ? 8 : (threads_for(16) <= 512 ? 16 : 24);
+    if (R == 24 && nc == 21 && threads_for(20) <= 512) R = 20;
     if (threads_for(R) > 512) return false;
     const int T = threads_for(R);
     if (nc == 21) return p2_variant_k21(R, T, out);

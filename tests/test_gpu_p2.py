@@ -1,6 +1,6 @@
 """GPU parity of the per-item parametrisation c_uik = -r(u,i) e_k exp(theta_i) against the FP64
 oracle, through the C-ABI: FP32 and BF16 relevance (the oracle gets the same BF16-rounded values),
-exact and padded column counts, 8 / 16 / 24 rows per thread."""
+exact and padded column counts, 8 / 16 / 20 / 24 rows per thread."""
 import numpy as np
 import pytest
 
@@ -49,7 +49,8 @@ def seeded(U, I, K, seed):
 @pytest.mark.parametrize("U,I,K,L,bf16", [
     (9, 300, 20, 50, False),    # 21 columns, 8 rows/thread
     (5, 2000, 20, 30, True),    # 21 columns, 16 rows/thread, BF16 relevance
-    (3, 9000, 20, 20, False),   # 21 columns, 24 rows/thread
+    (3, 9000, 20, 20, False),   # 21 columns, 20 rows/thread
+    (2, 10500, 20, 15, False),  # 21 columns, 24 rows/thread
     (7, 129, 10, 40, False),    # 11 columns, ragged
     (6, 77, 5, 50, True),       # 6 columns
     (4, 50, 3, 30, False),      # generic 8-column bucket
