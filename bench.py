@@ -212,13 +212,15 @@ def workload_config(args, w, world):
             "parallelism": f"independent markets x{world}" if world > 1 else "single market"}
 
 
-def run_reference(args, w):
+def run_reference(args, w, budget_s=8.0):
+    """The reference arm: the FP64 oracle on the host cores, each step a sample of `budget_s`
+    seconds of the workload; rank 0 prints the line, other ranks return without work."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     rates = []
     for j in range(args.warmup + args.steps):
-        rate, info, dt = oracle_sample(w, seed=0, budget_s=8.0)
+        rate, info, dt = oracle_sample(w, seed=0, budget_s=budget_s)
         if j >= args.warmup:
             rates.append((rate, dt, info))
     value = statistics.median([x[0] for x in rates])
