@@ -60,3 +60,38 @@ def test_null_context_is_rejected(lib):
     assert lib.fr_step(None, 1, None) == 1
     assert lib.fr_impacts(None, None, None, None) == 1
     assert lib.fr_trace(None, 0, None, None, None) == 1
+
+
+def batch_cfgs(lib, sizes, param=fr.PARAM_ITEM):
+    cfgs = (fr.Config * len(sizes))()
+    for j, (U, I, K) in enumerate(sizes):
+        lib.fr_config_default(ct.byref(cfgs[j]), U, I, K, param)
+    return cfgs
+
+
+@pytest.mark.parametrize("sizes,param,fields,status", [
+    ([(3, 50, 5), (0, 40, 5)], fr.PARAM_ITEM, {}, 1),                       # no consumers
+    ([(3, 50, 5), (3, 4, 5)], fr.PARAM_ITEM, {}, 1),                        # K > |I|
+    ([(3, 50, 5), (3, 40, 5)], fr.PARAM_ITEM, {1: {"param": fr.PARAM_FULL_C}}, 1),  # mixed params
+    ([(3, 50, 5), (3, 40, 5)], fr.PARAM_ITEM, {1: {"epsilon": 0.5}}, 1),    # fields must match
+    ([(3, 50, 5)], fr.PARAM_FULL_C, {0: {"rel_dtype": fr.BF16}}, 7),        # free costs: FP32 r
+    ([(3, 50, 5)], fr.PARAM_ITEM, {0: {"grad_mode": fr.GRAD_UNROLLED}}, 7),  # implicit only
+    ([(3, 4097, 20)], fr.PARAM_ITEM, {}, 7),                                 # per-item <= 4096 items
+    ([(3, 50, 40)], fr.PARAM_ITEM, {}, 7),                                   # per-item <= 32 columns
+])
+def test_batch_create_rejects_before_touching_the_device(lib, sizes, param, fields, status):
+    cfgs = batch_cfgs(lib, sizes, param)
+    for j, f in fields.items():
+        for k, v in f.items():
+            setattr(cfgs[j], k, v)
+    h = ct.c_void_p()
+    assert lib.fr_batch_create(cfgs, len(sizes), None, ct.byref(h)) == status and not h.value
+    assert len(lib.fr_batch_last_error(None)) > 0
+
+
+def test_batch_create_rejects_null_arguments(lib):
+    h = ct.c_void_p()
+    cfgs = batch_cfgs(lib, [(3, 50, 5)])
+    assert lib.fr_batch_create(cfgs, 1, None, None) == 1
+    assert lib.fr_batch_create(None, 1, None, ct.byref(h)) == 1
+    assert lib.fr_batch_create(cfgs, 0, None, ct.byref(h)) == 1
