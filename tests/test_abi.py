@@ -95,3 +95,15 @@ def test_batch_create_rejects_null_arguments(lib):
     assert lib.fr_batch_create(cfgs, 1, None, None) == 1
     assert lib.fr_batch_create(None, 1, None, ct.byref(h)) == 1
     assert lib.fr_batch_create(cfgs, 0, None, ct.byref(h)) == 1
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No fallback: without the compiled library every entry point of the binding raises."""
+    monkeypatch.setattr(fr, "_lib", None)
+    monkeypatch.setattr(fr, "LIB_PATH", os.path.join(ROOT, "no-such-dir", "libfairrank.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        fr.lib()
+    with pytest.raises(RuntimeError, match="not built"):
+        fr.FairRank(4, 10, 3)
+    with pytest.raises(RuntimeError, match="not built"):
+        fr.FairRankBatch([(4, 10, 3)])
