@@ -294,6 +294,31 @@ def test_algorithm1_reaches_bruteforce_optimum(U, I, seed):
     np.testing.assert_allclose(imp, bf["imp"], rtol=2e-3)  # Imp* is unique
 
 
+def test_nsw_is_concave_in_the_policies():
+    """Eq. (5) with Eq. (4): F is a sum of logarithms of impacts linear in the policies, so
+    F((X + Y) / 2) >= (F(X) + F(Y)) / 2 for feasible X, Y, strictly when the impacts differ. The
+    oracle's F of chosen policies comes from Theorem 1's costs C_u = -eps log X_u, from which one
+    Sinkhorn iteration from g = 0 returns X_u (checked)."""
+    U, I, K = 3, 7, 3
+    r = synth.relevance_uniform(U, I, 5)
+
+    def F_of(Xs):
+        o = oracle.Oracle(U, I, K, iters=1, warm_start=False)
+        o.set_relevance(r)
+        o.set_exposure(synth.dcg_exposure(K))
+        o.set_state(param=np.stack([-np.log(X) for X in Xs]))
+        np.testing.assert_allclose(o.policy(), np.stack(Xs), rtol=1e-12, atol=1e-15)
+        return o.impacts()[2]
+
+    for seed in range(6):
+        Xs = [feasible_policy(I, K, seed=100 * seed + u) for u in range(U)]
+        Ys = [feasible_policy(I, K, seed=100 * seed + 50 + u) for u in range(U)]
+        Ms = [(x + y) / 2 for x, y in zip(Xs, Ys)]
+        fx, fy, fm = F_of(Xs), F_of(Ys), F_of(Ms)
+        assert fm > (fx + fy) / 2 + 1e-9
+        assert F_of(Xs) == fx  # deterministic
+
+
 def test_certificate_bounds_gap_for_random_feasible_policies():
     U, I = 3, 4
     r = synth.relevance_uniform(U, I, 7)
