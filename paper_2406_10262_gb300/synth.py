@@ -86,8 +86,10 @@ def relevance_lowrank(U: int, I: int, seed: int = 0, dim: int = 32, boost_frac: 
         nb = int(round(boost_frac * I))
         order = np.argsort(uniform(seed, S_BOOST, I), kind="stable")
         b[order[:nb]] += math.log(boost)
-    p_all_needed = normal(seed, S_P, (row0 + rows) * dim, std=std).reshape(row0 + rows, dim)
-    p = p_all_needed[row0:row0 + rows]
+    # the consumer factors of all U rows, then the block: `normal` pairs its Box-Muller draws
+    # according to the count requested, so drawing only row0 + rows rows would give other values
+    # (and blocks that repeat rows of other blocks)
+    p = normal(seed, S_P, U * dim, std=std).reshape(U, dim)[row0:row0 + rows]
     z = np.broadcast_to(b, (rows, I)).copy()
     for d in range(dim):
         z += p[:, d:d + 1] * q[None, :, d]
@@ -98,8 +100,9 @@ def relevance_lowrank(U: int, I: int, seed: int = 0, dim: int = 32, boost_frac: 
 def relevance_lowrank_fast(U: int, I: int, seed: int = 0, dim: int = 32, boost_frac: float = 0.0,
                            boost: float = 10.0, row0: int = 0, rows: int | None = None):
     """Same distribution as relevance_lowrank, float32 through a BLAS matmul: for matrices too
-    large for the elementwise path. Values may differ across machines in the last bits, so both
-    sides of any comparison must consume the same array."""
+    large for the elementwise path. Values may differ across machines, and a row block from the
+    same rows of the whole matrix, in the last bits (the matmul's blocking), so both sides of any
+    comparison must consume the same array."""
     rows = U - row0 if rows is None else rows
     std = 1.0 / math.sqrt(dim)
     q = normal(seed, S_Q, I * dim, std=std).reshape(I, dim).astype(np.float32)
@@ -108,7 +111,7 @@ def relevance_lowrank_fast(U: int, I: int, seed: int = 0, dim: int = 32, boost_f
         nb = int(round(boost_frac * I))
         order = np.argsort(uniform(seed, S_BOOST, I), kind="stable")
         b[order[:nb]] += math.log(boost)
-    p = normal(seed, S_P, (row0 + rows) * dim, std=std).reshape(row0 + rows, dim)[row0:]
+    p = normal(seed, S_P, U * dim, std=std).reshape(U, dim)[row0:row0 + rows]  # as above
     z = p.astype(np.float32) @ q.T
     z += b.astype(np.float32)[None, :]
     np.negative(z, out=z)
