@@ -90,3 +90,18 @@ def test_bf16_rounding_is_round_to_nearest_even():
     np.testing.assert_array_equal(ours, ref)
     np.testing.assert_array_equal(synth.bf16_bits_to_f64(ours),
                                   torch.from_numpy(x).to(torch.bfloat16).double().numpy())
+
+
+def test_batching_markets_follow_the_stated_distribution():
+    """|U| ~ U[100, 4000], |I| ~ U[100, 2000] (inclusive integers), K uniform over {5, 10, 20},
+    each market with its own relevance seed; reproducible."""
+    ms = synth.markets(3000, seed=0)
+    U = np.array([m.n_users for m in ms])
+    I = np.array([m.n_items for m in ms])
+    K = np.array([m.n_slots for m in ms])
+    assert U.min() >= 100 and U.max() <= 4000 and I.min() >= 100 and I.max() <= 2000
+    assert abs(U.mean() - 2050) < 60 and abs(I.mean() - 1050) < 30
+    assert set(K) == {5, 10, 20} and all(abs((K == k).mean() - 1 / 3) < 0.04 for k in (5, 10, 20))
+    assert len({m.seed for m in ms}) == len(ms) and np.all(I >= K)
+    assert [(m.n_users, m.n_items, m.n_slots, m.seed) for m in synth.markets(5, seed=0)] == \
+        [(m.n_users, m.n_items, m.n_slots, m.seed) for m in ms[:5]]
