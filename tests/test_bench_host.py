@@ -2,7 +2,6 @@
 cores; the same contract as the GPU arm's line), the rule that a recorded ncu traffic figure is
 reported only while the kernel's sources are unchanged, and the MUFU-bound fraction."""
 import argparse
-import hashlib
 import json
 import os
 import shutil
