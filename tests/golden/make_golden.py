@@ -15,8 +15,6 @@ import time
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
-import numpy as np  # noqa: E402
-
 import oracle  # noqa: E402
 from paper_2406_10262_gb300 import synth  # noqa: E402
 

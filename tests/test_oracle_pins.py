@@ -4,8 +4,6 @@ Every check compares the oracle with something other than itself: closed forms, 
 the characterisation of the entropic-OT optimum, finite differences, torch autograd and
 torch.optim in float64, and brute-force enumeration of permutation mixtures.
 """
-import itertools
-
 import numpy as np
 import pytest
 import torch
