@@ -46,3 +46,23 @@ def test_plain2000x1000_golden_starts_like_the_oracle():
     np.testing.assert_allclose(F0, g["F0"], rtol=RTOL)
     np.testing.assert_allclose(F, g["F"][:2], rtol=RTOL)
     np.testing.assert_allclose(gn, g["grad_norm"][:2], rtol=RTOL)
+
+
+def test_oracle_results_do_not_depend_on_its_thread_count():
+    """The stored trajectories are written on one machine and used on another with a different
+    core count: F, the gradient norms and the gradient must be bit-identical for any number of
+    OpenMP threads (every reduction over consumers runs in a fixed order)."""
+    U, I, K = 37, 60, 5
+    r = synth.relevance_lowrank(U, I, seed=9)
+    for param in (oracle.PARAM_FULL_C, oracle.PARAM_ITEM):
+        runs = []
+        for threads in (1, 3, 8):
+            o = oracle.Oracle(U, I, K, param=param, iters=20, threads=threads)
+            o.set_relevance(r)
+            o.set_exposure(synth.dcg_exposure(K))
+            F, gn = o.step(5)
+            runs.append((F, gn, np.asarray(o.grad()).ravel()))
+        for F, gn, g in runs[1:]:
+            np.testing.assert_array_equal(F, runs[0][0])
+            np.testing.assert_array_equal(gn, runs[0][1])
+            np.testing.assert_array_equal(g, runs[0][2])
